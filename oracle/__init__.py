@@ -1,0 +1,196 @@
+"""CPU oracle for the implicit distance-matrix product of Indyk & Silwal,
+"Faster Linear Algebra for Distance Matrices" (arXiv 2210.15114).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package's ``smoke()`` check and
+the benchmark's CPU-baseline leg use this module; the library never imports
+it, and it imports nothing from the library.  It shares no code with the CUDA
+path.
+
+Three forms, all plain and slow on purpose:
+
+* ``l1_rows`` / ``l2sq_rows`` -- the definition ``(AZ)[r,:] = sum_j f(x_r, x_j)
+  Z[j,:]`` written out as a double loop in C (``dm_oracle.c``), FP64 or exact
+  int64, for all rows or a sample of rows.  f is the l1 distance of Section 2
+  or the squared l2 distance of Appendix A.
+* ``l1_sort`` -- Algorithm 1 (Preprocessing: sort each coordinate) followed by
+  Algorithm 2 (Query for p = 1: prefix sums B_i of y_j x_j(i) and C_i of y_j
+  in sorted order, then z(k) += x_k(i)(S3 - S4) + S2 - S1), in numpy.
+* ``l2sq_identity`` -- the p = 2 query of Appendix A (Theorem
+  "l2_squared_upper_bound"), with the typos of the printed algorithm read as
+  the proof's Gram decomposition (Section 1.2): (Ay)_k = ||x_k||^2 sum_j y_j
+  + sum_j y_j ||x_j||^2 - 2 <x_k, sum_j y_j x_j>.
+
+Floating-point inputs are promoted to FP64 (FP32 data are compared on the same
+FP32 values, promoted); integer inputs are computed in int64, whose
+wrap-around arithmetic is exact whenever the true result fits in int64.
+
+The sort order is ascending and stable (ties keep index order).  Any order of
+equal values gives the same exact product, because tied pairs contribute
+|0| = 0 on either side of the split.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_lock = threading.Lock()
+_lib = None
+
+
+def _lib_path() -> str:
+    with open(_SRC, "rb") as f:
+        tag = hashlib.sha1(f.read()).hexdigest()[:12]
+    return os.path.join(_BUILD, f"liboracle_{tag}.so")
+
+
+def build() -> str:
+    """Compile ``dm_oracle.c`` with gcc (no fused multiply-add contraction, so
+    x86 and Arm hosts round identically).  Returns the library path."""
+    path = _lib_path()
+    if os.path.exists(path):
+        return path
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                           "-shared", "-fPIC", "-o", tmp, _SRC])
+    os.replace(tmp, path)
+    return path
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            p = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            for name in ("oracle_l1_rows_f64", "oracle_l2sq_rows_f64",
+                         "oracle_l1_rows_i64", "oracle_l2sq_rows_i64"):
+                fn = getattr(lib, name)
+                fn.argtypes = [p, i64, i64, p, i64, p, i64, p]
+                fn.restype = None
+            _lib = lib
+    return _lib
+
+
+def _is_int(a: np.ndarray) -> bool:
+    return np.issubdtype(a.dtype, np.integer)
+
+
+def _prep(X, Z):
+    X = np.asarray(X)
+    Z = np.asarray(Z)
+    if X.ndim == 1:
+        X = X[:, None]
+    squeeze = Z.ndim == 1
+    if squeeze:
+        Z = Z[:, None]
+    if X.shape[0] != Z.shape[0]:
+        raise ValueError("X and Z must have the same number of rows")
+    integer = _is_int(X) and _is_int(Z)
+    dt = np.int64 if integer else np.float64
+    return (np.ascontiguousarray(X, dtype=dt), np.ascontiguousarray(Z, dtype=dt),
+            squeeze, integer)
+
+
+def _rows_call(kind: str, X, Z, rows):
+    X, Z, squeeze, integer = _prep(X, Z)
+    n, d = X.shape
+    k = Z.shape[1]
+    if rows is None:
+        rows = np.arange(n, dtype=np.int64)
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    if rows.size and (rows.min() < 0 or rows.max() >= n):
+        raise IndexError("row index out of range")
+    out = np.zeros((rows.size, k), dtype=X.dtype)
+    fn = getattr(_load(), f"oracle_{kind}_rows_{'i64' if integer else 'f64'}")
+    fn(X.ctypes.data, n, d, Z.ctypes.data, k, rows.ctypes.data, rows.size,
+       out.ctypes.data)
+    return out[:, 0] if squeeze else out
+
+
+def l1_rows(X, Z, rows=None) -> np.ndarray:
+    """Definition of the l1 product (Section 2: A_ij = ||x_i - x_j||_1) for
+    the given rows (all rows when ``rows`` is None).  O(n d k) per row."""
+    return _rows_call("l1", X, Z, rows)
+
+
+def l2sq_rows(X, Z, rows=None) -> np.ndarray:
+    """Definition of the squared-l2 product (Appendix A: A_ij =
+    ||x_i - x_j||_2^2) for the given rows.  O(n d k) per row."""
+    return _rows_call("l2sq", X, Z, rows)
+
+
+def preprocessing_order(column) -> np.ndarray:
+    """Algorithm 1 for one coordinate: the order pi^i that sorts the i-th
+    coordinates ascending (stable; ties keep index order)."""
+    return np.argsort(np.asarray(column), kind="stable")
+
+
+def l1_sort(X, Z) -> np.ndarray:
+    """Algorithms 1 and 2 (Section 2) for the l1 product of every row.
+
+    For each coordinate i: sort (Algorithm 1), then form the prefix arrays
+    B_i (partial sums of y_j x_j(i)) and C_i (partial sums of y_j) in the
+    sorted order, with B_i[q] / C_i[q] the sums over the q points that come
+    strictly before position q -- the sets {j : pi(j) < pi(k)} of the proof of
+    Theorem "p=1".  For every point k at position q:
+        S1 = B_i[q], S2 = B_i[n] - B_i[q], S3 = C_i[q], S4 = C_i[n] - C_i[q],
+        z(k) += x_k(i) (S3 - S4) + S2 - S1.
+    Each column of a block Z is an independent query (Lemma "matrixmult").
+    """
+    X, Z, squeeze, _ = _prep(X, Z)
+    n, d = X.shape
+    out = np.zeros(Z.shape, dtype=X.dtype)
+    zero_row = np.zeros((1, Z.shape[1]), dtype=X.dtype)
+    for i in range(d):
+        order = preprocessing_order(X[:, i])                 # Algorithm 1
+        xs = X[order, i]
+        ys = Z[order]
+        B = np.concatenate([zero_row, np.cumsum(xs[:, None] * ys, axis=0)])
+        C = np.concatenate([zero_row, np.cumsum(ys, axis=0)])
+        q = np.empty(n, dtype=np.int64)
+        q[order] = np.arange(n)                               # position of x_k(i)
+        S1 = B[q]
+        S2 = B[n] - B[q]
+        S3 = C[q]
+        S4 = C[n] - C[q]
+        out += X[:, i, None] * (S3 - S4) + S2 - S1
+    return out[:, 0] if squeeze else out
+
+
+def l2sq_identity(X, Z) -> np.ndarray:
+    """Query for p = 2 (Appendix A), every row:
+        v  = sum_j y_j x_j          (d x k)
+        S1 = sum_j y_j              (k)
+        S2 = sum_j y_j ||x_j||^2    (k)
+        z(k) = S1 ||x_k||^2 + S2 - 2 <x_k, v>.
+    The printed algorithm squares y_j in S1 and S2; the proof's Gram
+    decomposition (Section 1.2) fixes the reading used here."""
+    X, Z, squeeze, _ = _prep(X, Z)
+    sq = np.einsum("ij,ij->i", X, X)
+    v = X.T @ Z
+    S1 = Z.sum(axis=0)
+    S2 = sq @ Z
+    out = sq[:, None] * S1[None, :] + S2[None, :] - 2 * (X @ v)
+    return out[:, 0] if squeeze else out
+
+
+def relative_error(got, want) -> float:
+    """Frobenius relative error ||got - want|| / ||want|| over the whole block
+    (0 when both are zero)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    den = np.linalg.norm(want)
+    num = np.linalg.norm(got - want)
+    if den == 0.0:
+        return 0.0 if num == 0.0 else float("inf")
+    return float(num / den)

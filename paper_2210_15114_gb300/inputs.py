@@ -1,0 +1,98 @@
+"""Seeded synthetic inputs for the distance-matrix product.
+
+This module only draws numbers; it holds none of the method's arithmetic.
+Both the CUDA path (through the tests and the benchmark) and the CPU oracle
+receive the very same arrays from here.  Every generator uses numpy's PCG64
+``default_rng(seed)``, draws in FP64 and casts at the end, so a FP32 input is
+the FP64 draw rounded once.
+
+Workload shapes follow the paper's own experiments (Section 4: points from a
+mixture of spherical Gaussians; query vectors with Gaussian entries) and the
+sizes the library is benchmarked on:
+
+* ``uniform_points``   -- coordinates uniform in [lo, hi).
+* ``gaussian_mixture`` -- ``clusters`` spherical Gaussians, cluster means drawn
+  N(0, mean_sd^2) per coordinate, within-cluster sd ``sd``, cluster chosen
+  uniformly per point.
+* ``integer_points``   -- integer coordinates uniform in [lo, hi).
+* ``gaussian_queries`` -- query block Z with N(0, 1) entries.
+* ``integer_queries``  -- integer query block uniform in [lo, hi].
+* ``grid_1d``          -- the 1-D grid x_i = i.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_X = 0
+SEED_Z = 1
+
+
+def uniform_points(n: int, d: int, seed: int = SEED_X, lo: float = 0.0,
+                   hi: float = 1.0, dtype=np.float64) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(n, d)).astype(dtype)
+
+
+def gaussian_mixture(n: int, d: int, clusters: int, seed: int = SEED_X,
+                     mean_sd: float = 10.0, sd: float = 1.0,
+                     dtype=np.float32) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    means = rng.normal(0.0, mean_sd, size=(clusters, d))
+    label = rng.integers(0, clusters, size=n)
+    pts = means[label] + rng.normal(0.0, sd, size=(n, d))
+    return pts.astype(dtype)
+
+
+def integer_points(n: int, d: int, seed: int = SEED_X, lo: int = 0,
+                   hi: int = 1 << 16, dtype=np.int32) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi, size=(n, d)).astype(dtype)
+
+
+def gaussian_queries(n: int, k: int, seed: int = SEED_Z,
+                     dtype=np.float32) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, 1.0, size=(n, k)).astype(dtype)
+
+
+def integer_queries(n: int, k: int, seed: int = SEED_Z, lo: int = -100,
+                    hi: int = 100, dtype=np.int32) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, size=(n, k)).astype(dtype)
+
+
+def grid_1d(n: int, dtype=np.float64) -> np.ndarray:
+    return np.arange(n, dtype=np.float64).reshape(n, 1).astype(dtype)
+
+
+def sample_rows(n: int, count: int, seed: int = 7) -> np.ndarray:
+    """Row indices for sampled checks: the first and last rows plus a seeded
+    uniform sample, sorted and unique."""
+    rng = np.random.default_rng(seed)
+    rows = np.concatenate([[0, n - 1], rng.integers(0, n, size=max(0, count - 2))])
+    return np.unique(rows.astype(np.int64))
+
+
+# The workloads the library is measured and checked on.
+def workload_small_f64():
+    """n = 4096 points, d = 8, coordinates uniform [0, 1) in FP64; one FP64
+    Gaussian query."""
+    X = uniform_points(4096, 8, SEED_X, dtype=np.float64)
+    z = gaussian_queries(4096, 1, SEED_Z, dtype=np.float64)
+    return X, z
+
+
+def workload_mixture_f32(n: int = 1 << 20, d: int = 32, k: int = 16):
+    """16-cluster Gaussian mixture (means N(0, 10^2), sd 1), FP32 points and an
+    FP32 N(0, 1) query block of k columns."""
+    X = gaussian_mixture(n, d, 16, SEED_X, 10.0, 1.0, dtype=np.float32)
+    Z = gaussian_queries(n, k, SEED_Z, dtype=np.float32)
+    return X, Z
+
+
+def workload_integer(n: int = 1 << 20, d: int = 32, k: int = 16):
+    """int32 coordinates uniform in [0, 2^16), int32 query entries uniform in
+    [-100, 100]."""
+    X = integer_points(n, d, SEED_X, 0, 1 << 16)
+    Z = integer_queries(n, k, SEED_Z, -100, 100)
+    return X, Z
