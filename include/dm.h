@@ -1,0 +1,144 @@
+/*
+ * dm.h -- C ABI of the GB300 (sm_103a) library for implicit distance-matrix
+ * products, after Indyk & Silwal, "Faster Linear Algebra for Distance
+ * Matrices" (arXiv 2210.15114).
+ *
+ * Given n points x_1..x_n in R^d (the rows of X) and a block Z of k query
+ * columns, the library returns
+ *
+ *     out = A Z,    A_ij = f(x_i, x_j),
+ *
+ * for f = ||x - y||_1 (Section 2, Algorithms 1 and 2, Theorem "p=1") or
+ * f = ||x - y||_2^2 (Appendix A, Theorem "l2_squared_upper_bound" with the
+ * Gram decomposition of Section 1.2).  A is never formed.  A block Z is k
+ * independent queries sharing one preprocessing (Lemma "matrixmult").
+ *
+ * Conventions shared by every call:
+ *  - All array arguments are DEVICE pointers (caller-owned, any CUDA
+ *    allocation reachable from the context's device) unless the name ends in
+ *    _host.  Matrices are row-major with a leading dimension in elements:
+ *    X is n x d (ldx >= d), Z is n x k (ldz >= k), out is n x k (ldo >= k).
+ *  - Element types: DM_F32 points take F32 queries and give F32 results;
+ *    DM_F64 -> F64; DM_I32 points take I32 queries and give INT64 results
+ *    (exact: two's-complement arithmetic is exact whenever the true result
+ *    fits in int64).
+ *  - Every call is asynchronous on the context's stream.  Argument errors are
+ *    returned at once.  Errors found on the device (non-finite coordinates,
+ *    a bounded wait that ran out, an index check) are latched in the
+ *    context's error word and returned by the next dm_sync (dm_prepare and
+ *    dm_matmat_host synchronize and return them too).
+ *  - n >= 1, d >= 1, k >= 1, n < 2^30 (positions and tile counts are 32-bit).
+ *  - A call never reads outside the rows and columns described by its sizes
+ *    and leading dimensions.
+ */
+#ifndef DM_H
+#define DM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DM_OK = 0,
+    DM_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad leading dimension */
+    DM_ERR_UNSUPPORTED = 2,   /* valid call that this build does not handle    */
+    DM_ERR_NONFINITE = 3,     /* NaN or Inf among the point coordinates        */
+    DM_ERR_OOM = 4,           /* device allocation failed                      */
+    DM_ERR_CUDA = 5,          /* CUDA runtime error (launch, copy, device)     */
+    DM_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out            */
+    DM_ERR_INTERNAL = 7       /* a device-side consistency check failed (an
+                                 index out of range was skipped)              */
+} dm_status;
+
+typedef enum { DM_F32 = 0, DM_F64 = 1, DM_I32 = 2 } dm_dtype;
+typedef enum { DM_L1 = 0, DM_L2SQ = 1 } dm_metric;
+
+typedef struct dm_ctx dm_ctx;     /* opaque: device, stream, scratch, error word */
+typedef struct dm_plan dm_plan;   /* opaque: one preprocessed point set          */
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is borrowed:
+ * the caller keeps it alive for the context's lifetime.  The context owns a
+ * scratch arena (grown on demand, reused across calls) and a device error
+ * word. */
+dm_status dm_create(dm_ctx** ctx, int device, void* cuda_stream);
+
+/* Synchronize the stream and free the context.  Plans made from it must be
+ * destroyed first. */
+void dm_destroy(dm_ctx* ctx);
+
+/* Switch the stream later calls are issued on (borrowed, as in dm_create). */
+dm_status dm_set_stream(dm_ctx* ctx, void* cuda_stream);
+
+/* Preprocess a point set (Algorithm 1, Section 2, for DM_L1; Appendix A for
+ * DM_L2SQ).
+ *   DM_L1:   every coordinate column of X is sorted ascending with a stable
+ *            LSD radix sort; the plan owns the sorted values (d x n) and the
+ *            sorting permutation (d x n, int32).  X may be freed afterwards.
+ *   DM_L2SQ: the plan records the pointer X (the caller keeps X alive and
+ *            unchanged for the plan's lifetime), the column means mu (a shift:
+ *            the product is translation invariant) and s_i = ||x_i - mu||^2.
+ * This call synchronizes the context's stream once (DM_L1 reads the digit
+ * histograms back to skip radix passes whose digit is constant).  Returns
+ * DM_ERR_NONFINITE if X holds NaN or Inf. */
+dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* X,
+                     int64_t n, int64_t d, int64_t ldx, dm_plan** plan);
+
+/* Free a plan (stream-ordered: waits for the context's stream first). */
+void dm_plan_destroy(dm_plan* plan);
+
+/* out = A z for one query column z (n elements, contiguous) on an l1 plan
+ * (Algorithm 2: prefix sums of z and x.z in sorted order, evaluated per
+ * point and summed over coordinates).  out has n elements. */
+dm_status dm_matvec_l1(dm_plan* plan, const void* z, void* out);
+
+/* out = A z for one query column on a squared-l2 plan (Appendix A:
+ * (Az)_i = ||x_i||^2 (1^T z) + (||x||^2)^T z - 2 <x_i, X^T z>, in the mu-shifted
+ * frame). */
+dm_status dm_matvec_l2sq(dm_plan* plan, const void* z, void* out);
+
+/* out = A Z for a block of k query columns on a plan of either metric
+ * (Lemma "matrixmult": k independent queries sharing one preprocessing). */
+dm_status dm_matmat(dm_plan* plan, const void* Z, int64_t k, int64_t ldz,
+                    void* out, int64_t ldo);
+
+/* Wait for the context's stream and return (then clear) the first device-side
+ * error latched since the last dm_sync. */
+dm_status dm_sync(dm_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* dm_status_string(dm_status status);
+
+/* Copy an l1 plan's sorted coordinates (d x n, element type of the plan) and
+ * sorting permutation (d x n int32; row c lists the point indices in
+ * ascending order of coordinate c, ties in index order) into caller device
+ * buffers.  DM_ERR_INVALID_ARG for a squared-l2 plan. */
+dm_status dm_plan_export(dm_plan* plan, void* sorted_values, int32_t* perm);
+
+/* The plain method: out = A Z with every entry f(x_i, x_j) computed on the
+ * fly, O(n^2 (d + k)) work (the paper's naive baseline of Section 4, without
+ * materializing A).  Needs d <= 64. */
+dm_status dm_bruteforce(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
+                        const void* X, int64_t n, int64_t d, int64_t ldx,
+                        const void* Z, int64_t k, int64_t ldz,
+                        void* out, int64_t ldo);
+
+/* End to end with HOST buffers: copies X and Z to the device, preprocesses,
+ * computes out = A Z, copies out back and synchronizes.  Host buffers may be
+ * pageable or pinned (pinned is faster).  Device buffers are taken from the
+ * context's scratch arena. */
+dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
+                         const void* X_host, int64_t n, int64_t d, int64_t ldx,
+                         const void* Z_host, int64_t k, int64_t ldz,
+                         void* out_host, int64_t ldo);
+
+/* Number of kernels this context has launched so far (all calls). */
+int64_t dm_launch_count(const dm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DM_H */

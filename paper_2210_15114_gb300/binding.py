@@ -1,0 +1,298 @@
+"""ctypes binding of libdm's C ABI (include/dm.h).
+
+Each function here has the name of the C entry point it calls and does only
+argument marshalling: torch CUDA tensors become device pointers, numpy arrays
+become host pointers, the current torch stream becomes the context's stream.
+All computation happens in the CUDA kernels of libdm.  A missing or unloadable
+library raises ``DMError`` at once: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB, up_to_date
+
+DM_OK = 0
+DM_ERR_INVALID_ARG = 1
+DM_ERR_UNSUPPORTED = 2
+DM_ERR_NONFINITE = 3
+DM_ERR_OOM = 4
+DM_ERR_CUDA = 5
+DM_ERR_TIMEOUT = 6
+DM_ERR_INTERNAL = 7
+
+DM_F32, DM_F64, DM_I32 = 0, 1, 2
+DM_L1, DM_L2SQ = 0, 1
+
+METRICS = {"l1": DM_L1, "l2sq": DM_L2SQ}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = dm_status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{where}: {name}")
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libdm.so (built in-tree by build.build()).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB):
+            raise DMError(-1, f"libdm not built ({LIB} missing); run "
+                              "paper_2210_15114_gb300.build.build()")
+        if not up_to_date():
+            raise DMError(-1, "libdm.so is older than its sources; rebuild it")
+        lib = ctypes.CDLL(LIB)
+        P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        sigs = {
+            "dm_create": ([ctypes.POINTER(P), I32, P], I32),
+            "dm_destroy": ([P], None),
+            "dm_set_stream": ([P, P], I32),
+            "dm_prepare": ([P, I32, I32, P, I64, I64, I64, ctypes.POINTER(P)], I32),
+            "dm_plan_destroy": ([P], None),
+            "dm_matvec_l1": ([P, P, P], I32),
+            "dm_matvec_l2sq": ([P, P, P], I32),
+            "dm_matmat": ([P, P, I64, I64, P, I64], I32),
+            "dm_sync": ([P], I32),
+            "dm_status_string": ([I32], ctypes.c_char_p),
+            "dm_plan_export": ([P, P, P], I32),
+            "dm_bruteforce": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
+            "dm_matmat_host": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
+            "dm_launch_count": ([P], I64),
+        }
+        for name, (args, res) in sigs.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != DM_OK:
+        raise DMError(status, where)
+
+
+# ----------------------------------------------------------- dtype helpers
+def dtype_code(t) -> int:
+    """Map a torch or numpy dtype of the points to dm_dtype."""
+    import torch
+    table = {torch.float32: DM_F32, torch.float64: DM_F64, torch.int32: DM_I32,
+             np.dtype(np.float32): DM_F32, np.dtype(np.float64): DM_F64,
+             np.dtype(np.int32): DM_I32}
+    key = t if isinstance(t, torch.dtype) else np.dtype(t)
+    if key not in table:
+        raise DMError(DM_ERR_UNSUPPORTED, f"element type {t}")
+    return table[key]
+
+
+def out_torch_dtype(code: int):
+    import torch
+    return {DM_F32: torch.float32, DM_F64: torch.float64, DM_I32: torch.int64}[code]
+
+
+def out_numpy_dtype(code: int):
+    return {DM_F32: np.float32, DM_F64: np.float64, DM_I32: np.int64}[code]
+
+
+def _ld(t) -> int:
+    """Leading dimension (elements) of a row-major 2-D tensor/array view."""
+    if t.ndim == 1:
+        return 1
+    if hasattr(t, "stride") and callable(t.stride):
+        st = t.stride()
+        if st[1] != 1:
+            raise DMError(DM_ERR_INVALID_ARG, "matrix rows must be contiguous")
+        return st[0]
+    st = t.strides
+    if st[1] != t.itemsize:
+        raise DMError(DM_ERR_INVALID_ARG, "matrix rows must be contiguous")
+    return st[0] // t.itemsize
+
+
+def _dev_ptr(t) -> int:
+    if not t.is_cuda:
+        raise DMError(DM_ERR_INVALID_ARG, "expected a CUDA tensor")
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------- entry points
+class Context:
+    """Owner of a dm_ctx handle (device, stream, scratch arena)."""
+
+    def __init__(self, handle: int, device: int):
+        self.handle = handle
+        self.device = device
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dm_destroy(self.handle)
+            self.handle = None
+
+
+class Plan:
+    """Owner of a dm_plan handle."""
+
+    def __init__(self, handle: int, ctx: Context, metric: int, dtype: int, n: int, d: int):
+        self.handle = handle
+        self.ctx = ctx
+        self.metric = metric
+        self.dtype = dtype
+        self.n = n
+        self.d = d
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dm_plan_destroy(self.handle)
+            self.handle = None
+
+
+def dm_create(device: int = 0, stream=None) -> Context:
+    """dm_create on `device`; the stream defaults to torch's current stream."""
+    import torch
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    h = ctypes.c_void_p()
+    _check(lib.dm_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream)), "dm_create")
+    return Context(h.value, int(device))
+
+
+def dm_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        load().dm_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def dm_set_stream(ctx: Context, stream) -> None:
+    _check(load().dm_set_stream(ctx.handle, ctypes.c_void_p(stream)), "dm_set_stream")
+
+
+def dm_prepare(ctx: Context, metric, X) -> Plan:
+    """dm_prepare on a CUDA tensor X (n x d, rows contiguous)."""
+    lib = load()
+    m = METRICS[metric] if isinstance(metric, str) else int(metric)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    code = dtype_code(X.dtype)
+    n, d = X.shape
+    h = ctypes.c_void_p()
+    _check(lib.dm_prepare(ctx.handle, m, code, ctypes.c_void_p(_dev_ptr(X)), n, d, _ld(X),
+                          ctypes.byref(h)), "dm_prepare")
+    plan = Plan(h.value, ctx, m, code, n, d)
+    plan.X = X if m == DM_L2SQ else None   # the squared-l2 plan borrows X
+    return plan
+
+
+def dm_plan_destroy(plan: Plan) -> None:
+    if plan.handle:
+        load().dm_plan_destroy(plan.handle)
+        plan.handle = None
+
+
+def _alloc_out(plan: Plan, Z, out):
+    import torch
+    k = 1 if Z.ndim == 1 else Z.shape[1]
+    shape = (plan.n,) if Z.ndim == 1 else (plan.n, k)
+    if out is None:
+        out = torch.empty(shape, dtype=out_torch_dtype(plan.dtype), device=Z.device)
+    return out, k
+
+
+def dm_matvec_l1(plan: Plan, z, out=None):
+    out, _ = _alloc_out(plan, z, out)
+    _check(load().dm_matvec_l1(plan.handle, ctypes.c_void_p(_dev_ptr(z)),
+                               ctypes.c_void_p(_dev_ptr(out))), "dm_matvec_l1")
+    return out
+
+
+def dm_matvec_l2sq(plan: Plan, z, out=None):
+    out, _ = _alloc_out(plan, z, out)
+    _check(load().dm_matvec_l2sq(plan.handle, ctypes.c_void_p(_dev_ptr(z)),
+                                 ctypes.c_void_p(_dev_ptr(out))), "dm_matvec_l2sq")
+    return out
+
+
+def dm_matmat(plan: Plan, Z, out=None):
+    if dtype_code(Z.dtype) != plan.dtype:
+        raise DMError(DM_ERR_INVALID_ARG, "Z element type differs from the plan's")
+    out, k = _alloc_out(plan, Z, out)
+    _check(load().dm_matmat(plan.handle, ctypes.c_void_p(_dev_ptr(Z)), k, _ld(Z) if Z.ndim == 2 else 1,
+                            ctypes.c_void_p(_dev_ptr(out)), _ld(out) if out.ndim == 2 else 1),
+           "dm_matmat")
+    return out
+
+
+def dm_sync(ctx: Context) -> None:
+    _check(load().dm_sync(ctx.handle), "dm_sync")
+
+
+def dm_status_string(status: int) -> str:
+    return load().dm_status_string(int(status)).decode()
+
+
+def dm_plan_export(plan: Plan):
+    """Sorted coordinates (d x n) and permutation (d x n int32) of an l1 plan."""
+    import torch
+    tdt = {DM_F32: torch.float32, DM_F64: torch.float64, DM_I32: torch.int32}[plan.dtype]
+    dev = torch.device("cuda", plan.ctx.device)
+    vals = torch.empty((plan.d, plan.n), dtype=tdt, device=dev)
+    perm = torch.empty((plan.d, plan.n), dtype=torch.int32, device=dev)
+    _check(load().dm_plan_export(plan.handle, ctypes.c_void_p(vals.data_ptr()),
+                                 ctypes.c_void_p(perm.data_ptr())), "dm_plan_export")
+    return vals, perm
+
+
+def dm_bruteforce(ctx: Context, metric, X, Z, out=None):
+    import torch
+    m = METRICS[metric] if isinstance(metric, str) else int(metric)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    code = dtype_code(X.dtype)
+    squeeze = Z.ndim == 1
+    Z2 = Z.reshape(-1, 1) if squeeze else Z
+    n, d = X.shape
+    k = Z2.shape[1]
+    if out is None:
+        out = torch.empty((n, k), dtype=out_torch_dtype(code), device=X.device)
+    o2 = out.reshape(-1, 1) if out.ndim == 1 else out
+    _check(load().dm_bruteforce(ctx.handle, m, code, ctypes.c_void_p(_dev_ptr(X)), n, d, _ld(X),
+                                ctypes.c_void_p(_dev_ptr(Z2)), k, _ld(Z2),
+                                ctypes.c_void_p(_dev_ptr(o2)), _ld(o2)), "dm_bruteforce")
+    return out.reshape(-1) if squeeze else out
+
+
+def dm_matmat_host(ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out: np.ndarray = None):
+    """End to end with host (numpy) buffers; returns the numpy result."""
+    m = METRICS[metric] if isinstance(metric, str) else int(metric)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    squeeze = Z.ndim == 1
+    Z2 = Z.reshape(-1, 1) if squeeze else Z
+    code = dtype_code(X.dtype)
+    n, d = X.shape
+    k = Z2.shape[1]
+    if out is None:
+        out = np.empty((n, k), dtype=out_numpy_dtype(code))
+    _check(load().dm_matmat_host(ctx.handle, m, code, ctypes.c_void_p(X.ctypes.data), n, d, _ld(X),
+                                 ctypes.c_void_p(Z2.ctypes.data), k, _ld(Z2),
+                                 ctypes.c_void_p(out.ctypes.data), _ld(out)), "dm_matmat_host")
+    return out.reshape(-1) if squeeze else out
+
+
+def dm_launch_count(ctx: Context) -> int:
+    return int(load().dm_launch_count(ctx.handle))

@@ -1,0 +1,159 @@
+// Internal declarations shared by the CUDA translation units of libdm.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "../../include/dm.h"
+
+namespace dm {
+
+// ------------------------------------------------------------------ errors
+// Device error word values (first error wins, see set_error()).
+enum : uint32_t { kErrNone = 0, kErrNonfinite = DM_ERR_NONFINITE, kErrTimeout = DM_ERR_TIMEOUT,
+                  kErrInternal = DM_ERR_INTERNAL };
+
+// Iteration cap of every device-side spin wait (with a short __nanosleep per
+// round, about a second in total).  On expiry the waiting kernel latches
+// DM_ERR_TIMEOUT, stops waiting and finishes its tile with what it has.
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ void set_error(uint32_t* err, uint32_t code) {
+    atomicCAS(err, 0u, code);
+}
+
+// ----------------------------------------------------------- memory order
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// ------------------------------------------------------------ element types
+template <dm_dtype DT> struct Types;
+template <> struct Types<DM_F32> {
+    using V = float;      // coordinate / query element
+    using Acc = float;    // per-element and in-tile arithmetic
+    using Wide = double;  // per-tile and cross-tile arithmetic
+    using Out = float;    // result element
+    using Key = uint32_t; // radix key
+};
+template <> struct Types<DM_F64> {
+    using V = double; using Acc = double; using Wide = double; using Out = double;
+    using Key = unsigned long long;
+};
+template <> struct Types<DM_I32> {
+    using V = int32_t; using Acc = long long; using Wide = long long; using Out = long long;
+    using Key = uint32_t;
+};
+
+inline size_t dtype_size(dm_dtype t) { return t == DM_F64 ? 8 : 4; }
+inline size_t out_size(dm_dtype t) { return t == DM_F32 ? 4 : 8; }
+inline int key_bits(dm_dtype t) { return t == DM_F64 ? 64 : 32; }
+
+// ---------------------------------------------------------------- launches
+// Radix sort of every coordinate column (Algorithm 1).
+struct SortArgs {
+    dm_dtype dtype;
+    const void* X; int64_t n, d, ldx;
+    void* keys_a; void* keys_b;          // d x n keys (ping-pong)
+    int32_t* vals_a; int32_t* vals_b;    // d x n payload (ping-pong)
+    uint32_t* hist;                      // d x passes x 256 digit counts
+    uint32_t* lookback;                  // passes x d x tiles x 256 status words
+    uint32_t* counters;                  // passes tile counters
+    void* sorted_out; int32_t* perm_out; // plan outputs, d x n
+    uint32_t* err;
+};
+size_t sort_hist_words(dm_dtype t, int64_t d);
+size_t sort_lookback_words(dm_dtype t, int64_t n, int64_t d);
+int sort_passes(dm_dtype t);
+// Launch the keygen + histogram kernel.
+cudaError_t sort_launch_keygen(const SortArgs& a, cudaStream_t s, int64_t* launches);
+// Launch the radix passes listed in pass_list (digit positions, ascending).
+cudaError_t sort_launch_passes(const SortArgs& a, const int* pass_list, int npass,
+                               cudaStream_t s, int64_t* launches);
+
+// Column sums of the query block and the shifted contraction:
+//   u[j]   = sum_i Z[i,j]
+//   W[c,j] = sum_i (X[i,c] - mu[c]) Z[i,j]      (mu == nullptr: no shift)
+//   v[j]   = sum_i s[i] Z[i,j]                  (only when s != nullptr)
+// Result layout in `res` (Wide type): W (d x k), then u (k), then v (k).
+// X holds V elements, or Acc elements when x_acc is set.
+struct ReduceArgs {
+    dm_dtype dtype;
+    const void* X; int64_t n, d, ldx;
+    bool x_acc;
+    const void* mu; int64_t mu_stride;   // shift mu[c] = mu[c * mu_stride] (V type)
+    const void* s;                       // optional, Acc type, n entries
+    const void* Z; int64_t k, ldz;
+    void* partial;                       // scratch: blocks x (d+2) x k Wide
+    void* res;                           // (d+2) x k Wide
+    int num_sms;
+};
+bool reduce_supported(int64_t d, int64_t k);
+int reduce_blocks(const ReduceArgs& a);
+cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s, int64_t* launches);
+
+// R_i = sum_c (X[i,c] - mu_c) (Acc type), mu_c = mu[c * mu_stride] (V type).
+cudaError_t rowsum_launch(dm_dtype t, const void* X, int64_t n, int64_t d, int64_t ldx,
+                          const void* mu, int64_t mu_stride, void* R, cudaStream_t s,
+                          int64_t* launches);
+
+// Column means mu (V type, rounded) and s_i = ||x_i - mu||^2 (Acc type).
+struct L2PrepArgs {
+    dm_dtype dtype;
+    const void* X; int64_t n, d, ldx;
+    void* partial;                       // scratch: blocks x d Wide
+    void* mu;                            // d entries, V type
+    void* s;                             // n entries, Acc type
+    uint32_t* err;
+};
+int l2prep_blocks(const L2PrepArgs& a);
+cudaError_t l2prep_launch(const L2PrepArgs& a, cudaStream_t s, int64_t* launches);
+
+// out_i = s_i u + v - 2 (x_i - mu) . W
+struct L2ApplyArgs {
+    dm_dtype dtype;
+    const void* X; int64_t n, d, ldx;
+    const void* mu; const void* s;
+    const void* res;                     // W, u, v as produced by the reduce
+    int64_t k;
+    void* out; int64_t ldo;
+};
+cudaError_t l2apply_launch(const L2ApplyArgs& a, cudaStream_t s, int64_t* launches);
+
+// l1 query: scan + evaluate + cross-coordinate accumulation (Algorithm 2).
+struct L1QueryArgs {
+    dm_dtype dtype;
+    const void* xs; const int32_t* perm; int64_t n, d;   // plan (d x n each)
+    const void* R;                       // plan: R_i = sum_c (x_i(c) - mu_c), Acc type
+    const void* mu;  int64_t mu_stride;  // the shift mu_c (V type)
+    const void* Z; int64_t k, ldz;
+    const void* res;                     // R^T Z (k), then 1^T Z (k): Wide
+    void* out; int64_t ldo;
+    void* scratch;                       // l1_query_scratch_bytes()
+    uint32_t* err;
+    int num_sms;
+};
+size_t l1_query_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k);
+cudaError_t l1_query_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches);
+
+// Plain on-the-fly product (baseline).
+struct BruteArgs {
+    dm_dtype dtype; dm_metric metric;
+    const void* X; int64_t n, d, ldx;
+    const void* Z; int64_t k, ldz;
+    void* out; int64_t ldo;
+};
+cudaError_t brute_launch(const BruteArgs& a, cudaStream_t s, int64_t* launches);
+
+}  // namespace dm

@@ -1,0 +1,377 @@
+// Preprocessing of the l1 product (Algorithm 1, Section 2): sort every
+// coordinate column of X ascending, keeping the sorting permutation.
+//
+// Stable LSD radix sort with 8-bit digits over d independent column segments:
+//   keygen_hist   -- one read of row-major X: order-preserving unsigned keys
+//                    written column-major (d x n) plus the digit histograms of
+//                    every digit position of every column, in one pass.
+//   onesweep_pass -- one digit position: each CTA ranks a tile of keys by the
+//                    digit (warp match + per-warp counters, stable), publishes
+//                    its digit counts and finds the counts of all earlier tiles
+//                    of its column through a decoupled look-back (bounded
+//                    spin), then scatters keys and payload through shared
+//                    memory so that runs of equal digits are written
+//                    contiguously.  The last pass writes the sorted values (in
+//                    the input element type) and the permutation.
+// Ties keep index order (LSD is stable), so the permutation equals a stable
+// argsort of each column.  -0.0 sorts before +0.0 (they differ in key, not in
+// value; either order gives the same product).
+#include "dm_internal.h"
+
+namespace dm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRadix = 256;
+
+// ------------------------------------------------------------ key mapping
+__device__ __forceinline__ uint32_t to_key(float v) {
+    uint32_t u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long to_key(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | (1ull << 63));
+}
+__device__ __forceinline__ uint32_t to_key(int32_t v) { return (uint32_t)v ^ 0x80000000u; }
+
+__device__ __forceinline__ void from_key(uint32_t k, float* v) {
+    *v = __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ __forceinline__ void from_key(unsigned long long k, double* v) {
+    *v = __longlong_as_double((long long)((k >> 63) ? (k & ~(1ull << 63)) : ~k));
+}
+__device__ __forceinline__ void from_key(uint32_t k, int32_t* v) { *v = (int32_t)(k ^ 0x80000000u); }
+
+__device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_val(int32_t) { return true; }
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Exclusive scan of one value per thread over the 256 threads of the CTA.
+// `warp_tot` is kWarps words of shared memory.  Returns the exclusive prefix;
+// *total receives the sum over the CTA.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        uint32_t t = warp_tot[w];
+        if (w < warp) before += t;
+        all += t;
+    }
+    __syncthreads();
+    *total = all;
+    return before + inc - v;
+}
+
+// ------------------------------------------------------------ keygen + hist
+template <dm_dtype DT>
+struct KeygenCfg {
+    using Ty = Types<DT>;
+    using Key = typename Ty::Key;
+    static constexpr int P = (int)sizeof(Key);           // digit positions
+    static constexpr int DB = sizeof(Key) == 4 ? 8 : 4;  // columns per CTA
+    static constexpr int RB = 1024;                      // rows per CTA
+    static constexpr int TS = RB + 8;                    // padded row stride of the tile
+    static constexpr size_t smem = (size_t)DB * P * kRadix * 4 + (size_t)DB * TS * sizeof(Key);
+};
+
+template <dm_dtype DT>
+__global__ void __launch_bounds__(kThreads)
+keygen_hist_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64_t d, int64_t ldx,
+                   typename Types<DT>::Key* __restrict__ keys, uint32_t* __restrict__ hist,
+                   uint32_t* err) {
+    using Cfg = KeygenCfg<DT>;
+    using Key = typename Cfg::Key;
+    using V = typename Types<DT>::V;
+    constexpr int P = Cfg::P, DB = Cfg::DB, RB = Cfg::RB, TS = Cfg::TS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t* h = reinterpret_cast<uint32_t*>(smem_raw);                  // [DB][P][256]
+    Key* tile = reinterpret_cast<Key*>(smem_raw + (size_t)DB * P * kRadix * 4);  // [DB][TS]
+
+    const int64_t row0 = (int64_t)blockIdx.x * RB;
+    const int64_t c0 = (int64_t)blockIdx.y * DB;
+    const int nr = (int)min64(RB, n - row0);
+    const int nd = (int)min64(DB, d - c0);
+    const int lane = threadIdx.x & 31;
+
+    for (int i = threadIdx.x; i < DB * P * kRadix; i += kThreads) h[i] = 0;
+    __syncthreads();
+
+    bool bad = false;
+    const int c = threadIdx.x % DB;
+    for (int r = threadIdx.x / DB; r < RB; r += kThreads / DB) {
+        const bool ok = (r < nr) && (c < nd);
+        Key key = 0;
+        if (ok) {
+            V v = X[(row0 + r) * ldx + c0 + c];
+            bad |= !finite_val(v);
+            key = to_key(v);
+            tile[c * TS + r] = key;
+        }
+        // Warp-aggregated histogram updates: lanes with the same (column,
+        // digit) pair add once.
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const uint32_t digit = (uint32_t)(key >> (8 * p)) & 0xffu;
+            const uint32_t tag = ok ? (uint32_t)(c * kRadix + digit) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+            if (ok && lane == __ffs(peers) - 1)
+                atomicAdd(&h[(c * P + p) * kRadix + digit], (uint32_t)__popc(peers));
+        }
+    }
+    if (bad) set_error(err, kErrNonfinite);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd * RB; i += kThreads) {
+        const int cc = i / RB, r = i % RB;
+        if (r < nr) keys[(c0 + cc) * n + row0 + r] = tile[cc * TS + r];
+    }
+    for (int i = threadIdx.x; i < nd * P * kRadix; i += kThreads) {
+        const uint32_t v = h[i];
+        if (v) atomicAdd(&hist[c0 * P * kRadix + i], v);
+    }
+}
+
+// ------------------------------------------------------------ onesweep pass
+template <dm_dtype DT>
+struct PassCfg {
+    using Key = typename Types<DT>::Key;
+    static constexpr int ITEMS = sizeof(Key) == 4 ? 16 : 8;   // keys per thread
+    static constexpr int TILE = kThreads * ITEMS;
+};
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+template <dm_dtype DT>
+__global__ void __launch_bounds__(kThreads)
+onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
+                const int32_t* __restrict__ vals_in,            // null on the first pass
+                typename Types<DT>::Key* __restrict__ keys_out,
+                int32_t* __restrict__ vals_out,
+                typename Types<DT>::V* __restrict__ sorted_out,  // last pass only
+                int32_t* __restrict__ perm_out,                   // last pass only
+                const uint32_t* __restrict__ hist, uint32_t* lookback, uint32_t* counter,
+                int64_t n, int pass, int P, int T, int first, int last, uint32_t* err) {
+    using Key = typename Types<DT>::Key;
+    using V = typename Types<DT>::V;
+    constexpr int ITEMS = PassCfg<DT>::ITEMS, TILE = PassCfg<DT>::TILE;
+
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t wcount[kWarps][kRadix];
+    __shared__ uint32_t tile_start[kRadix];
+    __shared__ uint32_t gbase[kRadix];
+    __shared__ uint32_t warp_tot[kWarps];
+    __shared__ __align__(16) Key sk[TILE];
+    __shared__ int32_t sv[TILE];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&wcount[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t g = s_tile;
+    const int64_t c = g / (uint32_t)T;
+    const int t = (int)(g % (uint32_t)T);
+    const int64_t seg = c * n;
+    const int64_t tile0 = (int64_t)t * TILE;
+    const int shift = 8 * pass;
+
+    // Segment-level start of every digit from the upfront histogram.
+    uint32_t seg_total;
+    const uint32_t digit_start =
+        block_exclusive_scan(hist[(c * P + pass) * kRadix + tid], warp_tot, &seg_total);
+
+    // Load a warp-striped tile: item j of lane l sits at tile position
+    // warp*32*ITEMS + j*32 + l, so ranking items in (j, lane) order is the
+    // original order.  Positions past n get digit 255 and land after every
+    // real key of the tile; their global positions are >= n and are dropped.
+    Key key[ITEMS];
+    int32_t val[ITEMS];
+    uint32_t rank[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int64_t gi = tile0 + warp * 32 * ITEMS + j * 32 + lane;
+        if (gi < n) {
+            key[j] = keys_in[seg + gi];
+            val[j] = first ? (int32_t)gi : vals_in[seg + gi];
+        } else {
+            key[j] = ~(Key)0;
+            val[j] = -1;
+        }
+    }
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t dg = (uint32_t)(key[j] >> shift) & 0xffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t prior = wcount[warp][dg];
+        rank[j] = prior + __popc(peers & lt_mask);
+        __syncwarp();
+        if ((peers & lt_mask) == 0) wcount[warp][dg] = prior + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Per digit: exclusive offsets of the warps, and the tile's count.
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t x = wcount[w][tid];
+        wcount[w][tid] = cnt;
+        cnt += x;
+    }
+
+    // Decoupled look-back over the earlier tiles of this column.
+    uint32_t* lb = lookback + (int64_t)c * T * kRadix;
+    uint32_t excl = 0;
+    if (t == 0) {
+        st_relaxed(&lb[tid], kFlagInc | cnt);
+    } else {
+        st_relaxed(&lb[(int64_t)t * kRadix + tid], kFlagAgg | cnt);
+        int pred = t - 1;
+        uint32_t spins = 0;
+        while (true) {
+            const uint32_t s = ld_relaxed(&lb[(int64_t)pred * kRadix + tid]);
+            if ((s & ~kValMask) == 0) {
+                if (++spins > kSpinLimit) { set_error(err, kErrTimeout); break; }
+                __nanosleep(64);
+                continue;
+            }
+            excl += s & kValMask;
+            if ((s & ~kValMask) == kFlagInc || pred == 0) break;
+            --pred;
+        }
+        st_relaxed(&lb[(int64_t)t * kRadix + tid], kFlagInc | (excl + cnt));
+    }
+
+    uint32_t tile_total;
+    const uint32_t ts = block_exclusive_scan(cnt, warp_tot, &tile_total);
+    tile_start[tid] = ts;
+    gbase[tid] = digit_start + excl - ts;   // global = gbase[digit] + tile position
+    __syncthreads();
+
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t dg = (uint32_t)(key[j] >> shift) & 0xffu;
+        const uint32_t pos = tile_start[dg] + wcount[warp][dg] + rank[j];
+        sk[pos] = key[j];
+        sv[pos] = val[j];
+    }
+    __syncthreads();
+
+#pragma unroll 4
+    for (int pos = tid; pos < TILE; pos += kThreads) {
+        const Key k = sk[pos];
+        const uint32_t dg = (uint32_t)(k >> shift) & 0xffu;
+        const uint32_t gp = gbase[dg] + (uint32_t)pos;
+        if ((int64_t)gp < n) {
+            if (last) {
+                V v;
+                from_key(k, &v);
+                sorted_out[seg + gp] = v;
+                perm_out[seg + gp] = sv[pos];
+            } else {
+                keys_out[seg + gp] = k;
+                vals_out[seg + gp] = sv[pos];
+            }
+        }
+    }
+}
+
+template <dm_dtype DT>
+cudaError_t launch_keygen_t(const SortArgs& a, cudaStream_t s) {
+    using Cfg = KeygenCfg<DT>;
+    auto kern = keygen_hist_kernel<DT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((a.n + Cfg::RB - 1) / Cfg::RB), (unsigned)((a.d + Cfg::DB - 1) / Cfg::DB));
+    kern<<<grid, kThreads, Cfg::smem, s>>>(
+        static_cast<const typename Types<DT>::V*>(a.X), a.n, a.d, a.ldx,
+        static_cast<typename Types<DT>::Key*>(a.keys_a), a.hist, a.err);
+    return cudaGetLastError();
+}
+
+template <dm_dtype DT>
+cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, cudaStream_t s,
+                            int64_t* launches) {
+    using Key = typename Types<DT>::Key;
+    using V = typename Types<DT>::V;
+    constexpr int TILE = PassCfg<DT>::TILE;
+    const int T = (int)((a.n + TILE - 1) / TILE);
+    const int P = (int)sizeof(Key);
+    const Key* kin = static_cast<const Key*>(a.keys_a);
+    const int32_t* vin = nullptr;
+    Key* kbuf[2] = {static_cast<Key*>(a.keys_b), static_cast<Key*>(a.keys_a)};
+    int32_t* vbuf[2] = {a.vals_b, a.vals_a};
+    const size_t lb_stride = (size_t)a.d * T * kRadix;
+    for (int i = 0; i < npass; ++i) {
+        const int first = i == 0, last = i == npass - 1;
+        Key* kout = kbuf[i & 1];
+        int32_t* vout = vbuf[i & 1];
+        onesweep_kernel<DT><<<(unsigned)(a.d * T), kThreads, 0, s>>>(
+            kin, vin, kout, vout, static_cast<V*>(a.sorted_out), a.perm_out, a.hist,
+            a.lookback + i * lb_stride, a.counters + i, a.n, pass_list[i], P, T, first, last,
+            a.err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        ++*launches;
+        kin = kout;
+        vin = vout;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int sort_passes(dm_dtype t) { return key_bits(t) / 8; }
+
+size_t sort_hist_words(dm_dtype t, int64_t d) { return (size_t)d * sort_passes(t) * kRadix; }
+
+size_t sort_lookback_words(dm_dtype t, int64_t n, int64_t d) {
+    const int tile = (t == DM_F64) ? PassCfg<DM_F64>::TILE : PassCfg<DM_F32>::TILE;
+    const int64_t T = (n + tile - 1) / tile;
+    return (size_t)sort_passes(t) * d * T * kRadix;
+}
+
+cudaError_t sort_launch_keygen(const SortArgs& a, cudaStream_t s, int64_t* launches) {
+    cudaError_t e;
+    switch (a.dtype) {
+        case DM_F32: e = launch_keygen_t<DM_F32>(a, s); break;
+        case DM_F64: e = launch_keygen_t<DM_F64>(a, s); break;
+        default: e = launch_keygen_t<DM_I32>(a, s); break;
+    }
+    if (e == cudaSuccess) ++*launches;
+    return e;
+}
+
+cudaError_t sort_launch_passes(const SortArgs& a, const int* pass_list, int npass, cudaStream_t s,
+                               int64_t* launches) {
+    switch (a.dtype) {
+        case DM_F32: return launch_passes_t<DM_F32>(a, pass_list, npass, s, launches);
+        case DM_F64: return launch_passes_t<DM_F64>(a, pass_list, npass, s, launches);
+        default: return launch_passes_t<DM_I32>(a, pass_list, npass, s, launches);
+    }
+}
+
+}  // namespace dm

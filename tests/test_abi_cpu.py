@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, and exports every entry point declared in include/dm.h; status
+strings and argument checks work without touching a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "dm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(dm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2210_15114_gb300 import build, binding
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dm_create", "dm_destroy", "dm_prepare", "dm_plan_destroy", "dm_matvec_l1",
+                     "dm_matvec_l2sq", "dm_matmat", "dm_sync", "dm_status_string",
+                     "dm_bruteforce", "dm_matmat_host", "dm_plan_export"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2210_15114_gb300 import binding
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.lib_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(dm_\w+)$", out, flags=re.M))
+    for name in declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_build_flags_target_sm103a():
+    from paper_2210_15114_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings(lib):
+    from paper_2210_15114_gb300 import binding
+    assert binding.dm_status_string(0) == "DM_OK"
+    assert binding.dm_status_string(6) == "DM_ERR_TIMEOUT"
+    assert binding.dm_status_string(99) == "DM_ERR_UNKNOWN"
+
+
+def test_argument_checks_without_device(lib):
+    P = ctypes.c_void_p
+    h = P()
+    assert lib.dm_create(None, 0, None) == 1                     # null out pointer
+    assert lib.dm_prepare(None, 0, 0, None, 1, 1, 1, ctypes.byref(h)) == 1
+    assert lib.dm_matmat(None, None, 1, 1, None, 1) == 1
+    assert lib.dm_sync(None) == 1
+    assert lib.dm_matvec_l1(None, None, None) == 1
+    assert lib.dm_bruteforce(None, 0, 0, None, 1, 1, 1, None, 1, 1, None, 1) == 1
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.dm_create(ctypes.byref(h), 0, None) in (1, 5)
+    assert not h.value
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    from paper_2210_15114_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(binding.DMError):
+        binding.load()

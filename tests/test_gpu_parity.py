@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (Frobenius relative error over the whole block, against the FP64
+oracle evaluated on the same input values): 1e-12 for FP64 inputs, 1e-5 for
+FP32 inputs; int32 inputs are bit-exact (int64 results).  Small cases are
+compared element by element on every output; the full-size workloads
+(n = 2^20, d = 32, k = 16) on a seeded sample of output rows computed one by
+one by the oracle's definition, plus the symmetry w^T (A z) = z^T (A w).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_15114_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = {np.float32: 1e-5, np.float64: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def dm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_15114_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(dm):
+    return dm.dm_create(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_product(dm, ctx, metric, X, Z):
+    plan = dm.dm_prepare(ctx, metric, dev(X))
+    out = dm.dm_matmat(plan, dev(Z))
+    dm.dm_sync(ctx)
+    return out.cpu().numpy()
+
+
+def reference(metric, X, Z):
+    return oracle.l1_sort(X, Z) if metric == "l1" else oracle.l2sq_identity(X, Z)
+
+
+def check(got, want, dtype):
+    if np.issubdtype(np.dtype(dtype), np.integer):
+        np.testing.assert_array_equal(got, want)
+    else:
+        err = oracle.relative_error(got, want)
+        assert err <= TOL[dtype], f"relative error {err:.3e}"
+
+
+# ------------------------------------------------------------ small configs
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_small_fp64_workload(dm, ctx, metric):
+    # n = 4096, d = 8, U[0,1) FP64, one N(0,1) query, every row vs the definition.
+    X, z = inputs.workload_small_f64()
+    plan = dm.dm_prepare(ctx, metric, dev(X))
+    fn = dm.dm_matvec_l1 if metric == "l1" else dm.dm_matvec_l2sq
+    out = fn(plan, dev(z[:, 0]))
+    dm.dm_sync(ctx)
+    want = (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(X, z[:, 0])
+    assert oracle.relative_error(out.cpu().numpy(), want) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, np.int32])
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_grid_closed_form(dm, ctx, metric, dtype):
+    n = 4096
+    X = inputs.grid_1d(n).astype(dtype)
+    z = np.ones(n, dtype=dtype)
+    i = np.arange(n, dtype=np.int64)
+    if metric == "l1":
+        want = i * (i + 1) // 2 + (n - 1 - i) * (n - i) // 2
+    else:
+        want = i * (i + 1) * (2 * i + 1) // 6 + (n - 1 - i) * (n - i) * (2 * n - 2 * i - 1) // 6
+    out = gpu_product(dm, ctx, metric, X, z.reshape(n, 1))[:, 0]
+    if dtype == np.float32:
+        assert oracle.relative_error(out, want) <= 1e-5
+    else:
+        np.testing.assert_array_equal(out, want.astype(out.dtype))
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+@pytest.mark.parametrize("n", [1, 2, 3, 767, 768, 769, 1537, 4095, 4097, 20011])
+def test_fp32_mixture_sizes(dm, ctx, metric, n):
+    X, Z = inputs.workload_mixture_f32(n=n, d=32, k=16)
+    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.float32)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 16, 17, 40])
+def test_query_block_widths(dm, ctx, metric, k):
+    X, Z = inputs.workload_mixture_f32(n=5000, d=7, k=k)
+    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.float32)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+@pytest.mark.parametrize("dtype", [np.float64, np.int32])
+@pytest.mark.parametrize("k", [1, 3, 16, 20])
+def test_other_types(dm, ctx, metric, dtype, k):
+    n, d = 6007, 5
+    if dtype == np.int32:
+        X = inputs.integer_points(n, d, 3, 0, 1 << 16)
+        Z = inputs.integer_queries(n, k, 4)
+    else:
+        X = inputs.uniform_points(n, d, 3, dtype=np.float64)
+        Z = inputs.gaussian_queries(n, k, 4, dtype=np.float64)
+    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), dtype)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_integer_ties_exact(dm, ctx, metric):
+    rng = np.random.default_rng(21)
+    X = rng.integers(0, 6, size=(9000, 4)).astype(np.int32)
+    Z = rng.integers(-100, 101, size=(9000, 3)).astype(np.int32)
+    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.int32)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_fp32_ties_signed_zeros_negatives(dm, ctx, metric):
+    rng = np.random.default_rng(22)
+    X = rng.normal(size=(7000, 6)).astype(np.float32)
+    X[::3, 0] = 0.0
+    X[1::3, 0] = -0.0
+    X[:, 1] = np.round(X[:, 1] * 4) / 4
+    X[:, 2] = -np.abs(X[:, 2])
+    Z = rng.normal(size=(7000, 4)).astype(np.float32)
+    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.float32)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_fp32_offset_coordinates(dm, ctx, metric):
+    # Large common offset: the product is translation invariant; the kernels
+    # work in shifted frames.
+    X = (1000.0 + inputs.uniform_points(8000, 6, 5)).astype(np.float32)
+    Z = inputs.gaussian_queries(8000, 3, 6)
+    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.float32)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_identical_points_give_zero(dm, ctx, metric):
+    X = np.full((3000, 5), 2.5, dtype=np.float32)
+    Z = inputs.gaussian_queries(3000, 4, 2)
+    out = gpu_product(dm, ctx, metric, X, Z)
+    assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_leading_dimensions(dm, ctx, metric):
+    n, d, k = 4000, 6, 5
+    Xb = inputs.gaussian_mixture(n, d + 3, 4, 9)
+    Zb = inputs.gaussian_queries(n, k + 2, 10)
+    X, Z = Xb[:, :d], Zb[:, :k]
+    Xd = dev(Xb)[:, :d]
+    Zd = dev(Zb)[:, :k]
+    outb = torch.full((n, k + 4), 7.0, device="cuda")
+    plan = dm.dm_prepare(ctx, metric, Xd)
+    dm.dm_matmat(plan, Zd, out=outb[:, :k])
+    dm.dm_sync(ctx)
+    got = outb.cpu().numpy()
+    check(got[:, :k], reference(metric, X, Z), np.float32)
+    assert np.all(got[:, k:] == 7.0)
+
+
+def test_sort_matches_stable_argsort(dm, ctx):
+    for n, dtype in [(1, np.float32), (2, np.float32), (4095, np.float32), (4096, np.float32),
+                     (4097, np.float32), (30001, np.float32), (3000, np.float64),
+                     (5000, np.int32)]:
+        if dtype == np.int32:
+            X = inputs.integer_points(n, 5, 1, -50, 50)
+        else:
+            X = inputs.gaussian_mixture(n, 5, 3, 1).astype(dtype)
+            X[::4, 3] = X[0, 3]                        # ties
+        plan = dm.dm_prepare(ctx, "l1", dev(X))
+        vals, perm = dm.dm_plan_export(plan)
+        dm.dm_sync(ctx)
+        vals, perm = vals.cpu().numpy(), perm.cpu().numpy()
+        for c in range(X.shape[1]):
+            order = oracle.preprocessing_order(X[:, c])
+            np.testing.assert_array_equal(perm[c], order)
+            np.testing.assert_array_equal(vals[c], X[order, c])
+
+
+def test_sort_signed_zeros_valid(dm, ctx):
+    X = np.zeros((5000, 1), dtype=np.float32)
+    X[::2, 0] = -0.0
+    X[::7, 0] = 1.5
+    X[::11, 0] = -2.0
+    plan = dm.dm_prepare(ctx, "l1", dev(X))
+    vals, perm = dm.dm_plan_export(plan)
+    dm.dm_sync(ctx)
+    vals, perm = vals.cpu().numpy()[0], perm.cpu().numpy()[0]
+    assert np.all(np.diff(vals) >= 0)
+    assert np.array_equal(np.sort(perm), np.arange(5000))
+    np.testing.assert_array_equal(vals, X[perm, 0])
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_deterministic(dm, ctx, metric):
+    X, Z = inputs.workload_mixture_f32(n=50000, d=12, k=16)
+    a = gpu_product(dm, ctx, metric, X, Z)
+    b = gpu_product(dm, ctx, metric, X, Z)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_matvec_entry_points_reject_wrong_metric(dm, ctx):
+    X = inputs.uniform_points(100, 2, 1, dtype=np.float32)
+    z = dev(np.ones(100, dtype=np.float32))
+    p1 = dm.dm_prepare(ctx, "l1", dev(X))
+    p2 = dm.dm_prepare(ctx, "l2sq", dev(X))
+    with pytest.raises(dm.DMError):
+        dm.dm_matvec_l2sq(p1, z)
+    with pytest.raises(dm.DMError):
+        dm.dm_matvec_l1(p2, z)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_nonfinite_rejected(dm, ctx, metric):
+    X = inputs.uniform_points(1000, 3, 1, dtype=np.float32)
+    X[17, 1] = np.nan
+    with pytest.raises(dm.DMError) as e:
+        dm.dm_prepare(ctx, metric, dev(X))
+    assert e.value.status == dm.DM_ERR_NONFINITE
+    X[17, 1] = np.inf
+    with pytest.raises(dm.DMError):
+        dm.dm_prepare(ctx, metric, dev(X))
+    # the context stays usable
+    X[17, 1] = 0.5
+    Z = inputs.gaussian_queries(1000, 2, 1)
+    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.float32)
+
+
+def test_invalid_arguments(dm, ctx):
+    X = dev(inputs.uniform_points(100, 2, 1, dtype=np.float32))
+    with pytest.raises(dm.DMError) as e:
+        dm.dm_prepare(ctx, "l1", X[:0])
+    assert e.value.status == dm.DM_ERR_INVALID_ARG
+    plan = dm.dm_prepare(ctx, "l1", X)
+    with pytest.raises(dm.DMError):
+        dm.dm_matmat(plan, dev(np.ones((100, 2), dtype=np.float64)))
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int32])
+def test_bruteforce_kernel(dm, ctx, metric, dtype):
+    n, d, k = 3001, 9, 17
+    if dtype == np.int32:
+        X = inputs.integer_points(n, d, 2, 0, 1000)
+        Z = inputs.integer_queries(n, k, 3)
+    else:
+        X = inputs.gaussian_mixture(n, d, 4, 2).astype(dtype)
+        Z = inputs.gaussian_queries(n, k, 3).astype(dtype)
+    out = dm.dm_bruteforce(ctx, metric, dev(X), dev(Z))
+    dm.dm_sync(ctx)
+    want = (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(X, Z)
+    check(out.cpu().numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_host_entry_point(dm, ctx, metric):
+    X, Z = inputs.workload_mixture_f32(n=12000, d=10, k=6)
+    got = dm.dm_matmat_host(ctx, metric, X, Z)
+    check(got, reference(metric, X, Z), np.float32)
+
+
+# ----------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def full_fp32():
+    return inputs.workload_mixture_f32()
+
+
+@pytest.fixture(scope="module")
+def full_int():
+    return inputs.workload_integer()
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_full_size_fp32_sampled_rows(dm, ctx, metric, full_fp32):
+    X, Z = full_fp32
+    out = gpu_product(dm, ctx, metric, X, Z)
+    rows = inputs.sample_rows(len(X), 24)
+    want = (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(X, Z, rows)
+    assert oracle.relative_error(out[rows], want) <= 1e-5
+    assert np.all(np.isfinite(out))
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_full_size_int_sampled_rows_exact(dm, ctx, metric, full_int):
+    X, Z = full_int
+    out = gpu_product(dm, ctx, metric, X, Z)
+    rows = inputs.sample_rows(len(X), 12)
+    want = (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(X, Z, rows)
+    np.testing.assert_array_equal(out[rows], want)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_full_size_symmetry(dm, ctx, metric, full_fp32):
+    # w^T (A z) = z^T (A w) for the symmetric A, at full size.
+    X, Z = full_fp32
+    plan = dm.dm_prepare(ctx, metric, dev(X))
+    Zd = dev(Z)
+    out = dm.dm_matmat(plan, Zd).double()
+    dm.dm_sync(ctx)
+    G = Zd.double().T @ out                       # G[a,b] = z_a^T A z_b
+    asym = (G - G.T).abs().max().item()
+    assert asym <= 1e-5 * G.abs().max().item()
