@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the implicit distance-matrix product on GB300.
+
+Workload: n = 2^20 points in d = 32 dimensions from a 16-cluster Gaussian
+mixture (cluster means N(0, 10^2) per coordinate, within-cluster sd 1), FP32,
+and a block of k = 16 FP32 N(0, 1) query columns -- synthetic stand-ins of the
+shape of the paper's Gaussian-mixture experiment (Section 4), scaled up.
+
+One step = the whole hot path on that input, inputs already resident in HBM:
+  l1:   dm_prepare (radix sort of the 32 columns, Algorithm 1)
+        + dm_matmat (prefix-scan query of Algorithm 2, k = 16 columns);
+  l2sq: dm_prepare (column means, squared norms)
+        + dm_matmat (rank-(d+2) identity of Appendix A).
+Metric: point*query*dim per second, counting n*k*d units for each of the two
+products (2 n k d per step).  Between timed steps the L2 cache is flushed
+(a 512 MiB write); the flush is outside the per-step CUDA-event spans.
+
+Also reported: the per-part breakdown, the on-the-fly GPU brute force (the
+plain method) and speedups against it, the relative error of sampled output
+rows against the CPU oracle, the roofline of the dominant kernel (live CUDA
+events inside the library), an end-to-end number through the C ABI with host
+buffers, SM clocks sampled during the timed region, and the CPU oracle timed
+on a bounded sample of the workload.
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+Under torchrun (N > 1) every rank runs an independent replica (the product is
+not sharded; no collective is on the data path): value = all ranks' units / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point*query*dim/s (l1 + l2sq products, prepare included)"
+UNIT = "point*query*dim/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--d", type=int, default=32)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--no-brute", action="store_true", help="skip the brute-force comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warmup + steps only (for profiler captures); print nothing else")
+    return ap.parse_args()
+
+
+def workload_config(a, flush):
+    return {"workload": f"gaussian-mixture-16 n={a.n} d={a.d} k={a.k} fp32",
+            "n": a.n, "d": a.d, "k": a.k, "clusters": 16, "dtype": "fp32",
+            "products": ["l1", "l2sq"], "prepare_in_step": True, "l2_flush": flush}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="dm_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU oracle
+_WORKLOAD_CACHE = {}
+
+
+def cpu_oracle_sample(n, d, d_sample, k):
+    """Time the CPU oracle (sort-based l1 form and p = 2 identity) on the first
+    d_sample coordinates of the workload, in this process.  Returns seconds."""
+    import oracle
+    from paper_2210_15114_gb300 import inputs
+    key = (n, d, k)
+    if key not in _WORKLOAD_CACHE:
+        _WORKLOAD_CACHE.clear()
+        _WORKLOAD_CACHE[key] = inputs.workload_mixture_f32(n=n, d=d, k=k)
+    X, Z = _WORKLOAD_CACHE[key]
+    Xs = X[:, :d_sample]
+    t0 = time.perf_counter()
+    oracle.l1_sort(Xs, Z)
+    oracle.l2sq_identity(Xs, Z)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n, d, k, d_sample):
+    """The oracle as it stands, single-threaded, in a spawned subprocess."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_oracle_sample(%d, %d, %d, %d)))" % (ROOT, n, d, d_sample, k))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "error": r.stderr[-300:]}
+    secs = float(r.stdout.strip().splitlines()[-1])
+    units = 2 * n * d_sample * k
+    return {"value": units / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds": secs,
+            "sample": f"first {d_sample} of the coordinates at full n={n}, k={k}: numpy "
+                      f"sort-based l1 form (Algorithms 1-2) + p=2 identity, FP64, one thread"}
+
+
+# ------------------------------------------------------------- algorithmic bytes
+def algorithmic_bytes(group, n, d, k, launches):
+    """Bytes the method itself moves per launch of a kernel group (FP32)."""
+    nd = n * d
+    if group == "l1_query":     # key 4 + perm 4 + gathered Z row 4k + contribution 4k, + out 4k
+        return nd * (8 + 8 * k) + 4 * n * k
+    if group == "sort_onesweep":  # read key(+val) 8, write key+val 8 (first pass reads 4)
+        return (16 * nd * launches - 4 * nd) / launches
+    if group == "sort_keygen_hist":
+        return 8 * nd
+    if group == "l2_reduce":
+        return 4 * nd + 4 * n * k + 4 * n
+    if group == "l2_apply":
+        return 4 * nd + 4 * n + 4 * n * k
+    if group == "l1_totals":
+        return 4 * n + 4 * n * k
+    if group == "l1_rowsum":
+        return 4 * nd + 4 * d + 4 * n
+    if group == "l2_prepare":
+        return (2 * 4 * nd + 4 * n) / max(launches, 1)
+    return None
+
+
+def traffic_record(group):
+    """ncu DRAM bytes per launch for a kernel group, if recorded for the
+    current source of the kernel (profiles/traffic.json)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(group)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != rec["source_sha"]:
+            return None
+    return rec["bytes_per_launch"]
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"   # before numpy is imported: the oracle runs on one core
+    d_sample = 1
+    units = 2 * a.n * d_sample * a.k
+    for _ in range(a.warmup):
+        cpu_oracle_sample(a.n, a.d, d_sample, a.k)
+    times = [cpu_oracle_sample(a.n, a.d, d_sample, a.k) for _ in range(a.steps)]
+    ms = 1e3 * statistics.mean(times)
+    value = units / (ms / 1e3)
+    cores = 1
+    sample = (f"first {d_sample} of {a.d} coordinates at full n={a.n}, k={a.k} per step: numpy "
+              f"sort-based l1 form + p=2 identity, FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(a, "none (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- our arm
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2210_15114_gb300 import binding as dm
+    from paper_2210_15114_gb300 import build, inputs
+    build.build()
+    dm.load()
+
+    X, Z = inputs.workload_mixture_f32(n=a.n, d=a.d, k=a.k)
+    Xd = torch.from_numpy(X).to(dev)
+    Zd = torch.from_numpy(Z).to(dev)
+    o1 = torch.empty((a.n, a.k), dtype=torch.float32, device=dev)
+    o2 = torch.empty_like(o1)
+    flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)   # 512 MiB > L2
+    stream = torch.cuda.current_stream(dev)
+    ctx = dm.dm_create(local, stream.cuda_stream)
+
+    def step():
+        p1 = dm.dm_prepare(ctx, "l1", Xd)
+        dm.dm_matmat(p1, Zd, out=o1)
+        p2 = dm.dm_prepare(ctx, "l2sq", Xd)
+        dm.dm_matmat(p2, Zd, out=o2)
+        return p1, p2
+
+    for _ in range(a.warmup):
+        plans = step()
+        del plans
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- timed region
+    clocks = ClockSampler(local) if not a.profile_only else None
+    dm.dm_profile_enable(ctx, True)
+    launches0 = dm.dm_launch_count(ctx)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for i in range(a.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        plans = step()
+        ends[i].record(stream)
+        del plans
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = dm.dm_launch_count(ctx) - launches0
+    prof = dm.dm_profile_read(ctx)
+    dm.dm_profile_enable(ctx, False)
+    clk = clocks.stop() if clocks else None
+    dm.dm_sync(ctx)
+    if a.profile_only:
+        return
+
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units_step = 2 * a.n * a.d * a.k
+    value = world * units_step / (ms / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- parts, per-kernel groups, roofline
+    per_step = {g: t / a.steps for g, (l, t) in prof.items()}
+    parts = {
+        "l1_prepare_ms": sum(per_step.get(g, 0) for g in ("sort_keygen_hist", "sort_onesweep",
+                                                          "l1_rowsum")),
+        "l1_query_ms": sum(per_step.get(g, 0) for g in ("l1_totals", "l1_query")),
+        "l2_prepare_ms": per_step.get("l2_prepare", 0.0),
+        "l2_query_ms": sum(per_step.get(g, 0) for g in ("l2_reduce", "l2_apply")),
+    }
+    peak, peak_kind = load_peaks()
+    kernels = {}
+    for g, (l, t) in prof.items():
+        nl = l // a.steps if l else 0
+        per_launch_ms = t / l if l else None
+        b = algorithmic_bytes(g, a.n, a.d, a.k, max(nl, 1))
+        if b is not None and per_launch_ms:
+            kernels[g] = {"launches_per_step": nl, "ms_per_launch": per_launch_ms,
+                          "alg_bytes_per_launch": b,
+                          "alg_gbs": b / (per_launch_ms * 1e-3) / 1e9}
+    dominant = max(kernels, key=lambda g: kernels[g]["ms_per_launch"] * kernels[g]["launches_per_step"])
+    dk = kernels[dominant]
+    roofline = {"kernel": dominant, "bound": "hbm", "achieved": dk["alg_gbs"], "peak": peak,
+                "unit": "GB/s", "frac": dk["alg_gbs"] / peak,
+                "peak_kind": peak_kind + " HBM copy bandwidth",
+                "traffic": traffic_record(dominant)}
+
+    # ---- brute force (the plain method) and accuracy
+    brute = None
+    if not a.no_brute:
+        brute = {}
+        for metric in ("l1", "l2sq"):
+            ob = torch.empty_like(o1)
+            dm.dm_bruteforce(ctx, metric, Xd, Zd, out=ob)       # warm
+            torch.cuda.synchronize(dev)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            dm.dm_bruteforce(ctx, metric, Xd, Zd, out=ob)
+            e.record(stream)
+            dm.dm_sync(ctx)
+            bms = s.elapsed_time(e)
+            qms = parts["l1_query_ms"] if metric == "l1" else parts["l2_query_ms"]
+            pms = parts["l1_prepare_ms"] if metric == "l1" else parts["l2_prepare_ms"]
+            brute[metric] = {"ms": bms, "speedup_query": bms / qms, "speedup_prepare_query": bms / (qms + pms)}
+            del ob
+    import oracle
+    rows = inputs.sample_rows(a.n, 16)
+    err = {}
+    got1, got2 = o1.cpu().numpy(), o2.cpu().numpy()
+    err["l1"] = oracle.relative_error(got1[rows], oracle.l1_rows(X, Z, rows))
+    err["l2sq"] = oracle.relative_error(got2[rows], oracle.l2sq_rows(X, Z, rows))
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not a.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory().numpy()
+        Zh = torch.from_numpy(Z).pin_memory().numpy()
+        out_h = torch.empty((a.n, a.k), dtype=torch.float32).pin_memory().numpy()
+        for _ in range(2):
+            dm.dm_matmat_host(ctx, "l1", Xh, Zh, out_h)
+            dm.dm_matmat_host(ctx, "l2sq", Xh, Zh, out_h)
+        e_ms = []
+        for _ in range(max(3, a.steps // 2)):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            dm.dm_matmat_host(ctx, "l1", Xh, Zh, out_h)
+            dm.dm_matmat_host(ctx, "l2sq", Xh, Zh, out_h)
+            e.record(stream)
+            e.synchronize()
+            e_ms.append(s.elapsed_time(e))
+        em = statistics.mean(e_ms)
+        e2e = {"value": units_step / (em / 1e3), "unit": UNIT, "ms_per_step": em,
+               "h2d_bytes_per_step": 2 * (X.nbytes + Z.nbytes),
+               "d2h_bytes_per_step": 2 * out_h.nbytes}
+
+    cpu = None
+    if not a.no_cpu and world == 1:
+        cpu = cpu_baseline(a.n, a.d, a.k, 4)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(a, "512 MiB write between timed steps (outside the step events)"),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "gpu_launches": launches, "launches_per_step": launches / a.steps,
+            "wall_s_timed_region": t_wall,
+            "parts_ms": parts, "kernels": kernels, "roofline": roofline,
+            "bruteforce": brute, "rel_err_sampled_rows": err,
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -137,6 +137,20 @@ dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
 /* Number of kernels this context has launched so far (all calls). */
 int64_t dm_launch_count(const dm_ctx* ctx);
 
+/* Kernel timing.  While enabled, every group of launches a call makes
+ * ("sort_keygen_hist", "sort_onesweep", "l1_rowsum", "l1_totals", "l1_query",
+ * "l2_prepare", "l2_reduce", "l2_apply", "bruteforce") is bracketed by two CUDA events
+ * recorded on the context's stream.  Enabling (or disabling) clears what was
+ * collected.  Off by default; costs two event records per group. */
+dm_status dm_profile_enable(dm_ctx* ctx, int enable);
+
+/* Resolve the recorded events (synchronizes the stream) and report, for up to
+ * `max` groups, the name (NUL-terminated, 32 bytes per slot of `names`), the
+ * number of kernel launches and their total device time in milliseconds.
+ * *count receives the number of groups filled in. */
+dm_status dm_profile_read(dm_ctx* ctx, int max, int* count, char* names,
+                          int64_t* launches, double* total_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,8 @@ def load() -> ctypes.CDLL:
             "dm_bruteforce": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
             "dm_matmat_host": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
             "dm_launch_count": ([P], I64),
+            "dm_profile_enable": ([P, I32], I32),
+            "dm_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int), P, P, P], I32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -296,3 +298,24 @@ def dm_matmat_host(ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out: np.n
 
 def dm_launch_count(ctx: Context) -> int:
     return int(load().dm_launch_count(ctx.handle))
+
+
+def dm_profile_enable(ctx: Context, enable: bool = True) -> None:
+    _check(load().dm_profile_enable(ctx.handle, 1 if enable else 0), "dm_profile_enable")
+
+
+def dm_profile_read(ctx: Context, max_groups: int = 32) -> dict:
+    """{group name: (launches, total device ms)} collected since enabling."""
+    names = ctypes.create_string_buffer(32 * max_groups)
+    launches = (ctypes.c_int64 * max_groups)()
+    total = (ctypes.c_double * max_groups)()
+    count = ctypes.c_int()
+    _check(load().dm_profile_read(ctx.handle, max_groups, ctypes.byref(count),
+                                  ctypes.cast(names, ctypes.c_void_p),
+                                  ctypes.cast(launches, ctypes.c_void_p),
+                                  ctypes.cast(total, ctypes.c_void_p)), "dm_profile_read")
+    out = {}
+    for i in range(count.value):
+        name = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (int(launches[i]), float(total[i]))
+    return out

@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "dm_internal.h"
@@ -24,6 +26,13 @@ struct dm_ctx {
     void* hx = nullptr; size_t hx_bytes = 0;
     void* hz = nullptr; size_t hz_bytes = 0;
     void* ho = nullptr; size_t ho_bytes = 0;
+    // Kernel timing (dm_profile_enable / dm_profile_read).
+    struct Pending { std::string name; cudaEvent_t start, stop; int64_t launches; };
+    struct Stat { int64_t launches = 0; double ms = 0; };
+    bool profiling = false;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, Stat> stats;
 };
 
 struct dm_plan {
@@ -82,6 +91,57 @@ bool valid_dtype(dm_dtype t) { return t == DM_F32 || t == DM_F64 || t == DM_I32;
 bool valid_metric(dm_metric m) { return m == DM_L1 || m == DM_L2SQ; }
 
 size_t acc_size(dm_dtype t) { return t == DM_F32 ? 4 : 8; }
+
+cudaEvent_t pool_event(dm_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+// Brackets one group of launches with events when timing is enabled.
+struct ProfScope {
+    dm_ctx* ctx;
+    const char* name;
+    cudaEvent_t start = nullptr;
+    int64_t before = 0;
+    ProfScope(dm_ctx* c, const char* n) : ctx(c), name(n) {
+        if (!ctx->profiling) return;
+        start = pool_event(ctx);
+        before = ctx->launches;
+        if (start) cudaEventRecord(start, ctx->stream);
+    }
+    ~ProfScope() {
+        if (!ctx->profiling || !start) return;
+        cudaEvent_t stop = pool_event(ctx);
+        if (!stop) { ctx->event_pool.push_back(start); return; }
+        cudaEventRecord(stop, ctx->stream);
+        ctx->pending.push_back({name, start, stop, ctx->launches - before});
+    }
+};
+
+dm_status resolve_profile(dm_ctx* ctx) {
+    if (ctx->pending.empty()) return DM_OK;
+    DM_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& p : ctx->pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+            auto& st = ctx->stats[p.name];
+            st.launches += p.launches;
+            st.ms += ms;
+        } else {
+            cudaGetLastError();
+        }
+        ctx->event_pool.push_back(p.start);
+        ctx->event_pool.push_back(p.stop);
+    }
+    ctx->pending.clear();
+    return DM_OK;
+}
 size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
 
 dm_status ensure_arena(dm_ctx* ctx, size_t bytes) {
@@ -170,7 +230,10 @@ dm_status prepare_l1(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
     a.err = ctx->err;
 
     DM_TRY_CUDA(cudaMemsetAsync(base, 0, zero_bytes, ctx->stream));
-    DM_TRY_CUDA(sort_launch_keygen(a, ctx->stream, &ctx->launches));
+    {
+        ProfScope ps(ctx, "sort_keygen_hist");
+        DM_TRY_CUDA(sort_launch_keygen(a, ctx->stream, &ctx->launches));
+    }
 
     // Read the histograms back: skip digit positions that are constant in
     // every column (a stable pass over a constant digit is the identity).
@@ -197,12 +260,20 @@ dm_status prepare_l1(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
         if (needed) passes.push_back(q);
     }
     if (passes.empty()) passes.push_back(0);   // still writes values + permutation
-    DM_TRY_CUDA(sort_launch_passes(a, passes.data(), (int)passes.size(), ctx->stream, &ctx->launches));
+    {
+        ProfScope ps(ctx, "sort_onesweep");
+        DM_TRY_CUDA(sort_launch_passes(a, passes.data(), (int)passes.size(), ctx->stream,
+                                       &ctx->launches));
+    }
     // R_i for the part of the query that is linear in the point (shift: the
     // median of each column, xs[c * n + n / 2]).
     DM_TRY_CUDA(cudaMalloc(&p->R, (size_t)n * acc_size(t)));
-    DM_TRY_CUDA(rowsum_launch(t, X, n, d, ldx, static_cast<unsigned char*>(p->xs) + (size_t)(n / 2) * dtype_size(t),
-                              n, p->R, ctx->stream, &ctx->launches));
+    {
+        ProfScope ps(ctx, "l1_rowsum");
+        DM_TRY_CUDA(rowsum_launch(t, X, n, d, ldx,
+                                  static_cast<unsigned char*>(p->xs) + (size_t)(n / 2) * dtype_size(t),
+                                  n, p->R, ctx->stream, &ctx->launches));
+    }
     return DM_OK;
 }
 
@@ -220,7 +291,10 @@ dm_status prepare_l2(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
     const int blocks = l2prep_blocks(a);
     DM_TRY(ensure_arena(ctx, (size_t)blocks * p->d * 8 + 16));
     a.partial = ctx->arena;
-    DM_TRY_CUDA(l2prep_launch(a, ctx->stream, &ctx->launches));
+    {
+        ProfScope ps(ctx, "l2_prepare");
+        DM_TRY_CUDA(l2prep_launch(a, ctx->stream, &ctx->launches));
+    }
     return take_device_error(ctx);
 }
 
@@ -261,7 +335,10 @@ dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* o
         // R^T Z and 1^T Z, then the sorted part (Algorithm 2).
         r.X = p->R; r.ldx = 1; r.x_acc = true;
         r.mu = nullptr; r.mu_stride = 0; r.s = nullptr;
-        DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
+        {
+            ProfScope ps(ctx, "l1_totals");
+            DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
+        }
         L1QueryArgs q{};
         q.dtype = t;
         q.xs = p->xs; q.perm = p->perm; q.n = n; q.d = d;
@@ -274,18 +351,23 @@ dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* o
         q.scratch = base + o_l1;
         q.err = ctx->err;
         q.num_sms = ctx->num_sms;
+        ProfScope ps(ctx, "l1_query");
         DM_TRY_CUDA(l1_query_launch(q, ctx->stream, &ctx->launches));
         return DM_OK;
     }
     r.X = p->X; r.ldx = p->ldx; r.x_acc = false;
     r.mu = p->mu; r.mu_stride = 1;
     r.s = p->s;
-    DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
+    {
+        ProfScope ps(ctx, "l2_reduce");
+        DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
+    }
     L2ApplyArgs ap{};
     ap.dtype = t;
     ap.X = p->X; ap.n = n; ap.d = d; ap.ldx = p->ldx;
     ap.mu = p->mu; ap.s = p->s; ap.res = r.res; ap.k = k;
     ap.out = out; ap.ldo = ldo;
+    ProfScope ps(ctx, "l2_apply");
     DM_TRY_CUDA(l2apply_launch(ap, ctx->stream, &ctx->launches));
     return DM_OK;
 }
@@ -345,6 +427,8 @@ void dm_destroy(dm_ctx* ctx) {
     if (ctx->err) cudaFree(ctx->err);
     if (ctx->host_err) cudaFreeHost(ctx->host_err);
     if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
+    for (auto& p : ctx->pending) { cudaEventDestroy(p.start); cudaEventDestroy(p.stop); }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -355,6 +439,34 @@ dm_status dm_set_stream(dm_ctx* ctx, void* stream) {
 }
 
 int64_t dm_launch_count(const dm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+dm_status dm_profile_enable(dm_ctx* ctx, int enable) {
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    DM_TRY(resolve_profile(ctx));
+    ctx->stats.clear();
+    ctx->profiling = enable != 0;
+    return DM_OK;
+}
+
+dm_status dm_profile_read(dm_ctx* ctx, int max, int* count, char* names, int64_t* launches,
+                          double* total_ms) {
+    if (!ctx || !count || max < 0 || (max > 0 && (!names || !launches || !total_ms)))
+        return DM_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    DM_TRY(resolve_profile(ctx));
+    int i = 0;
+    for (const auto& kv : ctx->stats) {
+        if (i >= max) break;
+        std::memset(names + 32 * i, 0, 32);
+        std::strncpy(names + 32 * i, kv.first.c_str(), 31);
+        launches[i] = kv.second.launches;
+        total_ms[i] = kv.second.ms;
+        ++i;
+    }
+    *count = i;
+    return DM_OK;
+}
 
 dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* X, int64_t n,
                      int64_t d, int64_t ldx, dm_plan** plan) {
@@ -437,6 +549,7 @@ dm_status dm_bruteforce(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const voi
     a.X = X; a.n = n; a.d = d; a.ldx = ldx;
     a.Z = Z; a.k = k; a.ldz = ldz;
     a.out = out; a.ldo = ldo;
+    ProfScope ps(ctx, "bruteforce");
     DM_TRY_CUDA(brute_launch(a, ctx->stream, &ctx->launches));
     return DM_OK;
 }

@@ -47,6 +47,15 @@ def gpu_product(dm, ctx, metric, X, Z):
 
 
 def reference(metric, X, Z):
+    # The definition (double loop) where it is cheap; otherwise the oracle's
+    # sort-based form (l1) or p = 2 identity (squared l2), both pinned to the
+    # definition.  (At n = 1 the exact product is 0, which only the definition
+    # reproduces exactly; the identity leaves an FP64 cancellation residue.)
+    n = len(X)
+    d = 1 if np.ndim(X) == 1 else X.shape[1]
+    k = 1 if np.ndim(Z) == 1 else Z.shape[1]
+    if n * n * (d + k) <= 2e8:
+        return (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(X, Z)
     return oracle.l1_sort(X, Z) if metric == "l1" else oracle.l2sq_identity(X, Z)
 
 
