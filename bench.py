@@ -67,7 +67,8 @@ def parse_args():
 def workload_config(a, flush):
     return {"workload": f"gaussian-mixture-16 n={a.n} d={a.d} k={a.k} fp32",
             "n": a.n, "d": a.d, "k": a.k, "clusters": 16, "dtype": "fp32",
-            "products": ["l1", "l2sq"], "prepare_in_step": True, "l2_flush": flush}
+            "products": ["l1", "l2sq"], "prepare_in_step": True, "l2_flush": flush,
+            "l1_accumulation": "L2 reductions (dm_set_deterministic off)"}
 
 
 def dist_env():
@@ -181,16 +182,20 @@ def algorithmic_bytes(group, n, d, k, launches):
         return (16 * nd * launches - 4 * nd) / launches
     if group == "sort_keygen_hist":
         return 8 * nd
-    if group == "l2_reduce":
-        return 4 * nd + 4 * n * k + 4 * n
-    if group == "l2_apply":
-        return 4 * nd + 4 * n + 4 * n * k
-    if group == "l1_totals":
-        return 4 * n + 4 * n * k
+    if group == "l2_reduce":      # X and Z once
+        return 4 * nd + 4 * n * k
+    if group == "l2_apply":       # X once, out written
+        return 4 * nd + 4 * n * k
+    if group == "l1_aggregate":   # key 4 + perm 4 + gathered Z row 4k (tile sums)
+        return nd * (8 + 4 * k)
+    if group == "l1_prologue":    # read Z 4k + R 4, write the group-major copy 4k
+        return 8 * n * k + 4 * n
+    if group == "l1_finalize":    # read the partial output 4k + R 4, write out 4k
+        return 8 * n * k + 4 * n
     if group == "l1_rowsum":
         return 4 * nd + 4 * d + 4 * n
-    if group == "l2_prepare":
-        return (2 * 4 * nd + 4 * n) / max(launches, 1)
+    if group == "l2_prepare":     # column sums: X once
+        return 4 * nd / max(launches, 1)
     return None
 
 
@@ -328,7 +333,8 @@ def main():
     parts = {
         "l1_prepare_ms": sum(per_step.get(g, 0) for g in ("sort_keygen_hist", "sort_onesweep",
                                                           "l1_rowsum")),
-        "l1_query_ms": sum(per_step.get(g, 0) for g in ("l1_totals", "l1_query")),
+        "l1_query_ms": sum(per_step.get(g, 0) for g in ("l1_prologue", "l1_aggregate", "l1_query",
+                                                         "l1_finalize")),
         "l2_prepare_ms": per_step.get("l2_prepare", 0.0),
         "l2_query_ms": sum(per_step.get(g, 0) for g in ("l2_reduce", "l2_apply")),
     }

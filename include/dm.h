@@ -72,14 +72,25 @@ void dm_destroy(dm_ctx* ctx);
 /* Switch the stream later calls are issued on (borrowed, as in dm_create). */
 dm_status dm_set_stream(dm_ctx* ctx, void* cuda_stream);
 
+/* Accumulation order of the l1 query's d per-coordinate contributions
+ * (Algorithm 2 sums them over the coordinates).  on = 0 (the default): each
+ * contribution is added with a reduction in L2 as soon as it is ready; the
+ * order of the d additions of one output element varies from run to run, so
+ * results can differ in the last bits between runs.  on = 1: the
+ * contributions of coordinate c are added only after all of coordinate c-1,
+ * in a fixed order, so repeated runs give identical bits (slower: each
+ * coordinate waits for the previous one).  The squared-l2 path and integer
+ * data are deterministic in both settings (integer sums are exact). */
+dm_status dm_set_deterministic(dm_ctx* ctx, int on);
+
 /* Preprocess a point set (Algorithm 1, Section 2, for DM_L1; Appendix A for
  * DM_L2SQ).
  *   DM_L1:   every coordinate column of X is sorted ascending with a stable
  *            LSD radix sort; the plan owns the sorted values (d x n) and the
  *            sorting permutation (d x n, int32).  X may be freed afterwards.
  *   DM_L2SQ: the plan records the pointer X (the caller keeps X alive and
- *            unchanged for the plan's lifetime), the column means mu (a shift:
- *            the product is translation invariant) and s_i = ||x_i - mu||^2.
+ *            unchanged for the plan's lifetime) and the column means mu (a
+ *            shift: the product is translation invariant).
  * This call synchronizes the context's stream once (DM_L1 reads the digit
  * histograms back to skip radix passes whose digit is constant).  Returns
  * DM_ERR_NONFINITE if X holds NaN or Inf. */
@@ -138,8 +149,8 @@ dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
 int64_t dm_launch_count(const dm_ctx* ctx);
 
 /* Kernel timing.  While enabled, every group of launches a call makes
- * ("sort_keygen_hist", "sort_onesweep", "l1_rowsum", "l1_totals", "l1_query",
- * "l2_prepare", "l2_reduce", "l2_apply", "bruteforce") is bracketed by two CUDA events
+ * ("sort_keygen_hist", "sort_onesweep", "l1_rowsum", "l1_prologue",
+ * "l1_aggregate", "l1_query", "l1_finalize", "l2_prepare", "l2_reduce", "l2_apply", "bruteforce") is bracketed by two CUDA events
  * recorded on the context's stream.  Enabling (or disabling) clears what was
  * collected.  Off by default; costs two event records per group. */
 dm_status dm_profile_enable(dm_ctx* ctx, int enable);

@@ -62,6 +62,7 @@ def load() -> ctypes.CDLL:
             "dm_create": ([ctypes.POINTER(P), I32, P], I32),
             "dm_destroy": ([P], None),
             "dm_set_stream": ([P, P], I32),
+            "dm_set_deterministic": ([P, I32], I32),
             "dm_prepare": ([P, I32, I32, P, I64, I64, I64, ctypes.POINTER(P)], I32),
             "dm_plan_destroy": ([P], None),
             "dm_matvec_l1": ([P, P, P], I32),
@@ -182,6 +183,10 @@ def dm_destroy(ctx: Context) -> None:
 
 def dm_set_stream(ctx: Context, stream) -> None:
     _check(load().dm_set_stream(ctx.handle, ctypes.c_void_p(stream)), "dm_set_stream")
+
+
+def dm_set_deterministic(ctx: Context, on: bool = True) -> None:
+    _check(load().dm_set_deterministic(ctx.handle, 1 if on else 0), "dm_set_deterministic")
 
 
 def dm_prepare(ctx: Context, metric, X) -> Plan:

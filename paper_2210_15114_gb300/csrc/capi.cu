@@ -22,6 +22,7 @@ struct dm_ctx {
     uint32_t* host_hist = nullptr;   // pinned, histogram read-back in dm_prepare
     size_t host_hist_words = 0;
     int64_t launches = 0;
+    int deterministic = 0;           // dm_set_deterministic
     // Device buffers of dm_matmat_host (grown on demand).
     void* hx = nullptr; size_t hx_bytes = 0;
     void* hz = nullptr; size_t hz_bytes = 0;
@@ -48,7 +49,6 @@ struct dm_plan {
     const void* X = nullptr;
     int64_t ldx = 0;
     void* mu = nullptr;
-    void* s = nullptr;
 };
 
 namespace {
@@ -283,11 +283,10 @@ dm_status prepare_l2(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
     p->X = X;
     p->ldx = ldx;
     DM_TRY_CUDA(cudaMalloc(&p->mu, (size_t)p->d * dtype_size(t)));
-    DM_TRY_CUDA(cudaMalloc(&p->s, (size_t)p->n * acc_size(t)));
     L2PrepArgs a{};
     a.dtype = t;
     a.X = X; a.n = p->n; a.d = p->d; a.ldx = ldx;
-    a.mu = p->mu; a.s = p->s; a.err = ctx->err;
+    a.mu = p->mu; a.err = ctx->err;
     const int blocks = l2prep_blocks(a);
     DM_TRY(ensure_arena(ctx, (size_t)blocks * p->d * 8 + 16));
     a.partial = ctx->arena;
@@ -303,8 +302,7 @@ void free_plan_buffers(dm_plan* p) {
     if (p->perm) cudaFree(p->perm);
     if (p->R) cudaFree(p->R);
     if (p->mu) cudaFree(p->mu);
-    if (p->s) cudaFree(p->s);
-    p->xs = nullptr; p->perm = nullptr; p->R = nullptr; p->mu = nullptr; p->s = nullptr;
+    p->xs = nullptr; p->perm = nullptr; p->R = nullptr; p->mu = nullptr;
 }
 
 // ------------------------------------------------------------------ query
@@ -312,33 +310,11 @@ dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* o
     dm_ctx* ctx = p->ctx;
     const dm_dtype t = p->dtype;
     const int64_t n = p->n, d = p->d;
-    const int64_t rd = p->metric == DM_L1 ? 1 : d;   // rows of the reduce's X
-    if (!reduce_supported(rd, k)) return DM_ERR_UNSUPPORTED;
-
-    ReduceArgs r{};
-    r.dtype = t;
-    r.n = n; r.d = rd;
-    r.Z = Z; r.k = k; r.ldz = ldz;
-    r.num_sms = ctx->num_sms;
-    const int blocks = reduce_blocks(r);
-    const size_t o_partial = 0;
-    const size_t o_res = up16((size_t)blocks * (rd + 2) * k * 8);
-    const size_t o_l1 = up16(o_res + (size_t)(rd + 2) * k * 8);
-    size_t total = o_l1;
-    if (p->metric == DM_L1) total += l1_query_scratch_bytes(t, n, d, k);
-    DM_TRY(ensure_arena(ctx, total));
-    unsigned char* base = static_cast<unsigned char*>(ctx->arena);
-    r.partial = base + o_partial;
-    r.res = base + o_res;
 
     if (p->metric == DM_L1) {
-        // R^T Z and 1^T Z, then the sorted part (Algorithm 2).
-        r.X = p->R; r.ldx = 1; r.x_acc = true;
-        r.mu = nullptr; r.mu_stride = 0; r.s = nullptr;
-        {
-            ProfScope ps(ctx, "l1_totals");
-            DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
-        }
+        // R^T Z, 1^T Z and the group-major copy of Z, then the sorted part
+        // (Algorithm 2).
+        DM_TRY(ensure_arena(ctx, l1_query_scratch_bytes(t, n, d, k, ctx->num_sms)));
         L1QueryArgs q{};
         q.dtype = t;
         q.xs = p->xs; q.perm = p->perm; q.n = n; q.d = d;
@@ -346,18 +322,45 @@ dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* o
         q.mu = static_cast<unsigned char*>(p->xs) + (size_t)(n / 2) * dtype_size(t);
         q.mu_stride = n;
         q.Z = Z; q.k = k; q.ldz = ldz;
-        q.res = r.res;
         q.out = out; q.ldo = ldo;
-        q.scratch = base + o_l1;
+        q.scratch = ctx->arena;
         q.err = ctx->err;
         q.num_sms = ctx->num_sms;
-        ProfScope ps(ctx, "l1_query");
-        DM_TRY_CUDA(l1_query_launch(q, ctx->stream, &ctx->launches));
+        q.deterministic = ctx->deterministic;
+        {
+            ProfScope ps(ctx, "l1_prologue");
+            DM_TRY_CUDA(l1_prologue_launch(q, ctx->stream, &ctx->launches));
+        }
+        {
+            ProfScope ps(ctx, "l1_aggregate");
+            DM_TRY_CUDA(l1_aggregate_launch(q, ctx->stream, &ctx->launches));
+        }
+        {
+            ProfScope ps(ctx, "l1_query");
+            DM_TRY_CUDA(l1_query_launch(q, ctx->stream, &ctx->launches));
+        }
+        if (!q.deterministic) {
+            ProfScope ps(ctx, "l1_finalize");
+            DM_TRY_CUDA(l1_finalize_launch(q, ctx->stream, &ctx->launches));
+        }
         return DM_OK;
     }
+
+    if (!reduce_supported(d, k)) return DM_ERR_UNSUPPORTED;
+    ReduceArgs r{};
+    r.dtype = t;
+    r.n = n; r.d = d;
+    r.Z = Z; r.k = k; r.ldz = ldz;
+    r.num_sms = ctx->num_sms;
+    const int blocks = reduce_blocks(r);
+    const size_t o_res = up16((size_t)blocks * (d + 2) * k * 8);
+    DM_TRY(ensure_arena(ctx, up16(o_res + (size_t)(d + 2) * k * 8)));
+    unsigned char* base = static_cast<unsigned char*>(ctx->arena);
+    r.partial = base;
+    r.res = base + o_res;
     r.X = p->X; r.ldx = p->ldx; r.x_acc = false;
     r.mu = p->mu; r.mu_stride = 1;
-    r.s = p->s;
+    r.with_s = true;
     {
         ProfScope ps(ctx, "l2_reduce");
         DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
@@ -365,8 +368,9 @@ dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* o
     L2ApplyArgs ap{};
     ap.dtype = t;
     ap.X = p->X; ap.n = n; ap.d = d; ap.ldx = p->ldx;
-    ap.mu = p->mu; ap.s = p->s; ap.res = r.res; ap.k = k;
+    ap.mu = p->mu; ap.res = r.res; ap.k = k;
     ap.out = out; ap.ldo = ldo;
+    ap.num_sms = ctx->num_sms;
     ProfScope ps(ctx, "l2_apply");
     DM_TRY_CUDA(l2apply_launch(ap, ctx->stream, &ctx->launches));
     return DM_OK;
@@ -430,6 +434,12 @@ void dm_destroy(dm_ctx* ctx) {
     for (auto& p : ctx->pending) { cudaEventDestroy(p.start); cudaEventDestroy(p.stop); }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
+}
+
+dm_status dm_set_deterministic(dm_ctx* ctx, int on) {
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    ctx->deterministic = on ? 1 : 0;
+    return DM_OK;
 }
 
 dm_status dm_set_stream(dm_ctx* ctx, void* stream) {

@@ -85,7 +85,7 @@ cudaError_t sort_launch_passes(const SortArgs& a, const int* pass_list, int npas
 // Column sums of the query block and the shifted contraction:
 //   u[j]   = sum_i Z[i,j]
 //   W[c,j] = sum_i (X[i,c] - mu[c]) Z[i,j]      (mu == nullptr: no shift)
-//   v[j]   = sum_i s[i] Z[i,j]                  (only when s != nullptr)
+//   v[j]   = sum_i s_i Z[i,j],  s_i = ||x_i - mu||^2   (with_s; else 0)
 // Result layout in `res` (Wide type): W (d x k), then u (k), then v (k).
 // X holds V elements, or Acc elements when x_acc is set.
 struct ReduceArgs {
@@ -93,7 +93,7 @@ struct ReduceArgs {
     const void* X; int64_t n, d, ldx;
     bool x_acc;
     const void* mu; int64_t mu_stride;   // shift mu[c] = mu[c * mu_stride] (V type)
-    const void* s;                       // optional, Acc type, n entries
+    bool with_s;
     const void* Z; int64_t k, ldz;
     void* partial;                       // scratch: blocks x (d+2) x k Wide
     void* res;                           // (d+2) x k Wide
@@ -108,44 +108,51 @@ cudaError_t rowsum_launch(dm_dtype t, const void* X, int64_t n, int64_t d, int64
                           const void* mu, int64_t mu_stride, void* R, cudaStream_t s,
                           int64_t* launches);
 
-// Column means mu (V type, rounded) and s_i = ||x_i - mu||^2 (Acc type).
+// Column means mu (V type, rounded): the frame shift of the squared-l2 plan.
 struct L2PrepArgs {
     dm_dtype dtype;
     const void* X; int64_t n, d, ldx;
     void* partial;                       // scratch: blocks x d Wide
     void* mu;                            // d entries, V type
-    void* s;                             // n entries, Acc type
     uint32_t* err;
 };
 int l2prep_blocks(const L2PrepArgs& a);
 cudaError_t l2prep_launch(const L2PrepArgs& a, cudaStream_t s, int64_t* launches);
 
-// out_i = s_i u + v - 2 (x_i - mu) . W
+// out_i = s_i u + v - 2 (x_i - mu) . W,  s_i = ||x_i - mu||^2
 struct L2ApplyArgs {
     dm_dtype dtype;
     const void* X; int64_t n, d, ldx;
-    const void* mu; const void* s;
+    const void* mu;
     const void* res;                     // W, u, v as produced by the reduce
     int64_t k;
     void* out; int64_t ldo;
+    int num_sms;
 };
 cudaError_t l2apply_launch(const L2ApplyArgs& a, cudaStream_t s, int64_t* launches);
 
-// l1 query: scan + evaluate + cross-coordinate accumulation (Algorithm 2).
+// l1 query: scan + evaluate + cross-coordinate accumulation (Algorithm 2),
+// launched in order on one stream with the same arguments and scratch:
+// l1_prologue_launch (R^T Z, 1^T Z, group-major copy of Z),
+// l1_aggregate_launch (tile sums and their per-coordinate exclusive scan),
+// l1_query_launch (the sorted pass), l1_finalize_launch (L2-reduction mode).
 struct L1QueryArgs {
     dm_dtype dtype;
     const void* xs; const int32_t* perm; int64_t n, d;   // plan (d x n each)
     const void* R;                       // plan: R_i = sum_c (x_i(c) - mu_c), Acc type
     const void* mu;  int64_t mu_stride;  // the shift mu_c (V type)
     const void* Z; int64_t k, ldz;
-    const void* res;                     // R^T Z (k), then 1^T Z (k): Wide
     void* out; int64_t ldo;
     void* scratch;                       // l1_query_scratch_bytes()
     uint32_t* err;
     int num_sms;
+    int deterministic;                   // 1: ordered accumulation, 0: L2 reductions
 };
-size_t l1_query_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k);
+size_t l1_query_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k, int num_sms);
+cudaError_t l1_prologue_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches);
 cudaError_t l1_query_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches);
+cudaError_t l1_finalize_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches);
+cudaError_t l1_aggregate_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches);
 
 // Plain on-the-fly product (baseline).
 struct BruteArgs {

@@ -12,11 +12,22 @@
 // and stores R_k = sum_c (x_k(c) - mu_c)).  So the query is
 //     out[k,:] = R^T Z - R_k 1^T Z + sum_c 2 (x_r P_z[r] - P_xz[r]).
 //
-// One persistent kernel does the sorted part for all coordinates.  Work unit:
-// a tile of TILE_E consecutive sorted positions of one coordinate and one
-// group of KC query columns.  Per tile:
+// Two kernels.
+//
+// l1_prologue: one pass over the query block computes R^T Z and 1^T Z (FP32
+//   partial sums per 64 rows, added in FP64, fixed-order finalize) and writes
+//   a column-group-major copy Zg[g][i][0:KC] of Z (KC = 8 FP32 columns = one
+//   32-byte sector per row; a partial last group is zero-padded).
+//
+// l1_query: one persistent kernel does the sorted part for all coordinates.
+//   The k columns are processed one group of KC at a time, all coordinates of
+//   group g before group g+1, so the random-access working set of a group --
+//   the gathered rows of Zg[g] and the partial output outg[g], n*KC elements
+//   each (32 + 32 MiB at n = 2^20) -- stays resident in L2 while the sorted
+//   columns stream past it.  Work unit: a tile of TILE_E consecutive sorted
+//   positions of one coordinate of one group.  Per tile:
 //   A. stage perm, x - b (b = the tile's first sorted value) and gather the
-//      k-wide query rows Z[perm[r], :] into shared memory (cp.async);
+//      KC-wide rows Zg[g][perm[r]] into shared memory (cp.async);
 //   B. in-tile exclusive prefix sums Lz, Lxz of z and (x - b) z (FP32 for
 //      FP32 data);
 //   C. decoupled look-back over the earlier tiles of the same coordinate for
@@ -26,10 +37,12 @@
 //      so that 2 (x_r P_z[r] - P_xz[r]) = 2 ((x_r - b)(alpha + Lz_r) - (gamma + Lxz_r)):
 //      the large terms are combined in FP64 once per tile and each element
 //      works on tile-local values;
-//   D. wait until every tile of coordinate c-1 (same column group) has added
-//      its values (bounded spin on a counter), so each output element receives
+//   D. wait until every tile of coordinate c-1 (same group) has added its
+//      values (bounded spin on a counter), so each output element receives
 //      its d contributions in coordinate order: the result is deterministic;
-//   E. coordinate 0 stores value + R^T Z - R_k 1^T Z; later coordinates add;
+//   E. coordinate 0 stores value + R^T Z - R_k 1^T Z into outg, later
+//      coordinates add to it, the last one writes the sum into the caller's
+//      output (for d = 1 coordinate 0 writes it directly);
 //   F. publish "tile done" for coordinate c.
 // Tiles are claimed from an atomic counter in (group, coordinate, tile) order,
 // so every wait is on work claimed earlier by a running CTA: no deadlock.
@@ -50,30 +63,47 @@ template <dm_dtype DT, int KC>
 struct QCfg {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
-    static constexpr int SEGS = kThreads / KC;                 // thread segments per column
-    static constexpr int SEG_LEN = sizeof(V) == 4 ? (8 * KC < 48 ? 8 * KC : 48)
-                                                  : (4 * KC < 24 ? 4 * KC : 24);
+    // Thread (seg, quad) owns QW adjacent columns (one 16-byte vector of a Zg
+    // row, or the whole row when narrower) of SEG_LEN consecutive sorted
+    // positions; a column group of KC columns is NQ = KC / QW threads wide.
+    // The tile lives in registers: no shared-memory staging.
+    static constexpr int QW = (16 / (int)sizeof(V)) < KC ? (16 / (int)sizeof(V)) : KC;
+    static constexpr int NQ = KC / QW;
+    static constexpr int SEGS = kThreads / NQ;
+    static constexpr int SEG_LEN = sizeof(Acc) == 8 ? 4 : 8;
     static constexpr int TILE_E = SEGS * SEG_LEN;              // sorted positions per tile
-    static constexpr int SEG_STRIDE = (SEG_LEN + 1) * KC;      // padded (bank spread)
+    static constexpr int ROWB = KC * (int)sizeof(V);           // bytes of one Zg row
     static constexpr int NV = 2 * KC;                          // scanned quantities
-    static constexpr size_t dx_off = align16((size_t)SEGS * SEG_STRIDE * sizeof(V));
-    static constexpr size_t perm_off = dx_off + align16((size_t)TILE_E * sizeof(Acc));
-    static constexpr size_t smem = perm_off + (size_t)TILE_E * 4;
-    static constexpr int BATCH = SEG_LEN < 8 ? SEG_LEN : 8;   // RMW loads in flight per thread
+    static_assert(KC % QW == 0, "tile shape");
 };
+
+// Accumulation of the per-coordinate values into the group-major partial
+// output outg:
+//   kOrdered: coordinate c waits until every tile of coordinate c-1 has
+//             written, then reads, adds and writes (a fixed order: the result
+//             does not depend on scheduling); coordinate 0 stores the
+//             point-linear part R^T Z - R_k 1^T Z first and coordinate d-1
+//             writes the caller's output.
+//   kAtomic:  every value is added with a vector reduction in L2 (no waits;
+//             the order of the d additions per element varies from run to
+//             run); a finalize kernel adds the point-linear part and writes
+//             the caller's output.
+enum AccumMode : int { kOrdered = 0, kAtomic = 1 };
 
 template <class V, class Acc, class Wide>
 struct QParams {
     const V* xs; const int32_t* perm; int64_t n; int d;
     const Acc* R;                     // R_k = sum_c (x_k(c) - mu_c)
-    const V* Z; int64_t ldz; int k;
+    const V* Zg;                      // G x n x KC, group-major copy of Z
+    int k;
     const Wide* res;                  // R^T Z (k), then 1^T Z (k)
     const V* mu; int64_t mu_stride;
+    Acc* outg;                        // G x n x KC partial sums (d > 1)
     void* out; int64_t ldo;
-    uint32_t* counter; uint32_t* done; uint32_t* flags;
-    Wide* agg; Wide* inc;
+    uint32_t* counter; uint32_t* done;
+    const Wide* pre;                  // G x d x T x 2KC exclusive tile prefixes
     uint32_t* err;
-    int T, G, vw;
+    int T, G;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -110,6 +140,101 @@ __device__ __forceinline__ void stcg(float* p, float v) { __stcg(p, v); }
 __device__ __forceinline__ void stcg(double* p, double v) { __stcg(p, v); }
 __device__ __forceinline__ void stcg(long long* p, long long v) { __stcg(p, v); }
 
+// N consecutive elements (N * sizeof(T) in {4, 8, 16, 32}) moved as vectors.
+template <class T, int N>
+__device__ __forceinline__ void ld_vec(const T* p, T (&v)[N]) {
+    constexpr int B = N * (int)sizeof(T);
+    if constexpr (B % 16 == 0) {
+#pragma unroll
+        for (int h = 0; h < B / 16; ++h) {
+            const uint4 u = *reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(p) + 16 * h);
+            memcpy(reinterpret_cast<char*>(v) + 16 * h, &u, 16);
+        }
+    } else if constexpr (B == 8) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        memcpy(v, &u, 8);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) v[q] = p[q];
+    }
+}
+
+template <class T, int N>
+__device__ __forceinline__ void ldcg_vec(const T* p, T (&v)[N]) {
+    constexpr int B = N * (int)sizeof(T);
+    if constexpr (B % 16 == 0) {
+#pragma unroll
+        for (int h = 0; h < B / 16; ++h) {
+            const uint4 u = __ldcg(reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(p) + 16 * h));
+            memcpy(reinterpret_cast<char*>(v) + 16 * h, &u, 16);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) v[q] = ldcg(p + q);
+    }
+}
+
+template <class T, int N>
+__device__ __forceinline__ void stcg_vec(T* p, const T (&v)[N]) {
+    constexpr int B = N * (int)sizeof(T);
+    if constexpr (B % 16 == 0) {
+#pragma unroll
+        for (int h = 0; h < B / 16; ++h) {
+            uint4 u;
+            memcpy(&u, reinterpret_cast<const char*>(v) + 16 * h, 16);
+            __stcg(reinterpret_cast<uint4*>(reinterpret_cast<char*>(p) + 16 * h), u);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) stcg(p + q, v[q]);
+    }
+}
+
+// One row of N elements (N * sizeof(T) == 32 bytes) in a single 256-bit
+// global load; other sizes fall back to ld_vec.
+template <class T, int N>
+__device__ __forceinline__ void ld_row(const T* p, T (&v)[N]) {
+    if constexpr (N * sizeof(T) == 32) {
+        uint32_t r[8];
+        asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                       "=r"(r[6]), "=r"(r[7])
+                     : "l"(p));
+        memcpy(v, r, 32);
+    } else {
+        ld_vec<T, N>(p, v);
+    }
+}
+
+// Reductions in L2 (relaxed, gpu scope): vector form for FP32.
+template <int N>
+__device__ __forceinline__ void red_add(float* p, const float (&v)[N]) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int h = 0; h < N / 4; ++h)
+            asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                         :: "l"(p + 4 * h), "f"(v[4 * h]), "f"(v[4 * h + 1]), "f"(v[4 * h + 2]),
+                            "f"(v[4 * h + 3]) : "memory");
+    } else if constexpr (N == 2) {
+        asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};"
+                     :: "l"(p), "f"(v[0]), "f"(v[1]) : "memory");
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) atomicAdd(p + q, v[q]);
+    }
+}
+template <int N>
+__device__ __forceinline__ void red_add(double* p, const double (&v)[N]) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) atomicAdd(p + q, v[q]);
+}
+template <int N>
+__device__ __forceinline__ void red_add(long long* p, const long long (&v)[N]) {
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+        atomicAdd(reinterpret_cast<unsigned long long*>(p + q), (unsigned long long)v[q]);
+}
+
 // Bounded wait until *p >= target (acquire).  Returns false on timeout.
 __device__ __forceinline__ bool wait_geq(const uint32_t* p, uint32_t target, uint32_t* err) {
     uint32_t spins = 0;
@@ -120,53 +245,8 @@ __device__ __forceinline__ bool wait_geq(const uint32_t* p, uint32_t target, uin
     return true;
 }
 
-// Gather the query rows of the tile into shared memory: z_s[seg][i][col].
-template <dm_dtype DT, int KC>
-__device__ __forceinline__ void gather_rows(typename Types<DT>::V* z_s, const int32_t* perm_s,
-                                            const typename Types<DT>::V* Zg, int64_t ldz, int kg,
-                                            int vw) {
-    using Cfg = QCfg<DT, KC>;
-    using V = typename Types<DT>::V;
-    constexpr int ROWB = KC * (int)sizeof(V);
-    if constexpr (ROWB % 16 == 0) {
-        if (vw == 16 && kg == KC) {
-            constexpr int VPC = 16 / (int)sizeof(V), CPR = ROWB / 16;
-            for (int j = threadIdx.x; j < Cfg::TILE_E * CPR; j += kThreads) {
-                const int e = j / CPR, q = j % CPR;
-                const int32_t pe = perm_s[e];
-                V* dst = z_s + (e / Cfg::SEG_LEN) * Cfg::SEG_STRIDE + (e % Cfg::SEG_LEN) * KC + q * VPC;
-                const V* src = Zg + (int64_t)(pe < 0 ? 0 : pe) * ldz + q * VPC;
-                cp_async16(dst, src, pe >= 0 ? 16 : 0);
-            }
-            return;
-        }
-    }
-    if constexpr (ROWB % 8 == 0 && sizeof(V) <= 8) {
-        if (vw == 8 && kg == KC) {
-            constexpr int VPC = 8 / (int)sizeof(V), CPR = ROWB / 8;
-            for (int j = threadIdx.x; j < Cfg::TILE_E * CPR; j += kThreads) {
-                const int e = j / CPR, q = j % CPR;
-                const int32_t pe = perm_s[e];
-                V* dst = z_s + (e / Cfg::SEG_LEN) * Cfg::SEG_STRIDE + (e % Cfg::SEG_LEN) * KC + q * VPC;
-                const V* src = Zg + (int64_t)(pe < 0 ? 0 : pe) * ldz + q * VPC;
-                cp_async8(dst, src, pe >= 0 ? 8 : 0);
-            }
-            return;
-        }
-    }
-    for (int j = threadIdx.x; j < Cfg::TILE_E * KC; j += kThreads) {
-        const int e = j / KC, q = j % KC;
-        const int32_t pe = perm_s[e];
-        V* dst = z_s + (e / Cfg::SEG_LEN) * Cfg::SEG_STRIDE + (e % Cfg::SEG_LEN) * KC + q;
-        const V* src = Zg + (int64_t)(pe < 0 ? 0 : pe) * ldz + (q < kg ? q : 0);
-        const int bytes = (pe >= 0 && q < kg) ? (int)sizeof(V) : 0;
-        if constexpr (sizeof(V) == 8) cp_async8(dst, src, bytes);
-        else cp_async4(dst, src, bytes);
-    }
-}
-
 // ---------------------------------------------------------------- kernel
-template <dm_dtype DT, int KC>
+template <dm_dtype DT, int KC, int MODE>
 __global__ void __launch_bounds__(kThreads)
 l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename Types<DT>::Wide> p) {
     using Cfg = QCfg<DT, KC>;
@@ -175,196 +255,419 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
     constexpr int SEG_LEN = Cfg::SEG_LEN, TILE_E = Cfg::TILE_E, NV = Cfg::NV;
-    constexpr int SPW = 32 / KC;   // segments of one column per warp
+    constexpr int QW = Cfg::QW, NQ = Cfg::NQ;
+    constexpr int SPW = 32 / NQ;   // segments per warp
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* z_s = reinterpret_cast<V*>(smem_raw);
-    Acc* dx_s = reinterpret_cast<Acc*>(smem_raw + Cfg::dx_off);
-    int32_t* perm_s = reinterpret_cast<int32_t*>(smem_raw + Cfg::perm_off);
     __shared__ Acc wt[kWarps][NV];
-    __shared__ Acc tile_tot[NV];
     __shared__ Acc ag_s[4][KC];
-    __shared__ uint32_t s_claim;
+    __shared__ uint32_t s_claim[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int col = tid % KC, seg = tid / KC;
+    const int quad = tid % NQ, seg = tid / NQ;
+    const int col0 = quad * QW;                 // first column of this thread
     const int d = p.d, T = p.T, k = p.k;
     const uint32_t total_tiles = (uint32_t)p.G * (uint32_t)d * (uint32_t)T;
+    const int i0 = seg * SEG_LEN;
 
-    while (true) {
-        if (tid == 0) s_claim = atomicAdd(p.counter, 1u);
-        __syncthreads();
-        const uint32_t claim = s_claim;
-        if (claim >= total_tiles) break;
+    // The permutation and coordinates of the next tile are loaded while the
+    // current tile is evaluated (claims stay in order, one tile ahead).
+    int32_t pe[SEG_LEN];
+    V xv[SEG_LEN];
+    auto load_tile = [&](uint32_t claim, int32_t (&pv)[SEG_LEN], V (&xw)[SEG_LEN]) {
+        const int t = (int)(claim % (uint32_t)T);
+        const int c = (int)((claim / (uint32_t)T) % (uint32_t)d);
+        const int64_t e0 = (int64_t)t * TILE_E;
+        const int ne = (int)min64(TILE_E, p.n - e0);
+        const int64_t sbase = (int64_t)c * p.n + e0;
+#pragma unroll
+        for (int i = 0; i < SEG_LEN; ++i) {
+            pv[i] = -1;
+            xw[i] = V(0);
+            if (i0 + i < ne) { pv[i] = __ldcs(p.perm + sbase + i0 + i); xw[i] = __ldcs(p.xs + sbase + i0 + i); }
+        }
+    };
+    if (tid == 0) s_claim[0] = atomicAdd(p.counter, 1u);
+    __syncthreads();
+    uint32_t claim = s_claim[0];
+    if (claim < total_tiles) load_tile(claim, pe, xv);
+    int slot = 0;
+
+    while (claim < total_tiles) {
+        if (tid == 0) s_claim[slot ^ 1] = atomicAdd(p.counter, 1u);
         const int t = (int)(claim % (uint32_t)T);
         const int c = (int)((claim / (uint32_t)T) % (uint32_t)d);
         const int g = (int)(claim / ((uint32_t)T * (uint32_t)d));
         const int64_t e0 = (int64_t)t * TILE_E;
         const int ne = (int)min64(TILE_E, p.n - e0);
         const int64_t sbase = (int64_t)c * p.n + e0;
-        const V b = p.xs[sbase];
-        const int kg = min(KC, k - g * KC);
+        const V b = __ldcs(p.xs + sbase);
 
-        // A. stage the tile
-        for (int e = tid; e < TILE_E; e += kThreads) {
-            int32_t pe = -1;
-            Acc dx = 0;
-            if (e < ne) {
-                pe = p.perm[sbase + e];
-                dx = diff(p.xs[sbase + e], b);
-                if ((uint32_t)pe >= (uint32_t)p.n) {   // never for a valid plan
-                    set_error(p.err, kErrInternal);
-                    pe = -1;
+        // A. this thread's positions: x - b, checked permutation, gathered columns
+        Acc dx[SEG_LEN];
+        {
+            bool bad = false;
+#pragma unroll
+            for (int i = 0; i < SEG_LEN; ++i) {
+                if (i0 + i < ne && (uint32_t)pe[i] >= (uint32_t)p.n) { bad = true; pe[i] = -1; }   // never for a valid plan
+                dx[i] = i0 + i < ne ? diff(xv[i], b) : Acc(0);
+            }
+            if (bad) set_error(p.err, kErrInternal);
+        }
+        V zv[SEG_LEN][QW];
+        {
+            const V* zg = p.Zg + (int64_t)g * p.n * KC + col0;
+#pragma unroll
+            for (int i = 0; i < SEG_LEN; ++i) {
+                if (pe[i] >= 0) ld_vec<V, QW>(zg + (int64_t)pe[i] * KC, zv[i]);
+                else {
+#pragma unroll
+                    for (int q = 0; q < QW; ++q) zv[i][q] = V(0);
                 }
             }
-            perm_s[e] = pe;
-            dx_s[e] = dx;
         }
-        __syncthreads();
-        gather_rows<DT, KC>(z_s, perm_s, p.Z + (int64_t)g * KC, p.ldz, kg, p.vw);
-        cp_async_wait_all();
-        __syncthreads();
 
-        // B. in-tile exclusive prefix of this thread's segment
-        const V* zcol = z_s + seg * Cfg::SEG_STRIDE + col;
-        const Acc* dxs = dx_s + seg * SEG_LEN;
-        Acc sz = 0, sxz = 0;
-#pragma unroll 8
-        for (int i = 0; i < SEG_LEN; ++i) {
-            const Acc z = (Acc)zcol[i * KC];
-            sz += z;
-            sxz = fmac(dxs[i], z, sxz);
-        }
-        Acc iz = sz, ixz = sxz;
+        // B. in-tile exclusive prefix of this thread's segment and columns
+        Acc Lz[QW], Lxz[QW];
 #pragma unroll
-        for (int o = 1; o < SPW; o <<= 1) {
-            const Acc a = __shfl_up_sync(0xffffffffu, iz, o * KC);
-            const Acc bb = __shfl_up_sync(0xffffffffu, ixz, o * KC);
-            if (lane >= o * KC) { iz += a; ixz += bb; }
-        }
-        Acc ez = __shfl_up_sync(0xffffffffu, iz, KC);
-        Acc exz = __shfl_up_sync(0xffffffffu, ixz, KC);
-        if (lane < KC) { ez = 0; exz = 0; }
-        if (lane >= 32 - KC) { wt[warp][col] = iz; wt[warp][KC + col] = ixz; }
-        __syncthreads();
-        Acc pz = 0, pxz = 0, tz = 0, txz = 0;
+        for (int q = 0; q < QW; ++q) {
+            Acc sz = 0, sxz = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const Acc a = wt[w][col], bb = wt[w][KC + col];
-            if (w < warp) { pz += a; pxz += bb; }
-            tz += a;
-            txz += bb;
-        }
-        Acc Lz = pz + ez, Lxz = pxz + exz;
-        if (tid < KC) { tile_tot[tid] = tz; tile_tot[KC + tid] = txz; }
-        __syncthreads();
-
-        // C. look-back for the tile's exclusive prefix, then alpha / gamma
-        if (warp == 0) {
-            const Wide bm = (Wide)b - (Wide)p.mu[(int64_t)c * p.mu_stride];
-            const int64_t dimt = ((int64_t)g * d + c) * T;
-            uint32_t* fl = p.flags + dimt;
-            Wide* ag = p.agg + dimt * NV;
-            Wide* in = p.inc + dimt * NV;
-            Wide agg = 0, excl = 0;
-            if (lane < NV) {
-                const int cc = lane % KC;
-                agg = (lane < KC) ? (Wide)tile_tot[cc]
-                                  : bm * (Wide)tile_tot[cc] + (Wide)tile_tot[KC + cc];
+            for (int i = 0; i < SEG_LEN; ++i) {
+                const Acc z = (Acc)zv[i][q];
+                sz += z;
+                sxz = fmac(dx[i], z, sxz);
             }
-            if (t == 0) {
-                if (lane < NV) in[lane] = agg;
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release(&fl[0], 2u);
+            Acc iz = sz, ixz = sxz;
+#pragma unroll
+            for (int o = 1; o < SPW; o <<= 1) {
+                const Acc a = __shfl_up_sync(0xffffffffu, iz, o * NQ);
+                const Acc bb = __shfl_up_sync(0xffffffffu, ixz, o * NQ);
+                if (lane >= o * NQ) { iz += a; ixz += bb; }
+            }
+            Acc ez = __shfl_up_sync(0xffffffffu, iz, NQ);
+            Acc exz = __shfl_up_sync(0xffffffffu, ixz, NQ);
+            if (lane < NQ) { ez = 0; exz = 0; }
+            if (lane >= 32 - NQ) { wt[warp][col0 + q] = iz; wt[warp][KC + col0 + q] = ixz; }
+            Lz[q] = ez;
+            Lxz[q] = exz;
+        }
+        // C. the tile's exclusive prefix (from the tile scan) -> alpha, gamma
+        if (tid < KC) {
+            const Wide bm = (Wide)b - (Wide)p.mu[(int64_t)c * p.mu_stride];
+            const Wide* pr = p.pre + (((int64_t)g * d + c) * T + t) * NV;
+            const Wide Pz = pr[tid], Pxz = pr[KC + tid];
+            ag_s[0][tid] = (Acc)Pz;
+            ag_s[1][tid] = (Acc)(Pxz - bm * Pz);
+            if (MODE == kOrdered && c == 0) {
+                const int gc = g * KC + tid;
+                ag_s[2][tid] = gc < k ? (Acc)p.res[gc] : Acc(0);       // R^T Z
+                ag_s[3][tid] = gc < k ? (Acc)p.res[k + gc] : Acc(0);   // 1^T Z
+            }
+        }
+        // D. (ordered) coordinate order: wait for every tile of coordinate c-1
+        if (MODE == kOrdered) {
+            if (c > 0 && tid == 0) wait_geq(p.done + (int64_t)g * d + c - 1, (uint32_t)T, p.err);
+        }
+        __syncthreads();
+        const uint32_t next = s_claim[slot ^ 1];
+        int32_t pe_n[SEG_LEN];
+        V xv_n[SEG_LEN];
+        if (next < total_tiles) load_tile(next, pe_n, xv_n);
+#pragma unroll
+        for (int q = 0; q < QW; ++q) {
+            Acc pz = 0, pxz = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const Acc a = wt[w][col0 + q], bb = wt[w][KC + col0 + q];
+                if (w < warp) { pz += a; pxz += bb; }
+            }
+            Lz[q] += pz;
+            Lxz[q] += pxz;
+        }
+
+        // E. evaluate and accumulate
+        {
+            Acc al[QW], gm[QW];
+#pragma unroll
+            for (int q = 0; q < QW; ++q) { al[q] = ag_s[0][col0 + q]; gm[q] = ag_s[1][col0 + q]; }
+            Acc* og = p.outg + (int64_t)g * p.n * KC + col0;
+            if constexpr (MODE == kAtomic) {
+#pragma unroll
+                for (int i = 0; i < SEG_LEN; ++i) {
+                    Acc val[QW];
+#pragma unroll
+                    for (int q = 0; q < QW; ++q) {
+                        val[q] = Acc(2) * fmac(dx[i], al[q] + Lz[q], -(gm[q] + Lxz[q]));
+                        const Acc z = (Acc)zv[i][q];
+                        Lz[q] += z;
+                        Lxz[q] = fmac(dx[i], z, Lxz[q]);
+                    }
+                    if (pe[i] >= 0) red_add<QW>(og + (int64_t)pe[i] * KC, val);
+                }
             } else {
-                if (lane < NV) ag[(int64_t)t * NV + lane] = agg;
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release(&fl[t], 1u);
-                int pred = t - 1;
-                while (true) {
-                    uint32_t f = 0;
-                    if (lane == 0) {
-                        uint32_t spins = 0;
-                        while ((f = ld_acquire(&fl[pred])) == 0u) {
-                            if (++spins > kSpinLimit) { set_error(p.err, kErrTimeout); f = 2u; break; }
-                            __nanosleep(32);
+                const bool first = c == 0, final_ = c == d - 1;
+                const int kg = min(KC, k - g * KC);
+                Acc rz[QW], uz[QW];
+#pragma unroll
+                for (int q = 0; q < QW; ++q) {
+                    rz[q] = first ? ag_s[2][col0 + q] : Acc(0);
+                    uz[q] = first ? ag_s[3][col0 + q] : Acc(0);
+                }
+                Out* oc = static_cast<Out*>(p.out) + (int64_t)g * KC + col0;
+                Acc old[SEG_LEN][QW];
+#pragma unroll
+                for (int i = 0; i < SEG_LEN; ++i) {
+                    if (pe[i] >= 0 && !first) {
+                        ldcg_vec<Acc, QW>(og + (int64_t)pe[i] * KC, old[i]);
+                    } else if (pe[i] >= 0) {
+                        const Acc Rk = p.R[pe[i]];
+#pragma unroll
+                        for (int q = 0; q < QW; ++q) old[i][q] = rz[q] - Rk * uz[q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < QW; ++q) old[i][q] = 0;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < SEG_LEN; ++i) {
+                    Acc sum[QW];
+#pragma unroll
+                    for (int q = 0; q < QW; ++q) {
+                        const Acc v = fmac(dx[i], al[q] + Lz[q], -(gm[q] + Lxz[q]));
+                        sum[q] = fmac(Acc(2), v, old[i][q]);
+                        const Acc z = (Acc)zv[i][q];
+                        Lz[q] += z;
+                        Lxz[q] = fmac(dx[i], z, Lxz[q]);
+                    }
+                    if (pe[i] >= 0) {
+                        if (!final_) {
+                            stcg_vec<Acc, QW>(og + (int64_t)pe[i] * KC, sum);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < QW; ++q)
+                                if (col0 + q < kg) stcg(oc + (int64_t)pe[i] * p.ldo + q, (Out)sum[q]);
                         }
                     }
-                    f = __shfl_sync(0xffffffffu, f, 0);
-                    __syncwarp();
-                    if (lane < NV) excl += ldcg((f == 2u ? in : ag) + (int64_t)pred * NV + lane);
-                    if (f == 2u || pred == 0) break;
-                    --pred;
-                }
-                if (lane < NV) in[(int64_t)t * NV + lane] = excl + agg;
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release(&fl[t], 2u);
-            }
-            const Wide pxz_l = __shfl_sync(0xffffffffu, excl, (lane + KC) & 31);
-            if (lane < KC) {
-                const Wide Pz = excl, Pxz = pxz_l;
-                ag_s[0][lane] = (Acc)Pz;
-                ag_s[1][lane] = (Acc)(Pxz - bm * Pz);
-                if (c == 0) {
-                    const int gc = g * KC + lane;
-                    ag_s[2][lane] = gc < k ? (Acc)p.res[gc] : Acc(0);       // R^T Z
-                    ag_s[3][lane] = gc < k ? (Acc)p.res[k + gc] : Acc(0);   // 1^T Z
                 }
             }
         }
 
-        // D. coordinate order: wait for every tile of coordinate c-1
-        if (c > 0 && tid == 0) wait_geq(p.done + (int64_t)g * d + c - 1, (uint32_t)T, p.err);
-        __syncthreads();
-
-        // E. evaluate and accumulate into the output rows
-        {
-            const Acc al = ag_s[0][col], gm = ag_s[1][col];
-            const Acc rz = ag_s[2][col], uz = ag_s[3][col];
-            const bool colok = col < kg;
-            Out* ocol = static_cast<Out*>(p.out) + (int64_t)g * KC + col;
-            const int32_t* ps = perm_s + seg * SEG_LEN;
-            constexpr int B = Cfg::BATCH;
-            for (int i0 = 0; i0 < SEG_LEN; i0 += B) {
-                int32_t pr[B];
-                Acc old[B];
-#pragma unroll
-                for (int q = 0; q < B; ++q) {
-                    pr[q] = ps[i0 + q];
-                    old[q] = 0;
-                    if (colok && pr[q] >= 0) {
-                        if (c > 0) old[q] = (Acc)ldcg(ocol + (int64_t)pr[q] * p.ldo);
-                        else old[q] = rz - p.R[pr[q]] * uz;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < B; ++q) {
-                    const int i = i0 + q;
-                    const Acc z = (Acc)zcol[i * KC];
-                    const Acc dx = dxs[i];
-                    const Acc v = fmac(dx, al + Lz, -(gm + Lxz));
-                    if (colok && pr[q] >= 0) stcg(ocol + (int64_t)pr[q] * p.ldo, (Out)fmac(Acc(2), v, old[q]));
-                    Lz += z;
-                    Lxz = fmac(dx, z, Lxz);
-                }
-            }
+        // F. this tile's values are in place (the barrier also frees wt/ag_s)
+        if constexpr (MODE == kOrdered) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) red_release_add(p.done + (int64_t)g * d + c, 1u);
+        } else {
+            __syncthreads();
         }
-
-        // F. this tile's values are in place
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) red_release_add(p.done + (int64_t)g * d + c, 1u);
+        claim = next;
+        slot ^= 1;
+#pragma unroll
+        for (int i = 0; i < SEG_LEN; ++i) { pe[i] = pe_n[i]; xv[i] = xv_n[i]; }
     }
 }
 
+// Tile aggregates (the reduce half of reduce-then-scan): one warp per tile
+// of the query kernel's tiling, sum_r z[perm[r]] and sum_r (x_r - mu) z[perm[r]]
+// over the tile, formed as (b - mu) sum z + sum (x - b) z with b the tile's
+// first sorted value (FP32 partial sums per lane, warp tree, FP64 frame
+// shift).  No shared memory and no barriers: a pure stream of loads.
 template <dm_dtype DT, int KC>
-int tile_elems() { return QCfg<DT, KC>::TILE_E; }
+__global__ void __launch_bounds__(kThreads)
+l1_aggregate_kernel(const typename Types<DT>::V* __restrict__ xs, const int32_t* __restrict__ perm,
+                    int64_t n, int d, const typename Types<DT>::V* __restrict__ Zg,
+                    const typename Types<DT>::V* __restrict__ mu, int64_t mu_stride,
+                    typename Types<DT>::Wide* __restrict__ agg, int T, int G, uint32_t* err) {
+    using Cfg = QCfg<DT, KC>;
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Wide = typename Types<DT>::Wide;
+    constexpr int TILE_E = Cfg::TILE_E, NV = Cfg::NV, U = 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+    const int64_t total = (int64_t)G * d * T;
+    for (int64_t tile = gw; tile < total; tile += nw) {
+        const int t = (int)(tile % T);
+        const int c = (int)((tile / T) % d);
+        const int g = (int)(tile / ((int64_t)T * d));
+        const int64_t e0 = (int64_t)t * TILE_E;
+        const int ne = (int)min64(TILE_E, n - e0);
+        const int64_t sbase = (int64_t)c * n + e0;
+        const V b = xs[sbase];
+        const V* zg = Zg + (int64_t)g * n * KC;
+        Acc sz[KC], sxz[KC];
+#pragma unroll
+        for (int q = 0; q < KC; ++q) { sz[q] = 0; sxz[q] = 0; }
+        bool bad = false;
+        // Software pipeline: the permutation of block j+1 is loaded while the
+        // rows of block j are gathered and summed.
+        int32_t pe[U];
+        Acc dx[U];
+        auto load_block = [&](int e, int32_t (&pv)[U], Acc (&dv)[U]) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int ee = e + 32 * u;
+                pv[u] = -1;
+                dv[u] = 0;
+                if (ee < ne) { pv[u] = __ldcs(perm + sbase + ee); dv[u] = diff(__ldcs(xs + sbase + ee), b); }
+                if (ee < ne && (uint32_t)pv[u] >= (uint32_t)n) { bad = true; pv[u] = -1; }
+            }
+        };
+        load_block(lane, pe, dx);
+        for (int e = lane; e < ne; e += 32 * U) {
+            V zv[U][KC];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (pe[u] >= 0) ld_row<V, KC>(zg + (int64_t)pe[u] * KC, zv[u]);
+                else {
+#pragma unroll
+                    for (int q = 0; q < KC; ++q) zv[u][q] = V(0);
+                }
+            }
+            int32_t pe_n[U];
+            Acc dx_n[U];
+            load_block(e + 32 * U, pe_n, dx_n);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int q = 0; q < KC; ++q) {
+                    const Acc z = (Acc)zv[u][q];
+                    sz[q] += z;
+                    sxz[q] = fmac(dx[u], z, sxz[q]);
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u) { pe[u] = pe_n[u]; dx[u] = dx_n[u]; }
+        }
+        if (bad) set_error(err, kErrInternal);
+        const Wide bm = (Wide)b - (Wide)mu[(int64_t)c * mu_stride];
+        Wide mine = 0;
+#pragma unroll
+        for (int q = 0; q < KC; ++q) {
+            Acc a = sz[q], x = sxz[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+            }
+            if (lane == q) mine = (Wide)a;
+            if (lane == KC + q) mine = bm * (Wide)a + (Wide)x;
+        }
+        if (lane < NV) agg[tile * NV + lane] = mine;
+    }
+}
 
-int pick_kc(int64_t k) {
-    if (k >= 16) return 16;
+// Exclusive scan of the tile aggregates of each (group, coordinate) segment,
+// in place (the scan half): thread (value v, chunk ch) sums its chunk of
+// tiles, chunk bases are added in chunk order, then the chunk is rewritten
+// as running prefixes.  Fixed order: reproducible.
+template <class Wide>
+__global__ void __launch_bounds__(kThreads)
+l1_tile_scan_kernel(Wide* __restrict__ agg, int T, int NV) {
+    __shared__ Wide cs[kThreads];
+    Wide* a = agg + (int64_t)blockIdx.x * T * NV;
+    const int CH = kThreads / NV;
+    const int v = threadIdx.x % NV, ch = threadIdx.x / NV;
+    const int per = (T + CH - 1) / CH;
+    const int t0 = ch < CH ? min(T, ch * per) : T, t1 = ch < CH ? min(T, t0 + per) : T;
+    Wide sum = 0;
+    for (int t = t0; t < t1; ++t) sum += a[(int64_t)t * NV + v];
+    cs[threadIdx.x] = sum;
+    __syncthreads();
+    Wide run = 0;
+    for (int j = 0; j < ch && j < CH; ++j) run += cs[j * NV + v];
+    for (int t = t0; t < t1; ++t) {
+        const Wide x = a[(int64_t)t * NV + v];
+        a[(int64_t)t * NV + v] = run;
+        run += x;
+    }
+}
+
+// out[i, j] = outg[j / KC][i][j % KC] + R^T Z[j] - R_i 1^T Z[j]  (atomic mode)
+template <dm_dtype DT, int KC>
+__global__ void __launch_bounds__(kThreads)
+l1_finalize_kernel(const typename Types<DT>::Acc* __restrict__ outg,
+                   const typename Types<DT>::Acc* __restrict__ R,
+                   const typename Types<DT>::Wide* __restrict__ res, int64_t n, int k,
+                   typename Types<DT>::Out* __restrict__ out, int64_t ldo) {
+    using Acc = typename Types<DT>::Acc;
+    using Out = typename Types<DT>::Out;
+    const int64_t total = n * k;
+    for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * kThreads) {
+        const int64_t i = idx / k;
+        const int j = (int)(idx - i * k);
+        const Acc v = __ldcs(outg + ((int64_t)(j / KC) * n + i) * KC + (j % KC));
+        const Acc rz = (Acc)res[j], uz = (Acc)res[k + j];
+        out[i * ldo + j] = (Out)(v + (rz - R[i] * uz));
+    }
+}
+
+// ---------------------------------------------------------------- prologue
+// R^T Z and 1^T Z (per-block partials) and the group-major copy Zg of Z.
+// Thread (row group rg, padded column j < JW = G*KC); rows rg, rg + RGS, ...
+template <dm_dtype DT, int KC>
+__global__ void __launch_bounds__(kThreads)
+l1_prologue_kernel(const typename Types<DT>::V* __restrict__ Z, int64_t n, int k, int64_t ldz,
+                   const typename Types<DT>::Acc* __restrict__ R,
+                   typename Types<DT>::V* __restrict__ Zg, int JW,
+                   typename Types<DT>::Wide* __restrict__ partial, int64_t rows_per_block) {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Wide = typename Types<DT>::Wide;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Wide* red = reinterpret_cast<Wide*>(smem_raw);      // [RGS][2][JC]
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min64(n, r0 + rows_per_block);
+    const int JC = JW < kThreads ? JW : kThreads;          // columns per sweep
+    const int RGS = kThreads / JC;
+    const int rg = threadIdx.x / JC, jl = threadIdx.x % JC;
+    for (int jb = 0; jb < JW; jb += JC) {
+        const int j = jb + jl;
+        const bool active = rg < RGS && j < JW;
+        const int g = j / KC, q = j % KC;
+        Wide wu = 0, wr = 0;
+        if (active) {
+            Acc cu = 0, cr = 0;
+            int cnt = 0;
+            for (int64_t r = r0 + rg; r < r1; r += RGS) {
+                const V z = j < k ? Z[r * ldz + j] : V(0);
+                Zg[((int64_t)g * n + r) * KC + q] = z;
+                cu += (Acc)z;
+                cr += R[r] * (Acc)z;
+                if (++cnt == 64) { wu += (Wide)cu; wr += (Wide)cr; cu = 0; cr = 0; cnt = 0; }
+            }
+            wu += (Wide)cu;
+            wr += (Wide)cr;
+        }
+        __syncthreads();
+        if (rg < RGS) { red[(rg * 2 + 0) * JC + jl] = wu; red[(rg * 2 + 1) * JC + jl] = wr; }
+        __syncthreads();
+        if (rg == 0 && j < k) {
+            Wide tu = 0, tr = 0;
+            for (int t = 0; t < RGS; ++t) { tu += red[(t * 2) * JC + jl]; tr += red[(t * 2 + 1) * JC + jl]; }
+            Wide* out = partial + (int64_t)blockIdx.x * 2 * k;
+            out[j] = tr;       // R^T Z
+            out[k + j] = tu;   // 1^T Z
+        }
+    }
+}
+
+template <class Wide>
+__global__ void l1_prologue_finalize(const Wide* __restrict__ partial, int blocks, int k2,
+                                     Wide* __restrict__ res) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k2) return;
+    Wide t = 0;
+    for (int b = 0; b < blocks; ++b) t += partial[(int64_t)b * k2 + i];
+    res[i] = t;
+}
+
+int full_kc(dm_dtype t) { return t == DM_F64 ? 4 : 8; }
+
+int pick_kc(dm_dtype t, int64_t k) {
+    const int full = full_kc(t);
+    if (k >= full) return full;
     int kc = 1;
     while (kc < k) kc <<= 1;
     return kc;
@@ -373,11 +676,10 @@ int pick_kc(int64_t k) {
 template <dm_dtype DT>
 int tile_elems_rt(int kc) {
     switch (kc) {
-        case 1: return tile_elems<DT, 1>();
-        case 2: return tile_elems<DT, 2>();
-        case 4: return tile_elems<DT, 4>();
-        case 8: return tile_elems<DT, 8>();
-        default: return tile_elems<DT, 16>();
+        case 1: return QCfg<DT, 1>::TILE_E;
+        case 2: return QCfg<DT, 2>::TILE_E;
+        case 4: return QCfg<DT, 4>::TILE_E;
+        default: return QCfg<DT, DT == DM_F64 ? 4 : 8>::TILE_E;
     }
 }
 
@@ -389,106 +691,186 @@ int tile_elems_dt(dm_dtype t, int kc) {
     }
 }
 
+int prologue_blocks(int64_t n, int num_sms) {
+    const int64_t want = (n + 2047) / 2048;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * (int64_t)std::max(num_sms, 1)));
+}
+
 struct ScratchLayout {
-    size_t counter, done, flags, agg, inc, memset_bytes, total;
+    int kc; int64_t G, T;
+    size_t counter, done, memset_bytes, pre, partial, res, zg, outg, total;
 };
 
-ScratchLayout scratch_layout(dm_dtype t, int64_t n, int64_t d, int64_t k) {
-    const int kc = pick_kc(k);
-    const int64_t G = (k + kc - 1) / kc;
-    const int64_t T = (n + tile_elems_dt(t, kc) - 1) / tile_elems_dt(t, kc);
-    const size_t wide = 8;
+// Every region starts on a 256-byte boundary (the arena itself comes from
+// cudaMalloc): the 256-bit row loads from Zg need 32-byte alignment.
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+ScratchLayout scratch_layout(dm_dtype t, int64_t n, int64_t d, int64_t k, int num_sms) {
     ScratchLayout L;
+    L.kc = pick_kc(t, k);
+    L.G = (k + L.kc - 1) / L.kc;
+    const int64_t tile = tile_elems_dt(t, L.kc);
+    L.T = (n + tile - 1) / tile;
+    const size_t wide = 8, vsz = dtype_size(t), acc = (t == DM_F32) ? 4 : 8;
+    const size_t tiles = (size_t)(L.G * d * L.T);
     L.counter = 0;
     L.done = 16;
-    L.flags = align16(L.done + 4 * (size_t)(G * d));
-    L.memset_bytes = align16(L.flags + 4 * (size_t)(G * d * T));
-    L.agg = L.memset_bytes;
-    L.inc = align16(L.agg + wide * (size_t)(G * d * T) * 2 * kc);
-    L.total = align16(L.inc + wide * (size_t)(G * d * T) * 2 * kc);
+    L.memset_bytes = align256(L.done + 4 * (size_t)(L.G * d));
+    L.pre = L.memset_bytes;
+    L.partial = align256(L.pre + wide * tiles * 2 * L.kc);
+    L.res = align256(L.partial + wide * (size_t)prologue_blocks(n, num_sms) * 2 * k);
+    L.zg = align256(L.res + wide * 2 * (size_t)k);
+    L.outg = align256(L.zg + vsz * (size_t)(L.G * n * L.kc));
+    L.total = align256(L.outg + acc * (size_t)(L.G * n * L.kc));
     return L;
 }
 
 template <dm_dtype DT, int KC>
-cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches) {
+cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, int stage) {
     using Cfg = QCfg<DT, KC>;
     using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
-    const ScratchLayout L = scratch_layout(a.dtype, a.n, a.d, a.k);
+    const ScratchLayout L = scratch_layout(a.dtype, a.n, a.d, a.k, a.num_sms);
     unsigned char* sc = static_cast<unsigned char*>(a.scratch);
-    cudaError_t e = cudaMemsetAsync(sc, 0, L.memset_bytes, st);
-    if (e != cudaSuccess) return e;
+    // 256-bit loads of Zg rows and 16-byte accesses to outg need aligned bases.
+    if ((reinterpret_cast<uintptr_t>(sc + L.zg) % 32) != 0 ||
+        (reinterpret_cast<uintptr_t>(sc + L.outg) % 32) != 0)
+        return cudaErrorMisalignedAddress;
+    cudaError_t e;
+    const bool atomic = !a.deterministic;
+    if (stage == 2) {   // finalize (L2-reduction mode only)
+        if (!atomic) return cudaSuccess;
+        const int64_t total = a.n * a.k;
+        const int64_t fb = std::min<int64_t>((total + kThreads - 1) / kThreads, 8 * (int64_t)a.num_sms);
+        l1_finalize_kernel<DT, KC><<<(unsigned)std::max<int64_t>(fb, 1), kThreads, 0, st>>>(
+            reinterpret_cast<const Acc*>(sc + L.outg), static_cast<const Acc*>(a.R),
+            reinterpret_cast<const Wide*>(sc + L.res), a.n, (int)a.k,
+            static_cast<typename Types<DT>::Out*>(a.out), a.ldo);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+        return cudaSuccess;
+    }
+    if (stage == 0) {
+        const int blocks = prologue_blocks(a.n, a.num_sms);
+        const int64_t rpb = (a.n + blocks - 1) / blocks;
+        const int JW = (int)(L.G * KC);
+        const int JC = JW < kThreads ? JW : kThreads;
+        const size_t smem = sizeof(Wide) * 2 * (size_t)(kThreads / JC) * JC;
+        auto kern = l1_prologue_kernel<DT, KC>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<blocks, kThreads, smem, st>>>(
+            static_cast<const V*>(a.Z), a.n, (int)a.k, a.ldz, static_cast<const Acc*>(a.R),
+            reinterpret_cast<V*>(sc + L.zg), JW, reinterpret_cast<Wide*>(sc + L.partial), rpb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int k2 = (int)(2 * a.k);
+        l1_prologue_finalize<Wide><<<(k2 + 127) / 128, 128, 0, st>>>(
+            reinterpret_cast<const Wide*>(sc + L.partial), blocks, k2,
+            reinterpret_cast<Wide*>(sc + L.res));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 2;
+        return cudaSuccess;
+    }
 
-    QParams<V, typename Types<DT>::Acc, Wide> p;
+    if (stage == 3) {   // tile aggregates + per-segment exclusive scan
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, l1_aggregate_kernel<DT, KC>, kThreads, 0);
+        if (e != cudaSuccess) return e;
+        const int64_t warps = L.G * a.d * L.T;
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(
+            (warps + kWarps - 1) / kWarps, (int64_t)std::max(occ, 1) * a.num_sms));
+        l1_aggregate_kernel<DT, KC><<<(unsigned)blocks, kThreads, 0, st>>>(
+            static_cast<const V*>(a.xs), a.perm, a.n, (int)a.d, reinterpret_cast<const V*>(sc + L.zg),
+            static_cast<const V*>(a.mu), a.mu_stride, reinterpret_cast<Wide*>(sc + L.pre), (int)L.T,
+            (int)L.G, a.err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        l1_tile_scan_kernel<Wide><<<(unsigned)(L.G * a.d), kThreads, 0, st>>>(
+            reinterpret_cast<Wide*>(sc + L.pre), (int)L.T, 2 * KC);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *launches += 2;
+        return cudaSuccess;
+    }
+
+    e = cudaMemsetAsync(sc, 0, L.memset_bytes, st);
+    if (e != cudaSuccess) return e;
+    if (atomic) {
+        e = cudaMemsetAsync(sc + L.outg, 0, sizeof(Acc) * (size_t)(L.G * a.n * KC), st);
+        if (e != cudaSuccess) return e;
+    }
+    QParams<V, Acc, Wide> p;
     p.xs = static_cast<const V*>(a.xs);
-    p.R = static_cast<const typename Types<DT>::Acc*>(a.R);
     p.perm = a.perm;
     p.n = a.n;
     p.d = (int)a.d;
-    p.Z = static_cast<const V*>(a.Z);
-    p.ldz = a.ldz;
+    p.R = static_cast<const Acc*>(a.R);
+    p.Zg = reinterpret_cast<const V*>(sc + L.zg);
     p.k = (int)a.k;
-    p.res = static_cast<const Wide*>(a.res);
+    p.res = reinterpret_cast<const Wide*>(sc + L.res);
     p.mu = static_cast<const V*>(a.mu);
     p.mu_stride = a.mu_stride;
+    p.outg = reinterpret_cast<Acc*>(sc + L.outg);
     p.out = a.out;
     p.ldo = a.ldo;
     p.counter = reinterpret_cast<uint32_t*>(sc + L.counter);
     p.done = reinterpret_cast<uint32_t*>(sc + L.done);
-    p.flags = reinterpret_cast<uint32_t*>(sc + L.flags);
-    p.agg = reinterpret_cast<Wide*>(sc + L.agg);
-    p.inc = reinterpret_cast<Wide*>(sc + L.inc);
+    p.pre = reinterpret_cast<const Wide*>(sc + L.pre);
     p.err = a.err;
-    p.T = (int)((a.n + Cfg::TILE_E - 1) / Cfg::TILE_E);
-    p.G = (int)((a.k + KC - 1) / KC);
-    // Widest cp.async the query rows allow.
-    p.vw = (int)sizeof(V);
-    const size_t rowb = (size_t)KC * sizeof(V);
-    for (int cand : {16, 8}) {
-        if (rowb % cand == 0 && (reinterpret_cast<uintptr_t>(a.Z) % cand) == 0 &&
-            (a.ldz * sizeof(V)) % cand == 0) {
-            p.vw = cand;
-            break;
-        }
-    }
+    p.T = (int)L.T;
+    p.G = (int)L.G;
 
-    auto kern = l1_query_kernel<DT, KC>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem);
-    if (e != cudaSuccess) return e;
+    auto kern = atomic ? l1_query_kernel<DT, KC, kAtomic> : l1_query_kernel<DT, KC, kOrdered>;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, Cfg::smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0);
     if (e != cudaSuccess) return e;
     const int64_t total_tiles = (int64_t)p.G * p.d * p.T;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(total_tiles, (int64_t)std::max(occ, 1) * a.num_sms));
-    kern<<<(unsigned)blocks, kThreads, Cfg::smem, st>>>(p);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) ++*launches;
-    return e;
+    const int64_t blocks = std::max<int64_t>(
+        1, std::min<int64_t>(total_tiles, (int64_t)std::max(occ, 1) * a.num_sms));
+    kern<<<(unsigned)blocks, kThreads, 0, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*launches;
+    return cudaSuccess;
 }
 
 template <dm_dtype DT>
-cudaError_t launch_dt(const L1QueryArgs& a, cudaStream_t st, int64_t* launches) {
-    switch (pick_kc(a.k)) {
-        case 1: return launch_kc<DT, 1>(a, st, launches);
-        case 2: return launch_kc<DT, 2>(a, st, launches);
-        case 4: return launch_kc<DT, 4>(a, st, launches);
-        case 8: return launch_kc<DT, 8>(a, st, launches);
-        default: return launch_kc<DT, 16>(a, st, launches);
+cudaError_t launch_dt(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, int stage) {
+    constexpr int FULL = DT == DM_F64 ? 4 : 8;
+    switch (pick_kc(a.dtype, a.k)) {
+        case 1: return launch_kc<DT, 1>(a, st, launches, stage);
+        case 2: return launch_kc<DT, 2>(a, st, launches, stage);
+        case 4: return launch_kc<DT, 4>(a, st, launches, stage);
+        default: return launch_kc<DT, FULL>(a, st, launches, stage);
+    }
+}
+
+cudaError_t launch_any(const L1QueryArgs& a, cudaStream_t s, int64_t* launches, int stage) {
+    switch (a.dtype) {
+        case DM_F32: return launch_dt<DM_F32>(a, s, launches, stage);
+        case DM_F64: return launch_dt<DM_F64>(a, s, launches, stage);
+        default: return launch_dt<DM_I32>(a, s, launches, stage);
     }
 }
 
 }  // namespace
 
-size_t l1_query_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k) {
-    return scratch_layout(t, n, d, k).total;
+size_t l1_query_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k, int num_sms) {
+    return scratch_layout(t, n, d, k, num_sms).total;
+}
+
+cudaError_t l1_prologue_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches) {
+    return launch_any(a, s, launches, 0);
 }
 
 cudaError_t l1_query_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches) {
-    switch (a.dtype) {
-        case DM_F32: return launch_dt<DM_F32>(a, s, launches);
-        case DM_F64: return launch_dt<DM_F64>(a, s, launches);
-        default: return launch_dt<DM_I32>(a, s, launches);
-    }
+    return launch_any(a, s, launches, 1);
+}
+
+cudaError_t l1_finalize_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches) {
+    return launch_any(a, s, launches, 2);
+}
+
+cudaError_t l1_aggregate_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches) {
+    return launch_any(a, s, launches, 3);
 }
 
 }  // namespace dm

@@ -84,6 +84,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 }
 
 // ------------------------------------------------------------ keygen + hist
+// CTA = RB rows x DB columns of X.  All loads of a thread are issued first
+// (RB*DB/256 values in registers), the keys go to a padded shared tile, then
+// each warp histograms one column's keys into a private shared histogram
+// (no contention between warps; lanes that share a digit in the two highest
+// digit positions -- where sign and exponent bits make digits collide -- add
+// once through a warp match), and finally the tile is written column-major
+// and the histograms are added to the global counts.
 template <dm_dtype DT>
 struct KeygenCfg {
     using Ty = Types<DT>;
@@ -92,7 +99,10 @@ struct KeygenCfg {
     static constexpr int DB = sizeof(Key) == 4 ? 8 : 4;  // columns per CTA
     static constexpr int RB = 1024;                      // rows per CTA
     static constexpr int TS = RB + 8;                    // padded row stride of the tile
-    static constexpr size_t smem = (size_t)DB * P * kRadix * 4 + (size_t)DB * TS * sizeof(Key);
+    static constexpr int WPC = kWarps / DB;              // warps per column
+    static constexpr int PER = RB * DB / kThreads;       // loads per thread
+    static constexpr size_t hist_bytes = (size_t)kWarps * P * kRadix * 4;
+    static constexpr size_t smem = hist_bytes + (size_t)DB * TS * sizeof(Key);
 };
 
 template <dm_dtype DT>
@@ -103,51 +113,69 @@ keygen_hist_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64
     using Cfg = KeygenCfg<DT>;
     using Key = typename Cfg::Key;
     using V = typename Types<DT>::V;
-    constexpr int P = Cfg::P, DB = Cfg::DB, RB = Cfg::RB, TS = Cfg::TS;
+    constexpr int P = Cfg::P, DB = Cfg::DB, RB = Cfg::RB, TS = Cfg::TS, PER = Cfg::PER;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t* h = reinterpret_cast<uint32_t*>(smem_raw);                  // [DB][P][256]
-    Key* tile = reinterpret_cast<Key*>(smem_raw + (size_t)DB * P * kRadix * 4);  // [DB][TS]
+    uint32_t* h = reinterpret_cast<uint32_t*>(smem_raw);                    // [warp][P][256]
+    Key* tile = reinterpret_cast<Key*>(smem_raw + Cfg::hist_bytes);         // [DB][TS]
 
     const int64_t row0 = (int64_t)blockIdx.x * RB;
     const int64_t c0 = (int64_t)blockIdx.y * DB;
     const int nr = (int)min64(RB, n - row0);
     const int nd = (int)min64(DB, d - c0);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    for (int i = threadIdx.x; i < DB * P * kRadix; i += kThreads) h[i] = 0;
-    __syncthreads();
+    for (int i = threadIdx.x; i < kWarps * P * kRadix; i += kThreads) h[i] = 0;
 
-    bool bad = false;
-    const int c = threadIdx.x % DB;
-    for (int r = threadIdx.x / DB; r < RB; r += kThreads / DB) {
-        const bool ok = (r < nr) && (c < nd);
-        Key key = 0;
-        if (ok) {
-            V v = X[(row0 + r) * ldx + c0 + c];
-            bad |= !finite_val(v);
-            key = to_key(v);
-            tile[c * TS + r] = key;
-        }
-        // Warp-aggregated histogram updates: lanes with the same (column,
-        // digit) pair add once.
+    V v[PER];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const uint32_t digit = (uint32_t)(key >> (8 * p)) & 0xffu;
-            const uint32_t tag = ok ? (uint32_t)(c * kRadix + digit) : 0xffffffffu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, tag);
-            if (ok && lane == __ffs(peers) - 1)
-                atomicAdd(&h[(c * P + p) * kRadix + digit], (uint32_t)__popc(peers));
-        }
+    for (int j = 0; j < PER; ++j) {
+        const int idx = threadIdx.x + j * kThreads;
+        const int r = idx / DB, c = idx % DB;
+        v[j] = (r < nr && c < nd) ? X[(row0 + r) * ldx + c0 + c] : V(0);
+    }
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int idx = threadIdx.x + j * kThreads;
+        const int r = idx / DB, c = idx % DB;
+        if (r < nr && c < nd) bad |= !finite_val(v[j]);
+        tile[c * TS + r] = to_key(v[j]);
     }
     if (bad) set_error(err, kErrNonfinite);
+    __syncthreads();
+
+    {
+        const int c = warp % DB, part = warp / DB;
+        uint32_t* hw = h + warp * P * kRadix;
+        const int rows_per = RB / Cfg::WPC;
+        const int rb = part * rows_per;
+        const bool colok = c < nd;
+        for (int r = rb + lane; r < rb + rows_per; r += 32) {
+            const bool ok = colok && r < nr;
+            const Key key = ok ? tile[c * TS + r] : Key(0);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const uint32_t digit = (uint32_t)(key >> (8 * q)) & 0xffu;
+                if (q >= P - 2) {
+                    const uint32_t peers = __match_any_sync(0xffffffffu, ok ? digit : 0x100u);
+                    if (ok && lane == __ffs(peers) - 1) atomicAdd(&hw[q * kRadix + digit], (uint32_t)__popc(peers));
+                } else if (ok) {
+                    atomicAdd(&hw[q * kRadix + digit], 1u);
+                }
+            }
+        }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < nd * RB; i += kThreads) {
         const int cc = i / RB, r = i % RB;
         if (r < nr) keys[(c0 + cc) * n + row0 + r] = tile[cc * TS + r];
     }
     for (int i = threadIdx.x; i < nd * P * kRadix; i += kThreads) {
-        const uint32_t v = h[i];
-        if (v) atomicAdd(&hist[c0 * P * kRadix + i], v);
+        const int c = i / (P * kRadix), rest = i % (P * kRadix);
+        uint32_t tot = 0;
+#pragma unroll
+        for (int part = 0; part < Cfg::WPC; ++part) tot += h[(part * DB + c) * P * kRadix + rest];
+        if (tot) atomicAdd(&hist[(c0 + c) * P * kRadix + rest], tot);
     }
 }
 
@@ -172,7 +200,7 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
                 typename Types<DT>::V* __restrict__ sorted_out,  // last pass only
                 int32_t* __restrict__ perm_out,                   // last pass only
                 const uint32_t* __restrict__ hist, uint32_t* lookback, uint32_t* counter,
-                int64_t n, int pass, int P, int T, int first, int last, uint32_t* err) {
+                int64_t n, int D, int pass, int P, int T, int first, int last, uint32_t* err) {
     using Key = typename Types<DT>::Key;
     using V = typename Types<DT>::V;
     constexpr int ITEMS = PassCfg<DT>::ITEMS, TILE = PassCfg<DT>::TILE;
@@ -189,9 +217,12 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     for (int i = tid; i < kWarps * kRadix; i += kThreads) (&wcount[0][0])[i] = 0;
     __syncthreads();
+    // Claims interleave the columns (column fastest), so the look-back
+    // chains of all d columns advance side by side and each chain has only a
+    // few tiles in flight.
     const uint32_t g = s_tile;
-    const int64_t c = g / (uint32_t)T;
-    const int t = (int)(g % (uint32_t)T);
+    const int64_t c = g % (uint32_t)D;
+    const int t = (int)(g / (uint32_t)D);
     const int64_t seg = c * n;
     const int64_t tile0 = (int64_t)t * TILE;
     const int shift = 8 * pass;
@@ -331,8 +362,8 @@ cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, 
         int32_t* vout = vbuf[i & 1];
         onesweep_kernel<DT><<<(unsigned)(a.d * T), kThreads, 0, s>>>(
             kin, vin, kout, vout, static_cast<V*>(a.sorted_out), a.perm_out, a.hist,
-            a.lookback + i * lb_stride, a.counters + i, a.n, pass_list[i], P, T, first, last,
-            a.err);
+            a.lookback + i * lb_stride, a.counters + i, a.n, (int)a.d, pass_list[i], P, T, first,
+            last, a.err);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ++*launches;

@@ -2,19 +2,20 @@
 //
 // reduce  -- the shifted contraction of the query block with the points,
 //              W[c,j] = sum_i (x_ic - mu_c) Z[i,j],  u[j] = sum_i Z[i,j],
-//              v[j]   = sum_i s_i Z[i,j]             (squared l2 only),
+//              v[j]   = sum_i s_i Z[i,j],  s_i = ||x_i - mu||^2  (squared l2),
 //            i.e. [X - mu, 1, s]^T Z, a (d+2) x k result from a reduction of
-//            length n.  The l1 query uses u and W as the totals T_z and T_xz
-//            of its prefix sums; the squared-l2 query uses u, v and W as
-//            S1, S2 and v of the p = 2 query (Appendix A).
-//            Each CTA accumulates a contiguous row range (FP32 or exact int64
-//            within a 64-row chunk, the chunk sums added in the Wide type),
-//            writes one partial; a finalize kernel adds the partials in a
-//            fixed order (deterministic for a given device).
-// l2prep  -- column means mu (the frame shift; the product is translation
-//            invariant) and s_i = ||x_i - mu||^2.
-// l2apply -- out_i = s_i u + v - 2 (x_i - mu) . W  (Appendix A, in the
-//            mu-shifted frame of the Gram decomposition of Section 1.2).
+//            length n: u, v and W are S1, S2 and v of the p = 2 query of
+//            Appendix A (in the mu-shifted frame; the product is translation
+//            invariant).  Each CTA reduces a contiguous row range: rows arrive
+//            in chunks through a double-buffered cp.async pipeline, each thread
+//            owns a 2 x 4 block of the result (FP32 or exact int64 within a
+//            chunk, chunk sums added in the Wide type), the CTA writes one
+//            partial and a finalize kernel adds the partials in a fixed order.
+//            With s omitted the same kernel gives u and W alone.
+// l2prep  -- column means mu (the frame shift), FP64 sums, fixed order.
+// l2apply -- out_i = s_i u + v - 2 (x_i - mu) . W  (the p = 2 query, Appendix
+//            A), s_i recomputed from the staged row with the same code as in
+//            the reduce.
 // These kernels are HBM-bound at the shapes of interest (d, k <= 64): the
 // contraction does 2(d+2)k flops per (4d + 4k) bytes read, below the FP32
 // ALU ridge, so they run on the CUDA cores.
@@ -46,13 +47,47 @@ __device__ __forceinline__ float fma_acc<float>(float a, float b, float c) { ret
 template <>
 __device__ __forceinline__ double fma_acc<double>(double a, double b, double c) { return fma(a, b, c); }
 
-// Shared-memory layout of one staged chunk: xh[kChunk][D2P] (the augmented
-// row [x - mu, 1, s]) and zc[kChunk][KP].
-template <dm_dtype DT, class XT>
+template <int B>
+__device__ __forceinline__ void cp_async(void* s, const void* g, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    if constexpr (B == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(sa), "l"(g), "r"(valid ? 8 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(sa), "l"(g), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// s = ||x - mu||^2 of one staged row (x already shifted), one fixed order.
+template <class Acc>
+__device__ __forceinline__ Acc row_sqnorm(const Acc* xrow, int d) {
+    Acc acc = 0;
+    for (int c = 0; c < d; ++c) acc = fma_acc(xrow[c], xrow[c], acc);
+    return acc;
+}
+
+// Stage rows [base, base + nr) of X and Z (raw element types) into one buffer.
+template <class XT, class V>
+__device__ __forceinline__ void stage_chunk(XT* xr, V* zr, const XT* X, int64_t ldx, int d,
+                                            const V* Z, int64_t ldz, int k, int64_t base, int nr) {
+    for (int i = threadIdx.x; i < kChunk * d; i += kThreads) {
+        const int r = i / d, c = i % d;
+        const bool ok = r < nr;
+        cp_async<sizeof(XT)>(xr + r * d + c, X + (ok ? (base + r) * ldx + c : 0), ok);
+    }
+    for (int i = threadIdx.x; i < kChunk * k; i += kThreads) {
+        const int r = i / k, j = i % k;
+        const bool ok = r < nr;
+        cp_async<sizeof(V)>(zr + r * k + j, Z + (ok ? (base + r) * ldz + j : 0), ok);
+    }
+    cp_commit();
+}
+
+template <dm_dtype DT, class XT, int MAXOB>
 __global__ void __launch_bounds__(kThreads)
 reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
-              const typename Types<DT>::V* __restrict__ mu, int64_t mu_stride,
-              const typename Types<DT>::Acc* __restrict__ s,
+              const typename Types<DT>::V* __restrict__ mu, int64_t mu_stride, int with_s,
               const typename Types<DT>::V* __restrict__ Z, int k, int64_t ldz,
               typename Types<DT>::Wide* __restrict__ partial, int64_t rows_per_block) {
     using V = typename Types<DT>::V;
@@ -61,12 +96,20 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int D2 = d + 2;
     const int D2P = D2 + 1, KP = k + 1;
-    Acc* mu_s = reinterpret_cast<Acc*>(smem_raw);
-    Acc* xh = mu_s + d;
-    Acc* zc = xh + kChunk * D2P;
-    size_t red_off = sizeof(Acc) * ((size_t)d + (size_t)kChunk * D2P + (size_t)kChunk * KP);
-    red_off = (red_off + 15) & ~size_t(15);
-    Wide* red = reinterpret_cast<Wide*>(smem_raw + red_off);   // final combine
+    // layout: raw buffers [2][kChunk*d] XT, [2][kChunk*k] V; xh [kChunk][D2P] Acc;
+    //         zc [kChunk][KP] Acc; mu_s [d] Acc; red [D2*k] Wide
+    size_t off = 0;
+    XT* xraw = reinterpret_cast<XT*>(smem_raw + off);
+    off += ((2 * (size_t)kChunk * d * sizeof(XT)) + 15) & ~size_t(15);
+    V* zraw = reinterpret_cast<V*>(smem_raw + off);
+    off += ((2 * (size_t)kChunk * k * sizeof(V)) + 15) & ~size_t(15);
+    Acc* xh = reinterpret_cast<Acc*>(smem_raw + off);
+    off += (((size_t)kChunk * D2P * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* zc = reinterpret_cast<Acc*>(smem_raw + off);
+    off += (((size_t)kChunk * KP * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* mu_s = reinterpret_cast<Acc*>(smem_raw + off);
+    off += (((size_t)d * sizeof(Acc)) + 15) & ~size_t(15);
+    Wide* red = reinterpret_cast<Wide*>(smem_raw + off);
 
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min64(n, r0 + rows_per_block);
@@ -76,9 +119,8 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
     const int OB = OBc * OBj;
     const int RG = max(1, kThreads / OB);          // row groups
     const int ob_per_thread = (OB + kThreads - 1) / kThreads;
+    const int my_rg = (OB >= kThreads) ? 0 : threadIdx.x / OB;
 
-    // Each thread owns up to ob_per_thread output blocks of RC x RJ.
-    constexpr int MAXOB = 4;
     Wide wacc[MAXOB][RC][RJ];
 #pragma unroll
     for (int b = 0; b < MAXOB; ++b)
@@ -87,25 +129,37 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
 #pragma unroll
             for (int q = 0; q < RJ; ++q) wacc[b][a][q] = 0;
 
-    const int my_rg = (OB >= kThreads) ? 0 : threadIdx.x / OB;
-    __syncthreads();
-
-    for (int64_t base = r0; base < r1; base += kChunk) {
+    const int nchunks = (int)((r1 - r0 + kChunk - 1) / kChunk);
+    if (nchunks > 0)
+        stage_chunk(xraw, zraw, X, ldx, d, Z, ldz, k, r0, (int)min64(kChunk, r1 - r0));
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int64_t base = r0 + (int64_t)ch * kChunk;
         const int nr = (int)min64(kChunk, r1 - base);
+        const int buf = ch & 1;
+        if (ch + 1 < nchunks) {
+            const int64_t nb = base + kChunk;
+            stage_chunk(xraw + (buf ^ 1) * kChunk * d, zraw + (buf ^ 1) * kChunk * k, X, ldx, d, Z,
+                        ldz, k, nb, (int)min64(kChunk, r1 - nb));
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
         __syncthreads();
-        for (int i = threadIdx.x; i < kChunk * D2; i += kThreads) {
-            const int r = i / D2, c = i % D2;
-            Acc v = 0;
-            if (r < nr) {
-                if (c < d) v = to_acc(X[(base + r) * ldx + c], Acc()) - mu_s[c];
-                else if (c == d) v = 1;
-                else v = s ? s[base + r] : Acc(0);
-            }
-            xh[r * D2P + c] = v;
+        const XT* xb = xraw + buf * kChunk * d;
+        const V* zb = zraw + buf * kChunk * k;
+        for (int i = threadIdx.x; i < kChunk * d; i += kThreads) {
+            const int r = i / d, c = i % d;
+            xh[r * D2P + c] = (r < nr) ? to_acc(xb[i], Acc()) - mu_s[c] : Acc(0);
         }
         for (int i = threadIdx.x; i < kChunk * k; i += kThreads) {
             const int r = i / k, j = i % k;
-            zc[r * KP + j] = (r < nr) ? to_acc(Z[(base + r) * ldz + j], Acc()) : Acc(0);
+            zc[r * KP + j] = (r < nr) ? to_acc(zb[i], Acc()) : Acc(0);
+        }
+        __syncthreads();
+        if (threadIdx.x < kChunk) {
+            const int r = threadIdx.x;
+            xh[r * D2P + d] = r < nr ? Acc(1) : Acc(0);
+            xh[r * D2P + d + 1] = (with_s && r < nr) ? row_sqnorm(xh + r * D2P, d) : Acc(0);
         }
         __syncthreads();
 #pragma unroll
@@ -135,8 +189,8 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
 #pragma unroll
                 for (int q = 0; q < RJ; ++q) wacc[b][a][q] += (Wide)acc[a][q];
         }
+        __syncthreads();
     }
-    __syncthreads();
 
     // Combine the row groups in a fixed order and write this block's partial.
     const int total = D2 * k;
@@ -186,11 +240,14 @@ colsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int
               typename Types<DT>::Wide* __restrict__ partial, int64_t rows_per_block,
               uint32_t* err) {
     using Wide = typename Types<DT>::Wide;
+    using V = typename Types<DT>::V;
+    constexpr int U = 8;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min64(n, r0 + rows_per_block);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Wide* red = reinterpret_cast<Wide*>(smem_raw);
-    // Thread (column c0, row group g) walks rows g, g + rg, ... of its range.
+    // Thread (column c0, row group g) walks rows g, g + rg, ... of its range,
+    // U rows per step with all U loads issued first.
     const int cols = min(d, kThreads);
     const int rg = kThreads / cols;
     const int c0 = threadIdx.x % cols, g = threadIdx.x / cols;
@@ -199,10 +256,18 @@ colsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int
         const int c = cb + c0;
         Wide acc = 0;
         if (g < rg && c < d) {
-            for (int64_t r = r0 + g; r < r1; r += rg) {
-                const auto v = X[r * ldx + c];
-                bad |= !finite_val(v);
-                acc += (Wide)v;
+            for (int64_t r = r0 + g; r < r1; r += (int64_t)rg * U) {
+                V v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t rr = r + (int64_t)u * rg;
+                    v[u] = rr < r1 ? X[rr * ldx + c] : V(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    bad |= !finite_val(v[u]);
+                    acc += (Wide)v[u];
+                }
             }
         }
         red[threadIdx.x] = acc;
@@ -230,107 +295,138 @@ __global__ void mean_finalize_kernel(const typename Types<DT>::Wide* __restrict_
     mu[c] = (V)(t / (Wide)n);
 }
 
-template <dm_dtype DT>
-__global__ void __launch_bounds__(kThreads)
-sqnorm_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int64_t ldx,
-              const typename Types<DT>::V* __restrict__ mu, typename Types<DT>::Acc* __restrict__ s) {
-    using Acc = typename Types<DT>::Acc;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    Acc acc = 0;
-    for (int c = 0; c < d; ++c) {
-        const Acc t = to_acc(X[i * ldx + c], Acc()) - to_acc(mu[c], Acc());
-        acc = fma_acc(t, t, acc);
-    }
-    s[i] = acc;
-}
-
 // ----------------------------------------------------------------- l2apply
-// Block: kApplyRows rows x all k columns.  Thread (row pair, column quad).
+// Persistent CTAs over tiles of kApplyRows rows; each tile of X arrives by
+// cp.async into a double buffer while the previous tile is computed.  Thread
+// (row pair, column quad) accumulates s_i u + v - 2 (x_i - mu) . W.
 constexpr int kApplyRows = 128;
+
 template <dm_dtype DT>
 __global__ void __launch_bounds__(kThreads)
 l2apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int64_t ldx,
-               const typename Types<DT>::V* __restrict__ mu, const typename Types<DT>::Acc* __restrict__ s,
+               const typename Types<DT>::V* __restrict__ mu,
                const typename Types<DT>::Wide* __restrict__ res, int k,
                typename Types<DT>::Out* __restrict__ out, int64_t ldo) {
+    using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
+    using Out = typename Types<DT>::Out;
     constexpr int R = kApplyRows;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int DP = d + 1;
-    Acc* Wm2 = reinterpret_cast<Acc*>(smem_raw);   // -2 W, d x k
-    Acc* uv = Wm2 + d * k;                          // u (k), v (k)
-    Acc* xt = uv + 2 * k;                           // R x DP shifted rows
-    Acc* mu_s = xt + R * DP;
+    size_t off = 0;
+    V* xraw = reinterpret_cast<V*>(smem_raw);                      // [2][R*d]
+    off += ((2 * (size_t)R * d * sizeof(V)) + 15) & ~size_t(15);
+    Acc* Wm2 = reinterpret_cast<Acc*>(smem_raw + off);             // -2 W, d x k
+    off += (((size_t)d * k * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* uv = reinterpret_cast<Acc*>(smem_raw + off);              // u (k), v (k)
+    off += (((size_t)2 * k * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* xt = reinterpret_cast<Acc*>(smem_raw + off);              // R x DP shifted rows
+    off += (((size_t)R * DP * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* mu_s = reinterpret_cast<Acc*>(smem_raw + off);
+    off += (((size_t)d * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* s_s = reinterpret_cast<Acc*>(smem_raw + off);             // R
 
     for (int i = threadIdx.x; i < d * k; i += kThreads) Wm2[i] = (Acc)(-2 * res[i]);
     for (int i = threadIdx.x; i < 2 * k; i += kThreads) uv[i] = (Acc)res[d * k + i];
     for (int c = threadIdx.x; c < d; c += kThreads) mu_s[c] = to_acc(mu[c], Acc());
-    __syncthreads();
 
-    const int64_t row0 = (int64_t)blockIdx.x * R;
-    const int nr = (int)min64(R, n - row0);
-    for (int i = threadIdx.x; i < R * d; i += kThreads) {
-        const int r = i / d, c = i % d;
-        xt[r * DP + c] = (r < nr) ? to_acc(X[(row0 + r) * ldx + c], Acc()) - mu_s[c] : Acc(0);
-    }
-    __syncthreads();
-
-    const int QJ = (k + RJ - 1) / RJ;                 // column quads
-    for (int w = threadIdx.x; w < (R / 2) * QJ; w += kThreads) {
-        const int rp = w / QJ, jq = w % QJ;
-        const int ra = 2 * rp, jb = jq * RJ;
-        Acc acc[2][RJ];
-#pragma unroll
-        for (int q = 0; q < RJ; ++q) {
-            const int j = min(jb + q, k - 1);
-            const Acc base = uv[k + j];
-            acc[0][q] = (ra < nr) ? fma_acc(s[row0 + ra], uv[j], base) : Acc(0);
-            acc[1][q] = (ra + 1 < nr) ? fma_acc(s[row0 + ra + 1], uv[j], base) : Acc(0);
+    const int64_t tiles = (n + R - 1) / R;
+    auto stage = [&](int64_t tile, int buf) {
+        const int64_t row0 = tile * R;
+        const int nr = (int)min64(R, n - row0);
+        V* xr = xraw + (size_t)buf * R * d;
+        for (int i = threadIdx.x; i < R * d; i += kThreads) {
+            const int r = i / d, c = i % d;
+            const bool ok = r < nr;
+            cp_async<sizeof(V)>(xr + i, X + (ok ? (row0 + r) * ldx + c : 0), ok);
         }
-        for (int c = 0; c < d; ++c) {
-            const Acc x0 = xt[ra * DP + c], x1 = xt[(ra + 1) * DP + c];
+        cp_commit();
+    };
+    int64_t tile = blockIdx.x;
+    if (tile < tiles) stage(tile, 0);
+    int buf = 0;
+    const int QJ = (k + RJ - 1) / RJ;                 // column quads
+    for (; tile < tiles; tile += gridDim.x, buf ^= 1) {
+        const int64_t next = tile + gridDim.x;
+        if (next < tiles) { stage(next, buf ^ 1); cp_wait<1>(); }
+        else cp_wait<0>();
+        __syncthreads();
+        const int64_t row0 = tile * R;
+        const int nr = (int)min64(R, n - row0);
+        const V* xr = xraw + (size_t)buf * R * d;
+        for (int i = threadIdx.x; i < R * d; i += kThreads) {
+            const int r = i / d, c = i % d;
+            xt[r * DP + c] = (r < nr) ? to_acc(xr[i], Acc()) - mu_s[c] : Acc(0);
+        }
+        __syncthreads();
+        if (threadIdx.x < R) s_s[threadIdx.x] = row_sqnorm(xt + threadIdx.x * DP, d);
+        __syncthreads();
+        for (int w = threadIdx.x; w < (R / 2) * QJ; w += kThreads) {
+            const int rp = w / QJ, jq = w % QJ;
+            const int ra = 2 * rp, jb = jq * RJ;
+            Acc acc[2][RJ];
+            const Acc s0 = s_s[ra], s1 = s_s[ra + 1];
 #pragma unroll
             for (int q = 0; q < RJ; ++q) {
-                const Acc wv = Wm2[c * k + min(jb + q, k - 1)];
-                acc[0][q] = fma_acc(x0, wv, acc[0][q]);
-                acc[1][q] = fma_acc(x1, wv, acc[1][q]);
+                const int j = min(jb + q, k - 1);
+                const Acc base = uv[k + j];
+                acc[0][q] = fma_acc(s0, uv[j], base);
+                acc[1][q] = fma_acc(s1, uv[j], base);
+            }
+            for (int c = 0; c < d; ++c) {
+                const Acc x0 = xt[ra * DP + c], x1 = xt[(ra + 1) * DP + c];
+#pragma unroll
+                for (int q = 0; q < RJ; ++q) {
+                    const Acc wv = Wm2[c * k + min(jb + q, k - 1)];
+                    acc[0][q] = fma_acc(x0, wv, acc[0][q]);
+                    acc[1][q] = fma_acc(x1, wv, acc[1][q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RJ; ++q) {
+                if (jb + q >= k) break;
+                if (ra < nr) out[(row0 + ra) * ldo + jb + q] = (Out)acc[0][q];
+                if (ra + 1 < nr) out[(row0 + ra + 1) * ldo + jb + q] = (Out)acc[1][q];
             }
         }
-#pragma unroll
-        for (int q = 0; q < RJ; ++q) {
-            if (jb + q >= k) break;
-            if (ra < nr) out[(row0 + ra) * ldo + jb + q] = acc[0][q];
-            if (ra + 1 < nr) out[(row0 + ra + 1) * ldo + jb + q] = acc[1][q];
-        }
+        __syncthreads();
     }
-}
-
-template <dm_dtype DT>
-size_t reduce_smem(int d, int k) {
-    using Acc = typename Types<DT>::Acc;
-    using Wide = typename Types<DT>::Wide;
-    const int D2 = d + 2;
-    size_t a = sizeof(Acc) * ((size_t)d + kChunk * (D2 + 1) + (size_t)kChunk * (k + 1));
-    a = (a + 15) & ~size_t(15);
-    return a + sizeof(Wide) * (size_t)D2 * k;
 }
 
 template <dm_dtype DT, class XT>
-cudaError_t reduce_launch_t(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
+size_t reduce_smem(int d, int k) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
+    auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const int D2 = d + 2;
+    return up(2 * (size_t)kChunk * d * sizeof(XT)) + up(2 * (size_t)kChunk * k * sizeof(V)) +
+           up((size_t)kChunk * (D2 + 1) * sizeof(Acc)) + up((size_t)kChunk * (k + 1) * sizeof(Acc)) +
+           up((size_t)d * sizeof(Acc)) + sizeof(Wide) * (size_t)D2 * k;
+}
+
+int sm_count(int hint) {
+    if (hint > 0) return hint;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+template <dm_dtype DT, class XT, int MAXOB>
+cudaError_t reduce_launch_t(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
+    using V = typename Types<DT>::V;
+    using Wide = typename Types<DT>::Wide;
     const int blocks = reduce_blocks(a);
     const int64_t rpb = (a.n + blocks - 1) / blocks;
-    const size_t smem = reduce_smem<DT>((int)a.d, (int)a.k);
-    auto kern = reduce_kernel<DT, XT>;
+    const size_t smem = reduce_smem<DT, XT>((int)a.d, (int)a.k);
+    auto kern = reduce_kernel<DT, XT, MAXOB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<blocks, kThreads, smem, st>>>(
         static_cast<const XT*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const V*>(a.mu), a.mu_stride,
-        static_cast<const Acc*>(a.s), static_cast<const V*>(a.Z), (int)a.k, a.ldz,
-        static_cast<Wide*>(a.partial), rpb);
+        a.with_s ? 1 : 0, static_cast<const V*>(a.Z), (int)a.k, a.ldz, static_cast<Wide*>(a.partial),
+        rpb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int total = (int)((a.d + 2) * a.k);
     const int warps_per_block = 8;
@@ -342,34 +438,61 @@ cudaError_t reduce_launch_t(const ReduceArgs& a, cudaStream_t st, int64_t* launc
     return cudaSuccess;
 }
 
-template <dm_dtype DT>
-cudaError_t reduce_launch_dt(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
-    if (a.x_acc) return reduce_launch_t<DT, typename Types<DT>::Acc>(a, st, launches);
-    return reduce_launch_t<DT, typename Types<DT>::V>(a, st, launches);
+template <dm_dtype DT, class XT>
+cudaError_t reduce_launch_ob(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
+    const int64_t OB = ((a.d + 2 + RC - 1) / RC) * ((a.k + RJ - 1) / RJ);
+    if (OB <= kThreads) return reduce_launch_t<DT, XT, 1>(a, st, launches);
+    return reduce_launch_t<DT, XT, 4>(a, st, launches);
 }
 
-// R_i = sum_c (x_ic - mu_c), one thread per point.
+template <dm_dtype DT>
+cudaError_t reduce_launch_dt(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
+    if (a.x_acc) return reduce_launch_ob<DT, typename Types<DT>::Acc>(a, st, launches);
+    return reduce_launch_ob<DT, typename Types<DT>::V>(a, st, launches);
+}
+
+// R_i = sum_c (x_ic - mu_c): one warp per row, lanes over the coordinates,
+// U rows per warp step with all loads issued first.
 template <dm_dtype DT>
 __global__ void __launch_bounds__(kThreads)
 rowsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int64_t ldx,
               const typename Types<DT>::V* __restrict__ mu, int64_t mu_stride,
               typename Types<DT>::Acc* __restrict__ R) {
     using Acc = typename Types<DT>::Acc;
+    using V = typename Types<DT>::V;
+    constexpr int U = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc* mu_s = reinterpret_cast<Acc*>(smem_raw);
     for (int c = threadIdx.x; c < d; c += kThreads) mu_s[c] = to_acc(mu[c * mu_stride], Acc());
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    Acc acc = 0;
-    for (int c = 0; c < d; ++c) acc += to_acc(X[i * ldx + c], Acc()) - mu_s[c];
-    R[i] = acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t i0 = gw * U; i0 < n; i0 += nw * U) {
+        Acc acc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = 0;
+        for (int cb = 0; cb < d; cb += 32) {
+            const int c = cb + lane;
+            V v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = (c < d && i0 + u < n) ? X[(i0 + u) * ldx + c] : V(0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc[u] += (c < d) ? to_acc(v[u], Acc()) - mu_s[c] : Acc(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Acc x = acc[u];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0 && i0 + u < n) R[i0 + u] = x;
+        }
+    }
 }
 
 template <dm_dtype DT>
 cudaError_t l2prep_launch_t(const L2PrepArgs& a, cudaStream_t st, int64_t* launches) {
     using V = typename Types<DT>::V;
-    using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     const int blocks = l2prep_blocks(a);
     const int64_t rpb = (a.n + blocks - 1) / blocks;
@@ -380,28 +503,32 @@ cudaError_t l2prep_launch_t(const L2PrepArgs& a, cudaStream_t st, int64_t* launc
     mean_finalize_kernel<DT><<<(unsigned)((a.d + 127) / 128), 128, 0, st>>>(
         static_cast<const Wide*>(a.partial), blocks, (int)a.d, a.n, static_cast<V*>(a.mu));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    sqnorm_kernel<DT><<<(unsigned)((a.n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-        static_cast<const V*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const V*>(a.mu),
-        static_cast<Acc*>(a.s));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *launches += 3;
+    *launches += 2;
     return cudaSuccess;
 }
 
 template <dm_dtype DT>
-cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* launches) {
+cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* launches, int num_sms) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
-    const size_t smem = sizeof(Acc) * ((size_t)a.d * a.k + 2 * a.k + kApplyRows * (a.d + 1) + a.d);
+    auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const int R = kApplyRows;
+    const size_t smem = up(2 * (size_t)R * a.d * sizeof(V)) + up((size_t)a.d * a.k * sizeof(Acc)) +
+                        up(2 * (size_t)a.k * sizeof(Acc)) + up((size_t)R * (a.d + 1) * sizeof(Acc)) +
+                        up((size_t)a.d * sizeof(Acc)) + (size_t)R * sizeof(Acc);
     auto kern = l2apply_kernel<DT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)((a.n + kApplyRows - 1) / kApplyRows), kThreads, smem, st>>>(
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (a.n + R - 1) / R;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(occ, 1) * num_sms));
+    kern<<<(unsigned)blocks, kThreads, smem, st>>>(
         static_cast<const V*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const V*>(a.mu),
-        static_cast<const Acc*>(a.s), static_cast<const Wide*>(a.res), (int)a.k,
-        static_cast<Out*>(a.out), a.ldo);
+        static_cast<const Wide*>(a.res), (int)a.k, static_cast<Out*>(a.out), a.ldo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
     return cudaSuccess;
@@ -411,26 +538,24 @@ cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* lau
 
 bool reduce_supported(int64_t d, int64_t k) {
     const int64_t OB = ((d + 2 + RC - 1) / RC) * ((k + RJ - 1) / RJ);
-    return OB <= 4 * kThreads && d <= 4096 && k <= 4096;
+    if (OB > 4 * kThreads || d > 4096 || k > 4096) return false;
+    // shared memory of the reduce kernel (FP64/int64 worst case)
+    const size_t smem = 2 * (size_t)kChunk * d * 8 + 2 * (size_t)kChunk * k * 8 +
+                        (size_t)kChunk * (d + 3) * 8 + (size_t)kChunk * (k + 1) * 8 + (size_t)d * 8 +
+                        8 * (size_t)(d + 2) * k + 96;
+    return smem <= 200 * 1024;
 }
 
 int reduce_blocks(const ReduceArgs& a) {
-    int sms = a.num_sms;
-    if (sms <= 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = sm_count(a.num_sms);
     const int64_t want = (a.n + 1023) / 1024;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 3 * sms));
 }
 
 int l2prep_blocks(const L2PrepArgs& a) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count(0);
     const int64_t want = (a.n + 1023) / 1024;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 4 * sms));
 }
 
 cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s, int64_t* launches) {
@@ -450,7 +575,9 @@ cudaError_t rowsum_launch_t(const void* X, int64_t n, int64_t d, int64_t ldx, co
     auto kern = rowsum_kernel<DT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, smem, s>>>(
+    const int64_t warps = (n + 3) / 4;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 8 * (int64_t)sm_count(0)));
+    kern<<<(unsigned)blocks, kThreads, smem, s>>>(
         static_cast<const V*>(X), n, (int)d, ldx, static_cast<const V*>(mu), mu_stride,
         static_cast<Acc*>(R));
     return cudaGetLastError();
@@ -478,10 +605,11 @@ cudaError_t l2prep_launch(const L2PrepArgs& a, cudaStream_t s, int64_t* launches
 }
 
 cudaError_t l2apply_launch(const L2ApplyArgs& a, cudaStream_t s, int64_t* launches) {
+    const int sms = sm_count(a.num_sms);
     switch (a.dtype) {
-        case DM_F32: return l2apply_launch_t<DM_F32>(a, s, launches);
-        case DM_F64: return l2apply_launch_t<DM_F64>(a, s, launches);
-        default: return l2apply_launch_t<DM_I32>(a, s, launches);
+        case DM_F32: return l2apply_launch_t<DM_F32>(a, s, launches, sms);
+        case DM_F64: return l2apply_launch_t<DM_F64>(a, s, launches, sms);
+        default: return l2apply_launch_t<DM_I32>(a, s, launches, sms);
     }
 }
 

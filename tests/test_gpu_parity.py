@@ -35,6 +35,19 @@ def ctx(dm):
     return dm.dm_create(0)
 
 
+@pytest.fixture(scope="module")
+def ctx_ordered(dm):
+    c = dm.dm_create(0)
+    dm.dm_set_deterministic(c, True)
+    return c
+
+
+@pytest.fixture(params=["atomic", "ordered"])
+def mctx(request, ctx, ctx_ordered):
+    """Both accumulation modes of the l1 query (squared l2 ignores it)."""
+    return ctx if request.param == "atomic" else ctx_ordered
+
+
 def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
@@ -100,22 +113,23 @@ def test_grid_closed_form(dm, ctx, metric, dtype):
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
 @pytest.mark.parametrize("n", [1, 2, 3, 767, 768, 769, 1537, 4095, 4097, 20011])
-def test_fp32_mixture_sizes(dm, ctx, metric, n):
+def test_fp32_mixture_sizes(dm, mctx, metric, n):
     X, Z = inputs.workload_mixture_f32(n=n, d=32, k=16)
-    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.float32)
+    check(gpu_product(dm, mctx, metric, X, Z), reference(metric, X, Z), np.float32)
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
 @pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 16, 17, 40])
-def test_query_block_widths(dm, ctx, metric, k):
+def test_query_block_widths(dm, mctx, metric, k):
     X, Z = inputs.workload_mixture_f32(n=5000, d=7, k=k)
-    check(gpu_product(dm, ctx, metric, X, Z), reference(metric, X, Z), np.float32)
+    check(gpu_product(dm, mctx, metric, X, Z), reference(metric, X, Z), np.float32)
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
 @pytest.mark.parametrize("dtype", [np.float64, np.int32])
 @pytest.mark.parametrize("k", [1, 3, 16, 20])
-def test_other_types(dm, ctx, metric, dtype, k):
+def test_other_types(dm, mctx, metric, dtype, k):
+    ctx = mctx
     n, d = 6007, 5
     if dtype == np.int32:
         X = inputs.integer_points(n, d, 3, 0, 1 << 16)
@@ -127,7 +141,8 @@ def test_other_types(dm, ctx, metric, dtype, k):
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
-def test_integer_ties_exact(dm, ctx, metric):
+def test_integer_ties_exact(dm, mctx, metric):
+    ctx = mctx
     rng = np.random.default_rng(21)
     X = rng.integers(0, 6, size=(9000, 4)).astype(np.int32)
     Z = rng.integers(-100, 101, size=(9000, 3)).astype(np.int32)
@@ -164,7 +179,8 @@ def test_identical_points_give_zero(dm, ctx, metric):
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
-def test_leading_dimensions(dm, ctx, metric):
+def test_leading_dimensions(dm, mctx, metric):
+    ctx = mctx
     n, d, k = 4000, 6, 5
     Xb = inputs.gaussian_mixture(n, d + 3, 4, 9)
     Zb = inputs.gaussian_queries(n, k + 2, 10)
@@ -214,11 +230,15 @@ def test_sort_signed_zeros_valid(dm, ctx):
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
-def test_deterministic(dm, ctx, metric):
+def test_deterministic(dm, ctx, ctx_ordered, metric):
+    # Ordered accumulation: identical bits run to run.  L2-reduction mode:
+    # the same values up to the order of the d additions.
     X, Z = inputs.workload_mixture_f32(n=50000, d=12, k=16)
-    a = gpu_product(dm, ctx, metric, X, Z)
-    b = gpu_product(dm, ctx, metric, X, Z)
+    a = gpu_product(dm, ctx_ordered, metric, X, Z)
+    b = gpu_product(dm, ctx_ordered, metric, X, Z)
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    c = gpu_product(dm, ctx, metric, X, Z)
+    assert oracle.relative_error(c, a) <= 1e-6
 
 
 def test_matvec_entry_points_reject_wrong_metric(dm, ctx):
@@ -293,9 +313,9 @@ def full_int():
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
-def test_full_size_fp32_sampled_rows(dm, ctx, metric, full_fp32):
+def test_full_size_fp32_sampled_rows(dm, mctx, metric, full_fp32):
     X, Z = full_fp32
-    out = gpu_product(dm, ctx, metric, X, Z)
+    out = gpu_product(dm, mctx, metric, X, Z)
     rows = inputs.sample_rows(len(X), 24)
     want = (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(X, Z, rows)
     assert oracle.relative_error(out[rows], want) <= 1e-5
@@ -303,9 +323,9 @@ def test_full_size_fp32_sampled_rows(dm, ctx, metric, full_fp32):
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
-def test_full_size_int_sampled_rows_exact(dm, ctx, metric, full_int):
+def test_full_size_int_sampled_rows_exact(dm, mctx, metric, full_int):
     X, Z = full_int
-    out = gpu_product(dm, ctx, metric, X, Z)
+    out = gpu_product(dm, mctx, metric, X, Z)
     rows = inputs.sample_rows(len(X), 12)
     want = (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(X, Z, rows)
     np.testing.assert_array_equal(out[rows], want)
