@@ -91,13 +91,16 @@ dm_status dm_set_deterministic(dm_ctx* ctx, int on);
  *   DM_L2SQ: the plan records the pointer X (the caller keeps X alive and
  *            unchanged for the plan's lifetime) and the column means mu (a
  *            shift: the product is translation invariant).
- * This call synchronizes the context's stream once (DM_L1 reads the digit
- * histograms back to skip radix passes whose digit is constant).  Returns
- * DM_ERR_NONFINITE if X holds NaN or Inf. */
+ * DM_L1 synchronizes the context's stream once (it reads the digit
+ * histograms back to skip radix passes whose digit is constant) and returns
+ * DM_ERR_NONFINITE if X holds NaN or Inf; DM_L2SQ is asynchronous and reports
+ * non-finite coordinates through dm_sync. */
 dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* X,
                      int64_t n, int64_t d, int64_t ldx, dm_plan** plan);
 
-/* Free a plan (stream-ordered: waits for the context's stream first). */
+/* Release a plan.  Its device buffers go back to the context, which reuses
+ * them for later plans in stream order (no wait; buffers beyond 8 GiB per
+ * context are freed).  Work already queued that uses the plan still runs. */
 void dm_plan_destroy(dm_plan* plan);
 
 /* out = A z for one query column z (n elements, contiguous) on an l1 plan

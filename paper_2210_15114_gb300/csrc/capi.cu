@@ -34,10 +34,17 @@ struct dm_ctx {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
     std::map<std::string, Stat> stats;
+    // Device buffers of destroyed plans, reused by later plans.  All use is
+    // ordered on the context's stream, so a buffer handed back by
+    // dm_plan_destroy can be reused by the next call without a sync.
+    struct Block { void* p; size_t bytes; };
+    std::vector<Block> pool;
+    size_t pool_bytes = 0;
 };
 
 struct dm_plan {
     dm_ctx* ctx = nullptr;
+    std::vector<std::pair<void*, size_t>> owned;   // buffers from the context pool
     dm_metric metric = DM_L1;
     dm_dtype dtype = DM_F32;
     int64_t n = 0, d = 0;
@@ -178,6 +185,52 @@ dm_status ensure_buffer(dm_ctx* ctx, void** buf, size_t* have, size_t bytes) {
     return DM_OK;
 }
 
+constexpr size_t kPoolCap = size_t(8) << 30;   // cached plan buffers per context
+
+// A device buffer of at least `bytes` for plan p: a pooled block of the same
+// rounded size when one is free, else a new allocation.
+dm_status plan_alloc(dm_plan* p, size_t bytes, void** out) {
+    dm_ctx* ctx = p->ctx;
+    bytes = (bytes + 255) & ~size_t(255);
+    for (size_t i = 0; i < ctx->pool.size(); ++i) {
+        if (ctx->pool[i].bytes == bytes) {
+            *out = ctx->pool[i].p;
+            ctx->pool_bytes -= bytes;
+            ctx->pool.erase(ctx->pool.begin() + (long)i);
+            p->owned.push_back({*out, bytes});
+            return DM_OK;
+        }
+    }
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        // drop the cache and retry once
+        cudaStreamSynchronize(ctx->stream);
+        for (auto& b : ctx->pool) cudaFree(b.p);
+        ctx->pool.clear();
+        ctx->pool_bytes = 0;
+        e = cudaMalloc(out, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); *out = nullptr; return DM_ERR_OOM; }
+    }
+    p->owned.push_back({*out, bytes});
+    return DM_OK;
+}
+
+// Hand a plan's buffers back to the context pool (freed beyond the cap).
+void plan_release(dm_plan* p) {
+    dm_ctx* ctx = p->ctx;
+    for (auto& ob : p->owned) {
+        if (ctx->pool_bytes + ob.second <= kPoolCap) {
+            ctx->pool.push_back({ob.first, ob.second});
+            ctx->pool_bytes += ob.second;
+        } else {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ob.first);
+        }
+    }
+    p->owned.clear();
+}
+
 // Read (and clear) the device error word; the stream must be idle.
 dm_status take_device_error(dm_ctx* ctx) {
     DM_TRY_CUDA(cudaMemcpyAsync(ctx->host_err, ctx->err, 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -200,8 +253,8 @@ dm_status prepare_l1(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
     const size_t hist_words = sort_hist_words(t, d);
     const size_t lb_words = sort_lookback_words(t, n, d);
 
-    DM_TRY_CUDA(cudaMalloc(&p->xs, nd * dtype_size(t)));
-    DM_TRY_CUDA(cudaMalloc(reinterpret_cast<void**>(&p->perm), nd * 4));
+    DM_TRY(plan_alloc(p, nd * dtype_size(t), &p->xs));
+    DM_TRY(plan_alloc(p, nd * 4, reinterpret_cast<void**>(&p->perm)));
 
     // arena: [hist | counters | lookback] (zeroed) then keys_a, keys_b, vals_a, vals_b
     const size_t o_hist = 0;
@@ -267,7 +320,7 @@ dm_status prepare_l1(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
     }
     // R_i for the part of the query that is linear in the point (shift: the
     // median of each column, xs[c * n + n / 2]).
-    DM_TRY_CUDA(cudaMalloc(&p->R, (size_t)n * acc_size(t)));
+    DM_TRY(plan_alloc(p, (size_t)n * acc_size(t), &p->R));
     {
         ProfScope ps(ctx, "l1_rowsum");
         DM_TRY_CUDA(rowsum_launch(t, X, n, d, ldx,
@@ -282,7 +335,7 @@ dm_status prepare_l2(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
     const dm_dtype t = p->dtype;
     p->X = X;
     p->ldx = ldx;
-    DM_TRY_CUDA(cudaMalloc(&p->mu, (size_t)p->d * dtype_size(t)));
+    DM_TRY(plan_alloc(p, (size_t)p->d * dtype_size(t), &p->mu));
     L2PrepArgs a{};
     a.dtype = t;
     a.X = X; a.n = p->n; a.d = p->d; a.ldx = ldx;
@@ -294,14 +347,11 @@ dm_status prepare_l2(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
         ProfScope ps(ctx, "l2_prepare");
         DM_TRY_CUDA(l2prep_launch(a, ctx->stream, &ctx->launches));
     }
-    return take_device_error(ctx);
+    return DM_OK;
 }
 
 void free_plan_buffers(dm_plan* p) {
-    if (p->xs) cudaFree(p->xs);
-    if (p->perm) cudaFree(p->perm);
-    if (p->R) cudaFree(p->R);
-    if (p->mu) cudaFree(p->mu);
+    plan_release(p);
     p->xs = nullptr; p->perm = nullptr; p->R = nullptr; p->mu = nullptr;
 }
 
@@ -425,6 +475,7 @@ void dm_destroy(dm_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->arena) cudaFree(ctx->arena);
+    for (auto& b : ctx->pool) cudaFree(b.p);
     if (ctx->hx) cudaFree(ctx->hx);
     if (ctx->hz) cudaFree(ctx->hz);
     if (ctx->ho) cudaFree(ctx->ho);
@@ -444,6 +495,8 @@ dm_status dm_set_deterministic(dm_ctx* ctx, int on) {
 
 dm_status dm_set_stream(dm_ctx* ctx, void* stream) {
     if (!ctx) return DM_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);   // pooled buffers may be in use on the old stream
     ctx->stream = static_cast<cudaStream_t>(stream);
     return DM_OK;
 }
@@ -508,8 +561,7 @@ dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* 
 void dm_plan_destroy(dm_plan* p) {
     if (!p) return;
     DeviceGuard g(p->ctx->device);
-    cudaStreamSynchronize(p->ctx->stream);
-    free_plan_buffers(p);
+    free_plan_buffers(p);   // stream-ordered reuse: no wait needed
     delete p;
 }
 

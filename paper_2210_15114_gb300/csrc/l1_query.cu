@@ -583,8 +583,10 @@ l1_tile_scan_kernel(Wide* __restrict__ agg, int T, int NV) {
     }
 }
 
-// out[i, j] = outg[j / KC][i][j % KC] + R^T Z[j] - R_i 1^T Z[j]  (atomic mode)
-template <dm_dtype DT, int KC>
+// out[i, j] = outg[j / KC][i][j % KC] + R^T Z[j] - R_i 1^T Z[j]  (atomic mode).
+// Thread per (row, VEC adjacent columns); VEC = 4 needs k % 4 == 0, ldo % 4 == 0
+// and an aligned out.
+template <dm_dtype DT, int KC, int VEC>
 __global__ void __launch_bounds__(kThreads)
 l1_finalize_kernel(const typename Types<DT>::Acc* __restrict__ outg,
                    const typename Types<DT>::Acc* __restrict__ R,
@@ -592,21 +594,45 @@ l1_finalize_kernel(const typename Types<DT>::Acc* __restrict__ outg,
                    typename Types<DT>::Out* __restrict__ out, int64_t ldo) {
     using Acc = typename Types<DT>::Acc;
     using Out = typename Types<DT>::Out;
-    const int64_t total = n * k;
+    const int nv = (k + VEC - 1) / VEC;
+    const int64_t total = n * nv;
     for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = idx / k;
-        const int j = (int)(idx - i * k);
-        const Acc v = __ldcs(outg + ((int64_t)(j / KC) * n + i) * KC + (j % KC));
-        const Acc rz = (Acc)res[j], uz = (Acc)res[k + j];
-        out[i * ldo + j] = (Out)(v + (rz - R[i] * uz));
+        const int64_t i = idx / nv;
+        const int j0 = (int)(idx - i * nv) * VEC;
+        const Acc Ri = R[i];
+        Acc v[VEC];
+        if constexpr (VEC == 4 && KC % 4 == 0) {
+            ldcg_vec<Acc, 4>(outg + ((int64_t)(j0 / KC) * n + i) * KC + (j0 % KC), v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const int j = j0 + q;
+                v[q] = j < k ? __ldcs(outg + ((int64_t)(j / KC) * n + i) * KC + (j % KC)) : Acc(0);
+            }
+        }
+        Out o[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const int j = min(j0 + q, k - 1);
+            o[q] = (Out)(v[q] + ((Acc)res[j] - Ri * (Acc)res[k + j]));
+        }
+        if constexpr (VEC == 4 && sizeof(Out) == 4) {
+            *reinterpret_cast<float4*>(out + i * ldo + j0) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q)
+                if (j0 + q < k) out[i * ldo + j0 + q] = o[q];
+        }
     }
 }
 
 // ---------------------------------------------------------------- prologue
 // R^T Z and 1^T Z (per-block partials) and the group-major copy Zg of Z.
-// Thread (row group rg, padded column j < JW = G*KC); rows rg, rg + RGS, ...
-template <dm_dtype DT, int KC>
+// Thread (row group rg, column vector jv): VEC adjacent padded columns
+// j = jv*VEC .. +VEC of rows rg, rg + RGS, ..., U rows per step with all loads
+// issued first.  VEC = 4 needs k % 4 == 0, ldz % 4 == 0 and an aligned Z.
+template <dm_dtype DT, int KC, int VEC>
 __global__ void __launch_bounds__(kThreads)
 l1_prologue_kernel(const typename Types<DT>::V* __restrict__ Z, int64_t n, int k, int64_t ldz,
                    const typename Types<DT>::Acc* __restrict__ R,
@@ -615,52 +641,98 @@ l1_prologue_kernel(const typename Types<DT>::V* __restrict__ Z, int64_t n, int k
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
+    constexpr int U = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Wide* red = reinterpret_cast<Wide*>(smem_raw);      // [RGS][2][JC]
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min64(n, r0 + rows_per_block);
-    const int JC = JW < kThreads ? JW : kThreads;          // columns per sweep
+    const int NJV = JW / VEC;                              // column vectors per row
+    const int JC = NJV < kThreads ? NJV : kThreads;        // vectors per sweep
     const int RGS = kThreads / JC;
     const int rg = threadIdx.x / JC, jl = threadIdx.x % JC;
-    for (int jb = 0; jb < JW; jb += JC) {
-        const int j = jb + jl;
-        const bool active = rg < RGS && j < JW;
-        const int g = j / KC, q = j % KC;
-        Wide wu = 0, wr = 0;
+    for (int jb = 0; jb < NJV; jb += JC) {
+        const int jv = jb + jl;
+        const bool active = rg < RGS && jv < NJV;
+        const int j0 = jv * VEC;
+        const int g = j0 / KC, q0 = j0 % KC;
+        Wide wu[VEC], wr[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) { wu[v] = 0; wr[v] = 0; }
         if (active) {
-            Acc cu = 0, cr = 0;
+            Acc cu[VEC], cr[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) { cu[v] = 0; cr[v] = 0; }
             int cnt = 0;
-            for (int64_t r = r0 + rg; r < r1; r += RGS) {
-                const V z = j < k ? Z[r * ldz + j] : V(0);
-                Zg[((int64_t)g * n + r) * KC + q] = z;
-                cu += (Acc)z;
-                cr += R[r] * (Acc)z;
-                if (++cnt == 64) { wu += (Wide)cu; wr += (Wide)cr; cu = 0; cr = 0; cnt = 0; }
+            for (int64_t r = r0 + rg; r < r1; r += (int64_t)RGS * U) {
+                V z[U][VEC];
+                Acc rr[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t ru = r + (int64_t)u * RGS;
+                    rr[u] = ru < r1 ? R[ru] : Acc(0);
+                    if constexpr (VEC == 4) {
+                        // k % 4 == 0: a vector is wholly inside [0, k) or wholly padding
+                        if (ru < r1 && j0 < k) ld_vec<V, 4>(Z + ru * ldz + j0, z[u]);
+                        else {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) z[u][v] = V(0);
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) z[u][v] = (ru < r1 && j0 + v < k) ? Z[ru * ldz + j0 + v] : V(0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t ru = r + (int64_t)u * RGS;
+                    if (ru >= r1) continue;
+                    V* dst = Zg + ((int64_t)g * n + ru) * KC + q0;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        dst[v] = z[u][v];
+                        cu[v] += (Acc)z[u][v];
+                        cr[v] += rr[u] * (Acc)z[u][v];
+                    }
+                }
+                if (++cnt == 16) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) { wu[v] += (Wide)cu[v]; wr[v] += (Wide)cr[v]; cu[v] = 0; cr[v] = 0; }
+                    cnt = 0;
+                }
             }
-            wu += (Wide)cu;
-            wr += (Wide)cr;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) { wu[v] += (Wide)cu[v]; wr[v] += (Wide)cr[v]; }
         }
-        __syncthreads();
-        if (rg < RGS) { red[(rg * 2 + 0) * JC + jl] = wu; red[(rg * 2 + 1) * JC + jl] = wr; }
-        __syncthreads();
-        if (rg == 0 && j < k) {
-            Wide tu = 0, tr = 0;
-            for (int t = 0; t < RGS; ++t) { tu += red[(t * 2) * JC + jl]; tr += red[(t * 2 + 1) * JC + jl]; }
-            Wide* out = partial + (int64_t)blockIdx.x * 2 * k;
-            out[j] = tr;       // R^T Z
-            out[k + j] = tu;   // 1^T Z
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            __syncthreads();
+            if (rg < RGS) { red[(rg * 2 + 0) * JC + jl] = wu[v]; red[(rg * 2 + 1) * JC + jl] = wr[v]; }
+            __syncthreads();
+            const int j = j0 + v;
+            if (rg == 0 && jv < NJV && j < k) {
+                Wide tu = 0, tr = 0;
+                for (int t = 0; t < RGS; ++t) { tu += red[(t * 2) * JC + jl]; tr += red[(t * 2 + 1) * JC + jl]; }
+                Wide* out = partial + (int64_t)blockIdx.x * 2 * k;
+                out[j] = tr;       // R^T Z
+                out[k + j] = tu;   // 1^T Z
+            }
         }
     }
 }
 
+// One warp per result entry: lanes stride over the block partials, then a
+// fixed-order warp tree (reproducible).
 template <class Wide>
 __global__ void l1_prologue_finalize(const Wide* __restrict__ partial, int blocks, int k2,
                                      Wide* __restrict__ res) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k2) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= k2) return;
     Wide t = 0;
-    for (int b = 0; b < blocks; ++b) t += partial[(int64_t)b * k2 + i];
-    res[i] = t;
+    for (int b = lane; b < blocks; b += 32) t += partial[(int64_t)b * k2 + w];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) res[w] = t;
 }
 
 int full_kc(dm_dtype t) { return t == DM_F64 ? 4 : 8; }
@@ -741,9 +813,13 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
     const bool atomic = !a.deterministic;
     if (stage == 2) {   // finalize (L2-reduction mode only)
         if (!atomic) return cudaSuccess;
-        const int64_t total = a.n * a.k;
-        const int64_t fb = std::min<int64_t>((total + kThreads - 1) / kThreads, 8 * (int64_t)a.num_sms);
-        l1_finalize_kernel<DT, KC><<<(unsigned)std::max<int64_t>(fb, 1), kThreads, 0, st>>>(
+        const bool vec = (a.k % 4 == 0) && (a.ldo % 4 == 0) && sizeof(typename Types<DT>::Out) == 4 &&
+                         (reinterpret_cast<uintptr_t>(a.out) % 16 == 0);
+        const int64_t total = a.n * ((a.k + 3) / 4);
+        const int64_t fb = std::max<int64_t>(1, std::min<int64_t>((total + kThreads - 1) / kThreads,
+                                                                   8 * (int64_t)a.num_sms));
+        auto kern = vec ? l1_finalize_kernel<DT, KC, 4> : l1_finalize_kernel<DT, KC, 1>;
+        kern<<<(unsigned)fb, kThreads, 0, st>>>(
             reinterpret_cast<const Acc*>(sc + L.outg), static_cast<const Acc*>(a.R),
             reinterpret_cast<const Wide*>(sc + L.res), a.n, (int)a.k,
             static_cast<typename Types<DT>::Out*>(a.out), a.ldo);
@@ -755,9 +831,13 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
         const int blocks = prologue_blocks(a.n, a.num_sms);
         const int64_t rpb = (a.n + blocks - 1) / blocks;
         const int JW = (int)(L.G * KC);
-        const int JC = JW < kThreads ? JW : kThreads;
+        const bool vec = (a.k % 4 == 0) && (a.ldz % 4 == 0) && sizeof(V) == 4 && KC % 4 == 0 &&
+                         (reinterpret_cast<uintptr_t>(a.Z) % 16 == 0);
+        const int VEC = vec ? 4 : 1;
+        const int NJV = JW / VEC;
+        const int JC = NJV < kThreads ? NJV : kThreads;
         const size_t smem = sizeof(Wide) * 2 * (size_t)(kThreads / JC) * JC;
-        auto kern = l1_prologue_kernel<DT, KC>;
+        auto kern = vec ? l1_prologue_kernel<DT, KC, 4> : l1_prologue_kernel<DT, KC, 1>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<blocks, kThreads, smem, st>>>(
@@ -765,7 +845,7 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
             reinterpret_cast<V*>(sc + L.zg), JW, reinterpret_cast<Wide*>(sc + L.partial), rpb);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int k2 = (int)(2 * a.k);
-        l1_prologue_finalize<Wide><<<(k2 + 127) / 128, 128, 0, st>>>(
+        l1_prologue_finalize<Wide><<<(k2 + 7) / 8, 256, 0, st>>>(
             reinterpret_cast<const Wide*>(sc + L.partial), blocks, k2,
             reinterpret_cast<Wide*>(sc + L.res));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

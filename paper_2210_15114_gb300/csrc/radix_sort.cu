@@ -6,7 +6,7 @@
 //                    written column-major (d x n) plus the digit histograms of
 //                    every digit position of every column, in one pass.
 //   onesweep_pass -- one digit position: each CTA ranks a tile of keys by the
-//                    digit (warp match + per-warp counters, stable), publishes
+//                    digit (ballot peer masks + per-warp counters, stable), publishes
 //                    its digit counts and finds the counts of all earlier tiles
 //                    of its column through a decoupled look-back (bounded
 //                    spin), then scatters keys and payload through shared
@@ -16,6 +16,8 @@
 // Ties keep index order (LSD is stable), so the permutation equals a stable
 // argsort of each column.  -0.0 sorts before +0.0 (they differ in key, not in
 // value; either order gives the same product).
+#include <algorithm>
+
 #include "dm_internal.h"
 
 namespace dm {
@@ -55,6 +57,21 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
 }
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Lanes of the warp holding the same 8-bit digit as this lane, from eight
+// ballots (one per digit bit): a lane is a peer when it agrees on every bit.
+// Lanes with valid == false are excluded from every mask (their own result
+// is meaningless).  All 32 lanes must call it.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t digit, bool valid) {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (digit >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
 }
 
 // Exclusive scan of one value per thread over the 256 threads of the CTA.
@@ -118,58 +135,64 @@ keygen_hist_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64
     uint32_t* h = reinterpret_cast<uint32_t*>(smem_raw);                    // [warp][P][256]
     Key* tile = reinterpret_cast<Key*>(smem_raw + Cfg::hist_bytes);         // [DB][TS]
 
-    const int64_t row0 = (int64_t)blockIdx.x * RB;
-    const int64_t c0 = (int64_t)blockIdx.y * DB;
-    const int nr = (int)min64(RB, n - row0);
+    // Persistent over row blocks (one histogram flush per CTA instead of one
+    // per row block); blockIdx.x is the column block, so the CTAs that share
+    // the rows' cache lines run side by side.
+    const int64_t c0 = (int64_t)blockIdx.x * DB;
     const int nd = (int)min64(DB, d - c0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nrb = (n + RB - 1) / RB;
 
     for (int i = threadIdx.x; i < kWarps * P * kRadix; i += kThreads) h[i] = 0;
 
-    V v[PER];
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int idx = threadIdx.x + j * kThreads;
-        const int r = idx / DB, c = idx % DB;
-        v[j] = (r < nr && c < nd) ? X[(row0 + r) * ldx + c0 + c] : V(0);
-    }
     bool bad = false;
+    for (int64_t rb = blockIdx.y; rb < nrb; rb += gridDim.y) {
+        const int64_t row0 = rb * RB;
+        const int nr = (int)min64(RB, n - row0);
+        V v[PER];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int idx = threadIdx.x + j * kThreads;
-        const int r = idx / DB, c = idx % DB;
-        if (r < nr && c < nd) bad |= !finite_val(v[j]);
-        tile[c * TS + r] = to_key(v[j]);
-    }
-    if (bad) set_error(err, kErrNonfinite);
-    __syncthreads();
-
-    {
-        const int c = warp % DB, part = warp / DB;
-        uint32_t* hw = h + warp * P * kRadix;
-        const int rows_per = RB / Cfg::WPC;
-        const int rb = part * rows_per;
-        const bool colok = c < nd;
-        for (int r = rb + lane; r < rb + rows_per; r += 32) {
-            const bool ok = colok && r < nr;
-            const Key key = ok ? tile[c * TS + r] : Key(0);
+        for (int j = 0; j < PER; ++j) {
+            const int idx = threadIdx.x + j * kThreads;
+            const int r = idx / DB, c = idx % DB;
+            v[j] = (r < nr && c < nd) ? X[(row0 + r) * ldx + c0 + c] : V(0);
+        }
+        __syncthreads();   // the previous block's tile has been written out
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                const uint32_t digit = (uint32_t)(key >> (8 * q)) & 0xffu;
-                if (q >= P - 2) {
-                    const uint32_t peers = __match_any_sync(0xffffffffu, ok ? digit : 0x100u);
-                    if (ok && lane == __ffs(peers) - 1) atomicAdd(&hw[q * kRadix + digit], (uint32_t)__popc(peers));
-                } else if (ok) {
-                    atomicAdd(&hw[q * kRadix + digit], 1u);
+        for (int j = 0; j < PER; ++j) {
+            const int idx = threadIdx.x + j * kThreads;
+            const int r = idx / DB, c = idx % DB;
+            if (r < nr && c < nd) bad |= !finite_val(v[j]);
+            tile[c * TS + r] = to_key(v[j]);
+        }
+        __syncthreads();
+        {
+            const int c = warp % DB, part = warp / DB;
+            uint32_t* hw = h + warp * P * kRadix;
+            const int rows_per = RB / Cfg::WPC;
+            const int rbeg = part * rows_per;
+            const bool colok = c < nd;
+            for (int r = rbeg + lane; r < rbeg + rows_per; r += 32) {
+                const bool ok = colok && r < nr;
+                const Key key = ok ? tile[c * TS + r] : Key(0);
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const uint32_t digit = (uint32_t)(key >> (8 * q)) & 0xffu;
+                    if (q >= P - 2) {
+                        const uint32_t peers = digit_peers(digit, ok);
+                        if (ok && lane == __ffs(peers) - 1) atomicAdd(&hw[q * kRadix + digit], (uint32_t)__popc(peers));
+                    } else if (ok) {
+                        atomicAdd(&hw[q * kRadix + digit], 1u);
+                    }
                 }
             }
         }
+        for (int i = threadIdx.x; i < nd * RB; i += kThreads) {
+            const int cc = i / RB, r = i % RB;
+            if (r < nr) keys[(c0 + cc) * n + row0 + r] = tile[cc * TS + r];
+        }
     }
+    if (bad) set_error(err, kErrNonfinite);
     __syncthreads();
-    for (int i = threadIdx.x; i < nd * RB; i += kThreads) {
-        const int cc = i / RB, r = i % RB;
-        if (r < nr) keys[(c0 + cc) * n + row0 + r] = tile[cc * TS + r];
-    }
     for (int i = threadIdx.x; i < nd * P * kRadix; i += kThreads) {
         const int c = i / (P * kRadix), rest = i % (P * kRadix);
         uint32_t tot = 0;
@@ -183,7 +206,7 @@ keygen_hist_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64
 template <dm_dtype DT>
 struct PassCfg {
     using Key = typename Types<DT>::Key;
-    static constexpr int ITEMS = sizeof(Key) == 4 ? 16 : 8;   // keys per thread
+    static constexpr int ITEMS = sizeof(Key) == 4 ? 12 : 8;   // keys per thread
     static constexpr int TILE = kThreads * ITEMS;
 };
 
@@ -192,7 +215,7 @@ constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
 template <dm_dtype DT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
                 const int32_t* __restrict__ vals_in,            // null on the first pass
                 typename Types<DT>::Key* __restrict__ keys_out,
@@ -237,30 +260,31 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
     // original order.  Positions past n get digit 255 and land after every
     // real key of the tile; their global positions are >= n and are dropped.
     Key key[ITEMS];
-    int32_t val[ITEMS];
     uint32_t rank[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int64_t gi = tile0 + warp * 32 * ITEMS + j * 32 + lane;
-        if (gi < n) {
-            key[j] = keys_in[seg + gi];
-            val[j] = first ? (int32_t)gi : vals_in[seg + gi];
-        } else {
-            key[j] = ~(Key)0;
-            val[j] = -1;
-        }
+        key[j] = gi < n ? keys_in[seg + gi] : ~(Key)0;
     }
+    // Stable ranks within the warp: item j of every lane is ranked after all
+    // items j' < j of the warp and after lower lanes' item j.  All matches are
+    // issued first; then the lowest lane of each group of equal digits adds the
+    // group size to the warp's counter with an atomic that returns the prior
+    // count (one warp's shared atomics take effect in program order, so the
+    // counts stay in item order) and hands it to its peers.
     const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t peers[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) peers[j] = digit_peers((uint32_t)(key[j] >> shift) & 0xffu, true);
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t dg = (uint32_t)(key[j] >> shift) & 0xffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t prior = wcount[warp][dg];
-        rank[j] = prior + __popc(peers & lt_mask);
-        __syncwarp();
-        if ((peers & lt_mask) == 0) wcount[warp][dg] = prior + __popc(peers);
-        __syncwarp();
+        rank[j] = 0;
+        if ((peers[j] & lt_mask) == 0) rank[j] = atomicAdd(&wcount[warp][dg], (uint32_t)__popc(peers[j]));
     }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+        rank[j] = __shfl_sync(0xffffffffu, rank[j], __ffs(peers[j]) - 1) + __popc(peers[j] & lt_mask);
     __syncthreads();
 
     // Per digit: exclusive offsets of the warps, and the tile's count.
@@ -279,18 +303,32 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
         st_relaxed(&lb[tid], kFlagInc | cnt);
     } else {
         st_relaxed(&lb[(int64_t)t * kRadix + tid], kFlagAgg | cnt);
-        int pred = t - 1;
+        // Predecessors are read W at a time (one round trip per window); a
+        // tile that has not published yet is waited for (bounded), and the
+        // walk stops at the first inclusive count.
+        constexpr int W = 8;
+        int base = t - 1;
         uint32_t spins = 0;
-        while (true) {
-            const uint32_t s = ld_relaxed(&lb[(int64_t)pred * kRadix + tid]);
-            if ((s & ~kValMask) == 0) {
-                if (++spins > kSpinLimit) { set_error(err, kErrTimeout); break; }
-                __nanosleep(64);
-                continue;
+        bool done = false;
+        while (!done) {
+            uint32_t sv[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                sv[u] = base - u >= 0 ? ld_relaxed(&lb[(int64_t)(base - u) * kRadix + tid]) : kFlagInc;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (!done) {
+                    uint32_t sq = sv[u];
+                    while ((sq & ~kValMask) == 0) {
+                        if (++spins > kSpinLimit) { set_error(err, kErrTimeout); sq = kFlagInc; break; }
+                        __nanosleep(64);
+                        sq = ld_relaxed(&lb[(int64_t)(base - u) * kRadix + tid]);
+                    }
+                    excl += sq & kValMask;
+                    if ((sq & ~kValMask) == kFlagInc) done = true;
+                }
             }
-            excl += s & kValMask;
-            if ((s & ~kValMask) == kFlagInc || pred == 0) break;
-            --pred;
+            base -= W;
         }
         st_relaxed(&lb[(int64_t)t * kRadix + tid], kFlagInc | (excl + cnt));
     }
@@ -301,12 +339,17 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
     gbase[tid] = digit_start + excl - ts;   // global = gbase[digit] + tile position
     __syncthreads();
 
+    // Tile positions; the payload is read only now, straight to its slot.
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t dg = (uint32_t)(key[j] >> shift) & 0xffu;
-        const uint32_t pos = tile_start[dg] + wcount[warp][dg] + rank[j];
-        sk[pos] = key[j];
-        sv[pos] = val[j];
+        rank[j] += tile_start[dg] + wcount[warp][dg];
+        sk[rank[j]] = key[j];
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int64_t gi = tile0 + warp * 32 * ITEMS + j * 32 + lane;
+        sv[rank[j]] = gi < n ? (first ? (int32_t)gi : vals_in[seg + gi]) : -1;
     }
     __syncthreads();
 
@@ -336,7 +379,13 @@ cudaError_t launch_keygen_t(const SortArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg::smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((a.n + Cfg::RB - 1) / Cfg::RB), (unsigned)((a.d + Cfg::DB - 1) / Cfg::DB));
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t cb = (a.d + Cfg::DB - 1) / Cfg::DB;
+    const int64_t nrb = (a.n + Cfg::RB - 1) / Cfg::RB;
+    const int64_t per_col = std::max<int64_t>(1, std::min<int64_t>(nrb, (3 * (int64_t)sms + cb - 1) / cb));
+    dim3 grid((unsigned)cb, (unsigned)per_col);
     kern<<<grid, kThreads, Cfg::smem, s>>>(
         static_cast<const typename Types<DT>::V*>(a.X), a.n, a.d, a.ldx,
         static_cast<typename Types<DT>::Key*>(a.keys_a), a.hist, a.err);

@@ -8,8 +8,8 @@
 //            Appendix A (in the mu-shifted frame; the product is translation
 //            invariant).  Each CTA reduces a contiguous row range: rows arrive
 //            in chunks through a double-buffered cp.async pipeline, each thread
-//            owns a 2 x 4 block of the result (FP32 or exact int64 within a
-//            chunk, chunk sums added in the Wide type), the CTA writes one
+//            owns a 4 x 4 block of the result (FP32 or exact int64 over 8
+//            chunks, then added in the Wide type), the CTA writes one
 //            partial and a finalize kernel adds the partials in a fixed order.
 //            With s omitted the same kernel gives u and W alone.
 // l2prep  -- column means mu (the frame shift), FP64 sums, fixed order.
@@ -27,9 +27,11 @@ namespace dm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunk = 64;   // rows staged in shared memory per step
-constexpr int RC = 2;        // output rows (of X-hat) per thread
+constexpr int kChunk = 128;  // rows staged in shared memory per step
+constexpr int RC = 4;        // output rows (of X-hat) per thread
 constexpr int RJ = 4;        // output columns (of Z) per thread
+
+__host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 
 __device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
@@ -59,28 +61,85 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
-// s = ||x - mu||^2 of one staged row (x already shifted), one fixed order.
+// Four consecutive shared-memory elements (16-byte aligned for 4-byte types).
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+    const float4 u = *reinterpret_cast<const float4*>(p);
+    v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const long long* p, long long (&v)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = p[q];
+}
+
+// s = ||x - mu||^2 of one staged row (x already shifted), by four adjacent
+// lanes: lane `part` sums columns part, part + 4, ...; the four partials are
+// combined as (p0 + p1) + (p2 + p3).  The reduce and the apply kernels use
+// this same function, so both see identical s_i.  All 32 lanes must call it.
 template <class Acc>
-__device__ __forceinline__ Acc row_sqnorm(const Acc* xrow, int d) {
-    Acc acc = 0;
-    for (int c = 0; c < d; ++c) acc = fma_acc(xrow[c], xrow[c], acc);
-    return acc;
+__device__ __forceinline__ Acc row_sqnorm4(const Acc* xrow, int d, int part) {
+    Acc a = 0;
+    for (int c = part; c < d; c += 4) a = fma_acc(xrow[c], xrow[c], a);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    return a;
+}
+
+// Calls f(r, c) for every (row, column) of a rows x w block, the columns of
+// a row on adjacent threads, with one division per thread instead of one per
+// element: thread t takes column t % w of rows t / w, t / w + 256 / w, ...
+// (w <= 256), or columns t, t + 256, ... of every row (w > 256).
+template <class F>
+__device__ __forceinline__ void for_each_rc(int rows, int w, F&& f) {
+    if (w <= kThreads) {
+        const int per = kThreads / w;
+        if (threadIdx.x >= per * w) return;
+        const int c = threadIdx.x % w;
+        for (int r = threadIdx.x / w; r < rows; r += per) f(r, c);
+    } else {
+        for (int r = 0; r < rows; ++r)
+            for (int c = threadIdx.x; c < w; c += kThreads) f(r, c);
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* s, const void* g, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(sa), "l"(g), "r"(bytes) : "memory");
+}
+
+// Copy rows [base, base + nr) of a row-major matrix (w elements of type T per
+// row, leading dimension ld) into a dense [kChunk or R][w] shared buffer: as
+// 16-byte pieces when every row start is 16-byte aligned (vec16), else one
+// element at a time.  Rows past nr are zero-filled.
+template <class T>
+__device__ __forceinline__ void stage_rows(T* dst, const T* src, int64_t ld, int w, int64_t base,
+                                           int rows, int nr, bool vec16) {
+    if (vec16) {
+        const int pr = w * (int)sizeof(T) / 16;    // pieces per row
+        for_each_rc(rows, pr, [&](int r, int q) {
+            const bool ok = r < nr;
+            cp_async16(reinterpret_cast<char*>(dst + r * w) + 16 * q,
+                       reinterpret_cast<const char*>(src + (ok ? (base + r) * ld : 0)) + 16 * q,
+                       ok ? 16 : 0);
+        });
+    } else {
+        for_each_rc(rows, w, [&](int r, int c) {
+            const bool ok = r < nr;
+            cp_async<sizeof(T)>(dst + r * w + c, src + (ok ? (base + r) * ld + c : 0), ok);
+        });
+    }
 }
 
 // Stage rows [base, base + nr) of X and Z (raw element types) into one buffer.
 template <class XT, class V>
 __device__ __forceinline__ void stage_chunk(XT* xr, V* zr, const XT* X, int64_t ldx, int d,
-                                            const V* Z, int64_t ldz, int k, int64_t base, int nr) {
-    for (int i = threadIdx.x; i < kChunk * d; i += kThreads) {
-        const int r = i / d, c = i % d;
-        const bool ok = r < nr;
-        cp_async<sizeof(XT)>(xr + r * d + c, X + (ok ? (base + r) * ldx + c : 0), ok);
-    }
-    for (int i = threadIdx.x; i < kChunk * k; i += kThreads) {
-        const int r = i / k, j = i % k;
-        const bool ok = r < nr;
-        cp_async<sizeof(V)>(zr + r * k + j, Z + (ok ? (base + r) * ldz + j : 0), ok);
-    }
+                                            const V* Z, int64_t ldz, int k, int64_t base, int nr,
+                                            bool xv16, bool zv16) {
+    stage_rows(xr, X, ldx, d, base, kChunk, nr, xv16);
+    stage_rows(zr, Z, ldz, k, base, kChunk, nr, zv16);
     cp_commit();
 }
 
@@ -89,13 +148,14 @@ __global__ void __launch_bounds__(kThreads)
 reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
               const typename Types<DT>::V* __restrict__ mu, int64_t mu_stride, int with_s,
               const typename Types<DT>::V* __restrict__ Z, int k, int64_t ldz,
-              typename Types<DT>::Wide* __restrict__ partial, int64_t rows_per_block) {
+              typename Types<DT>::Wide* __restrict__ partial, int64_t rows_per_block,
+              int xv16, int zv16) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int D2 = d + 2;
-    const int D2P = D2 + 1, KP = k + 1;
+    const int D2P = round4(D2), KP = round4(k);   // 16-byte aligned rows, zero padded
     // layout: raw buffers [2][kChunk*d] XT, [2][kChunk*k] V; xh [kChunk][D2P] Acc;
     //         zc [kChunk][KP] Acc; mu_s [d] Acc; red [D2*k] Wide
     size_t off = 0;
@@ -121,17 +181,32 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
     const int ob_per_thread = (OB + kThreads - 1) / kThreads;
     const int my_rg = (OB >= kThreads) ? 0 : threadIdx.x / OB;
 
+    // Block sums stay in the element type for kFlush chunks, then go into the
+    // Wide accumulators (the FP64 pipe is far narrower than FP32).
+    constexpr int kFlush = 8;
     Wide wacc[MAXOB][RC][RJ];
+    Acc cacc[MAXOB][RC][RJ];
 #pragma unroll
     for (int b = 0; b < MAXOB; ++b)
 #pragma unroll
         for (int a = 0; a < RC; ++a)
 #pragma unroll
-            for (int q = 0; q < RJ; ++q) wacc[b][a][q] = 0;
+            for (int q = 0; q < RJ; ++q) { wacc[b][a][q] = 0; cacc[b][a][q] = 0; }
+
+    // This thread's output blocks (fixed for the whole row range).
+    bool bact[MAXOB];
+    int bcb[MAXOB], bjb[MAXOB];
+#pragma unroll
+    for (int b = 0; b < MAXOB; ++b) {
+        const int ob = (OB >= kThreads) ? threadIdx.x + b * kThreads : threadIdx.x % OB;
+        bact[b] = b < ob_per_thread && ob < OB && my_rg < RG;
+        bcb[b] = (ob / OBj) * RC;
+        bjb[b] = (ob % OBj) * RJ;
+    }
 
     const int nchunks = (int)((r1 - r0 + kChunk - 1) / kChunk);
     if (nchunks > 0)
-        stage_chunk(xraw, zraw, X, ldx, d, Z, ldz, k, r0, (int)min64(kChunk, r1 - r0));
+        stage_chunk(xraw, zraw, X, ldx, d, Z, ldz, k, r0, (int)min64(kChunk, r1 - r0), xv16, zv16);
     for (int ch = 0; ch < nchunks; ++ch) {
         const int64_t base = r0 + (int64_t)ch * kChunk;
         const int nr = (int)min64(kChunk, r1 - base);
@@ -139,7 +214,7 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
         if (ch + 1 < nchunks) {
             const int64_t nb = base + kChunk;
             stage_chunk(xraw + (buf ^ 1) * kChunk * d, zraw + (buf ^ 1) * kChunk * k, X, ldx, d, Z,
-                        ldz, k, nb, (int)min64(kChunk, r1 - nb));
+                        ldz, k, nb, (int)min64(kChunk, r1 - nb), xv16, zv16);
             cp_wait<1>();
         } else {
             cp_wait<0>();
@@ -147,47 +222,46 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
         __syncthreads();
         const XT* xb = xraw + buf * kChunk * d;
         const V* zb = zraw + buf * kChunk * k;
-        for (int i = threadIdx.x; i < kChunk * d; i += kThreads) {
-            const int r = i / d, c = i % d;
-            xh[r * D2P + c] = (r < nr) ? to_acc(xb[i], Acc()) - mu_s[c] : Acc(0);
-        }
-        for (int i = threadIdx.x; i < kChunk * k; i += kThreads) {
-            const int r = i / k, j = i % k;
-            zc[r * KP + j] = (r < nr) ? to_acc(zb[i], Acc()) : Acc(0);
-        }
+        for_each_rc(kChunk, d, [&](int r, int c) {
+            xh[r * D2P + c] = (r < nr) ? to_acc(xb[r * d + c], Acc()) - mu_s[c] : Acc(0);
+        });
+        for_each_rc(kChunk, KP, [&](int r, int j) {
+            zc[r * KP + j] = (r < nr && j < k) ? to_acc(zb[r * k + j], Acc()) : Acc(0);
+        });
         __syncthreads();
-        if (threadIdx.x < kChunk) {
-            const int r = threadIdx.x;
-            xh[r * D2P + d] = r < nr ? Acc(1) : Acc(0);
-            xh[r * D2P + d + 1] = (with_s && r < nr) ? row_sqnorm(xh + r * D2P, d) : Acc(0);
+        static_assert(kChunk % (kThreads / 4) == 0, "four lanes per staged row");
+        for (int r = threadIdx.x >> 2; r < kChunk; r += kThreads / 4) {
+            const int part = threadIdx.x & 3;
+            const Acc sq = row_sqnorm4(xh + r * D2P, d, part);
+            if (part == 0) {
+                xh[r * D2P + d] = r < nr ? Acc(1) : Acc(0);
+                xh[r * D2P + d + 1] = (with_s && r < nr) ? sq : Acc(0);
+            } else if (D2 + part - 1 < D2P) {
+                xh[r * D2P + D2 + part - 1] = Acc(0);   // padding columns
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int b = 0; b < MAXOB; ++b) {
-            if (b >= ob_per_thread) break;
-            const int ob = (OB >= kThreads) ? threadIdx.x + b * kThreads : threadIdx.x % OB;
-            if (ob >= OB || my_rg >= RG) continue;
-            const int cb = (ob / OBj) * RC, jb = (ob % OBj) * RJ;
-            Acc acc[RC][RJ];
-#pragma unroll
-            for (int a = 0; a < RC; ++a)
-#pragma unroll
-                for (int q = 0; q < RJ; ++q) acc[a][q] = 0;
+            if (!bact[b]) continue;
+            const int cb = bcb[b], jb = bjb[b];
             for (int r = my_rg; r < kChunk; r += RG) {
                 Acc xv[RC], zv[RJ];
-#pragma unroll
-                for (int a = 0; a < RC; ++a) xv[a] = (cb + a < D2) ? xh[r * D2P + cb + a] : Acc(0);
-#pragma unroll
-                for (int q = 0; q < RJ; ++q) zv[q] = (jb + q < k) ? zc[r * KP + jb + q] : Acc(0);
+                load4(xh + r * D2P + cb, xv);
+                load4(zc + r * KP + jb, zv);
 #pragma unroll
                 for (int a = 0; a < RC; ++a)
 #pragma unroll
-                    for (int q = 0; q < RJ; ++q) acc[a][q] = fma_acc(xv[a], zv[q], acc[a][q]);
+                    for (int q = 0; q < RJ; ++q) cacc[b][a][q] = fma_acc(xv[a], zv[q], cacc[b][a][q]);
             }
+        }
+        if ((ch + 1) % kFlush == 0 || ch + 1 == nchunks) {
 #pragma unroll
-            for (int a = 0; a < RC; ++a)
+            for (int b = 0; b < MAXOB; ++b)
 #pragma unroll
-                for (int q = 0; q < RJ; ++q) wacc[b][a][q] += (Wide)acc[a][q];
+                for (int a = 0; a < RC; ++a)
+#pragma unroll
+                    for (int q = 0; q < RJ; ++q) { wacc[b][a][q] += (Wide)cacc[b][a][q]; cacc[b][a][q] = 0; }
         }
         __syncthreads();
     }
@@ -241,7 +315,7 @@ colsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int
               uint32_t* err) {
     using Wide = typename Types<DT>::Wide;
     using V = typename Types<DT>::V;
-    constexpr int U = 8;
+    constexpr int U = 16;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min64(n, r0 + rows_per_block);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -263,11 +337,15 @@ colsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int
                     const int64_t rr = r + (int64_t)u * rg;
                     v[u] = rr < r1 ? X[rr * ldx + c] : V(0);
                 }
+                // U values summed in the element type, then one Wide add (the
+                // FP64 pipe is far narrower than FP32 on this GPU).
+                V part = V(0);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     bad |= !finite_val(v[u]);
-                    acc += (Wide)v[u];
+                    part += v[u];
                 }
+                acc += (Wide)part;
             }
         }
         red[threadIdx.x] = acc;
@@ -301,51 +379,53 @@ __global__ void mean_finalize_kernel(const typename Types<DT>::Wide* __restrict_
 // (row pair, column quad) accumulates s_i u + v - 2 (x_i - mu) . W.
 constexpr int kApplyRows = 128;
 
-template <dm_dtype DT>
+template <dm_dtype DT, bool VST>
 __global__ void __launch_bounds__(kThreads)
 l2apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int64_t ldx,
                const typename Types<DT>::V* __restrict__ mu,
                const typename Types<DT>::Wide* __restrict__ res, int k,
-               typename Types<DT>::Out* __restrict__ out, int64_t ldo) {
+               typename Types<DT>::Out* __restrict__ out, int64_t ldo, int xv16) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Out = typename Types<DT>::Out;
     constexpr int R = kApplyRows;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int DP = d + 1;
+    const int DP = round4(d) + 4, KP = round4(k);   // DP: 16-byte rows, bank-spread
+    const int DR = round4(d);                         // columns read (zero padded)
     size_t off = 0;
     V* xraw = reinterpret_cast<V*>(smem_raw);                      // [2][R*d]
     off += ((2 * (size_t)R * d * sizeof(V)) + 15) & ~size_t(15);
-    Acc* Wm2 = reinterpret_cast<Acc*>(smem_raw + off);             // -2 W, d x k
-    off += (((size_t)d * k * sizeof(Acc)) + 15) & ~size_t(15);
-    Acc* uv = reinterpret_cast<Acc*>(smem_raw + off);              // u (k), v (k)
-    off += (((size_t)2 * k * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* Wm2 = reinterpret_cast<Acc*>(smem_raw + off);             // -2 W, d x KP (zero padded)
+    off += (((size_t)d * KP * sizeof(Acc)) + 15) & ~size_t(15);
+    Acc* uv = reinterpret_cast<Acc*>(smem_raw + off);              // u (KP), v (KP)
+    off += (((size_t)2 * KP * sizeof(Acc)) + 15) & ~size_t(15);
     Acc* xt = reinterpret_cast<Acc*>(smem_raw + off);              // R x DP shifted rows
     off += (((size_t)R * DP * sizeof(Acc)) + 15) & ~size_t(15);
     Acc* mu_s = reinterpret_cast<Acc*>(smem_raw + off);
     off += (((size_t)d * sizeof(Acc)) + 15) & ~size_t(15);
     Acc* s_s = reinterpret_cast<Acc*>(smem_raw + off);             // R
 
-    for (int i = threadIdx.x; i < d * k; i += kThreads) Wm2[i] = (Acc)(-2 * res[i]);
-    for (int i = threadIdx.x; i < 2 * k; i += kThreads) uv[i] = (Acc)res[d * k + i];
+    for (int i = threadIdx.x; i < DR * KP; i += kThreads) {
+        const int c = i / KP, j = i % KP;
+        Wm2[i] = (j < k && c < d) ? (Acc)(-2 * res[c * k + j]) : Acc(0);
+    }
+    for (int i = threadIdx.x; i < 2 * KP; i += kThreads) {
+        const int h = i / KP, j = i % KP;
+        uv[i] = j < k ? (Acc)res[d * k + h * k + j] : Acc(0);
+    }
     for (int c = threadIdx.x; c < d; c += kThreads) mu_s[c] = to_acc(mu[c], Acc());
 
     const int64_t tiles = (n + R - 1) / R;
     auto stage = [&](int64_t tile, int buf) {
         const int64_t row0 = tile * R;
         const int nr = (int)min64(R, n - row0);
-        V* xr = xraw + (size_t)buf * R * d;
-        for (int i = threadIdx.x; i < R * d; i += kThreads) {
-            const int r = i / d, c = i % d;
-            const bool ok = r < nr;
-            cp_async<sizeof(V)>(xr + i, X + (ok ? (row0 + r) * ldx + c : 0), ok);
-        }
+        stage_rows(xraw + (size_t)buf * R * d, X, ldx, d, row0, R, nr, xv16 != 0);
         cp_commit();
     };
     int64_t tile = blockIdx.x;
     if (tile < tiles) stage(tile, 0);
     int buf = 0;
-    const int QJ = (k + RJ - 1) / RJ;                 // column quads
+    const int QJ = KP / RJ;                           // column quads
     for (; tile < tiles; tile += gridDim.x, buf ^= 1) {
         const int64_t next = tile + gridDim.x;
         if (next < tiles) { stage(next, buf ^ 1); cp_wait<1>(); }
@@ -354,39 +434,53 @@ l2apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, in
         const int64_t row0 = tile * R;
         const int nr = (int)min64(R, n - row0);
         const V* xr = xraw + (size_t)buf * R * d;
-        for (int i = threadIdx.x; i < R * d; i += kThreads) {
-            const int r = i / d, c = i % d;
-            xt[r * DP + c] = (r < nr) ? to_acc(xr[i], Acc()) - mu_s[c] : Acc(0);
-        }
+        for_each_rc(R, DR, [&](int r, int c) {
+            xt[r * DP + c] = (r < nr && c < d) ? to_acc(xr[r * d + c], Acc()) - mu_s[c] : Acc(0);
+        });
         __syncthreads();
-        if (threadIdx.x < R) s_s[threadIdx.x] = row_sqnorm(xt + threadIdx.x * DP, d);
+        for (int r = threadIdx.x >> 2; r < R; r += kThreads / 4) {
+            const Acc sq = row_sqnorm4(xt + r * DP, d, threadIdx.x & 3);
+            if ((threadIdx.x & 3) == 0) s_s[r] = sq;
+        }
         __syncthreads();
         for (int w = threadIdx.x; w < (R / 2) * QJ; w += kThreads) {
             const int rp = w / QJ, jq = w % QJ;
             const int ra = 2 * rp, jb = jq * RJ;
-            Acc acc[2][RJ];
+            Acc acc[2][RJ], u4[RJ], v4[RJ];
+            load4(uv + jb, u4);
+            load4(uv + KP + jb, v4);
             const Acc s0 = s_s[ra], s1 = s_s[ra + 1];
 #pragma unroll
             for (int q = 0; q < RJ; ++q) {
-                const int j = min(jb + q, k - 1);
-                const Acc base = uv[k + j];
-                acc[0][q] = fma_acc(s0, uv[j], base);
-                acc[1][q] = fma_acc(s1, uv[j], base);
+                acc[0][q] = fma_acc(s0, u4[q], v4[q]);
+                acc[1][q] = fma_acc(s1, u4[q], v4[q]);
             }
-            for (int c = 0; c < d; ++c) {
-                const Acc x0 = xt[ra * DP + c], x1 = xt[(ra + 1) * DP + c];
+            for (int c0 = 0; c0 < DR; c0 += 4) {
+                Acc x0[4], x1[4];
+                load4(xt + ra * DP + c0, x0);
+                load4(xt + (ra + 1) * DP + c0, x1);
 #pragma unroll
-                for (int q = 0; q < RJ; ++q) {
-                    const Acc wv = Wm2[c * k + min(jb + q, k - 1)];
-                    acc[0][q] = fma_acc(x0, wv, acc[0][q]);
-                    acc[1][q] = fma_acc(x1, wv, acc[1][q]);
+                for (int cc = 0; cc < 4; ++cc) {
+                    Acc wv[RJ];
+                    load4(Wm2 + (c0 + cc) * KP + jb, wv);
+#pragma unroll
+                    for (int q = 0; q < RJ; ++q) {
+                        acc[0][q] = fma_acc(x0[cc], wv[q], acc[0][q]);
+                        acc[1][q] = fma_acc(x1[cc], wv[q], acc[1][q]);
+                    }
                 }
             }
 #pragma unroll
-            for (int q = 0; q < RJ; ++q) {
-                if (jb + q >= k) break;
-                if (ra < nr) out[(row0 + ra) * ldo + jb + q] = (Out)acc[0][q];
-                if (ra + 1 < nr) out[(row0 + ra + 1) * ldo + jb + q] = (Out)acc[1][q];
+            for (int h = 0; h < 2; ++h) {
+                if (ra + h >= nr) break;
+                Out* o = out + (row0 + ra + h) * ldo + jb;
+                if constexpr (VST) {
+                    *reinterpret_cast<float4*>(o) = make_float4(acc[h][0], acc[h][1], acc[h][2], acc[h][3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < RJ; ++q)
+                        if (jb + q < k) o[q] = (Out)acc[h][q];
+                }
             }
         }
         __syncthreads();
@@ -401,7 +495,7 @@ size_t reduce_smem(int d, int k) {
     auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
     const int D2 = d + 2;
     return up(2 * (size_t)kChunk * d * sizeof(XT)) + up(2 * (size_t)kChunk * k * sizeof(V)) +
-           up((size_t)kChunk * (D2 + 1) * sizeof(Acc)) + up((size_t)kChunk * (k + 1) * sizeof(Acc)) +
+           up((size_t)kChunk * round4(D2) * sizeof(Acc)) + up((size_t)kChunk * round4(k) * sizeof(Acc)) +
            up((size_t)d * sizeof(Acc)) + sizeof(Wide) * (size_t)D2 * k;
 }
 
@@ -413,20 +507,29 @@ int sm_count(int hint) {
     return sms;
 }
 
+bool rows16(const void* p, int64_t ld, int64_t w, size_t es) {
+    return reinterpret_cast<uintptr_t>(p) % 16 == 0 && (ld * es) % 16 == 0 && (w * es) % 16 == 0;
+}
+
 template <dm_dtype DT, class XT, int MAXOB>
 cudaError_t reduce_launch_t(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
     using V = typename Types<DT>::V;
     using Wide = typename Types<DT>::Wide;
-    const int blocks = reduce_blocks(a);
-    const int64_t rpb = (a.n + blocks - 1) / blocks;
     const size_t smem = reduce_smem<DT, XT>((int)a.d, (int)a.k);
     auto kern = reduce_kernel<DT, XT, MAXOB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    // One wave: no tail of partially filled SMs (at most reduce_blocks()).
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(
+        reduce_blocks(a), (int64_t)std::max(occ, 1) * sm_count(a.num_sms)));
+    const int64_t rpb = (a.n + blocks - 1) / blocks;
     kern<<<blocks, kThreads, smem, st>>>(
         static_cast<const XT*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const V*>(a.mu), a.mu_stride,
         a.with_s ? 1 : 0, static_cast<const V*>(a.Z), (int)a.k, a.ldz, static_cast<Wide*>(a.partial),
-        rpb);
+        rpb, rows16(a.X, a.ldx, a.d, sizeof(XT)) ? 1 : 0, rows16(a.Z, a.ldz, a.k, sizeof(V)) ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int total = (int)((a.d + 2) * a.k);
     const int warps_per_block = 8;
@@ -515,10 +618,14 @@ cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* lau
     using Out = typename Types<DT>::Out;
     auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
     const int R = kApplyRows;
-    const size_t smem = up(2 * (size_t)R * a.d * sizeof(V)) + up((size_t)a.d * a.k * sizeof(Acc)) +
-                        up(2 * (size_t)a.k * sizeof(Acc)) + up((size_t)R * (a.d + 1) * sizeof(Acc)) +
+    const int KP = round4((int)a.k);
+    const int DR = round4((int)a.d);
+    const size_t smem = up(2 * (size_t)R * a.d * sizeof(V)) + up((size_t)DR * KP * sizeof(Acc)) +
+                        up(2 * (size_t)KP * sizeof(Acc)) + up((size_t)R * (DR + 4) * sizeof(Acc)) +
                         up((size_t)a.d * sizeof(Acc)) + (size_t)R * sizeof(Acc);
-    auto kern = l2apply_kernel<DT>;
+    const bool vst = sizeof(Out) == 4 && a.k % 4 == 0 && a.ldo % 4 == 0 &&
+                     reinterpret_cast<uintptr_t>(a.out) % 16 == 0;
+    auto kern = vst ? l2apply_kernel<DT, true> : l2apply_kernel<DT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -528,7 +635,8 @@ cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* lau
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(occ, 1) * num_sms));
     kern<<<(unsigned)blocks, kThreads, smem, st>>>(
         static_cast<const V*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const V*>(a.mu),
-        static_cast<const Wide*>(a.res), (int)a.k, static_cast<Out*>(a.out), a.ldo);
+        static_cast<const Wide*>(a.res), (int)a.k, static_cast<Out*>(a.out), a.ldo,
+        rows16(a.X, a.ldx, a.d, sizeof(V)) ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
     return cudaSuccess;
@@ -541,9 +649,9 @@ bool reduce_supported(int64_t d, int64_t k) {
     if (OB > 4 * kThreads || d > 4096 || k > 4096) return false;
     // shared memory of the reduce kernel (FP64/int64 worst case)
     const size_t smem = 2 * (size_t)kChunk * d * 8 + 2 * (size_t)kChunk * k * 8 +
-                        (size_t)kChunk * (d + 3) * 8 + (size_t)kChunk * (k + 1) * 8 + (size_t)d * 8 +
+                        (size_t)kChunk * (d + 6) * 8 + (size_t)kChunk * (k + 4) * 8 + (size_t)d * 8 +
                         8 * (size_t)(d + 2) * k + 96;
-    return smem <= 200 * 1024;
+    return smem <= 220 * 1024;
 }
 
 int reduce_blocks(const ReduceArgs& a) {

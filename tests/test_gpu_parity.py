@@ -254,14 +254,18 @@ def test_matvec_entry_points_reject_wrong_metric(dm, ctx):
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
 def test_nonfinite_rejected(dm, ctx, metric):
+    # l1 reports it from dm_prepare (which synchronizes), squared l2 from the
+    # next dm_sync.
     X = inputs.uniform_points(1000, 3, 1, dtype=np.float32)
     X[17, 1] = np.nan
     with pytest.raises(dm.DMError) as e:
         dm.dm_prepare(ctx, metric, dev(X))
+        dm.dm_sync(ctx)
     assert e.value.status == dm.DM_ERR_NONFINITE
     X[17, 1] = np.inf
     with pytest.raises(dm.DMError):
         dm.dm_prepare(ctx, metric, dev(X))
+        dm.dm_sync(ctx)
     # the context stays usable
     X[17, 1] = 0.5
     Z = inputs.gaussian_queries(1000, 2, 1)
