@@ -165,6 +165,33 @@ dm_status dm_profile_enable(dm_ctx* ctx, int enable);
 dm_status dm_profile_read(dm_ctx* ctx, int max, int* count, char* names,
                           int64_t* launches, double* total_ms);
 
+/* out = A Z for the squared-l2 metric (the same product as dm_prepare with
+ * DM_L2SQ followed by dm_matmat) for callers that cannot allocate device
+ * memory when they call in -- code running inside a memory pool or arena it
+ * does not own, or on a path where an allocation (which can synchronize the
+ * device) is not allowed.  The paper has no counterpart: this is an
+ * interface variant only.
+ *   - Needs no context and allocates nothing (no cudaMalloc / cudaFree, no
+ *     allocating library call).  Its scratch is one file-scope device array
+ *     of a little under 3 MiB that every GPU loading this library holds
+ *     until the process exits.
+ *   - Limits: 1 <= d <= 32 and 1 <= k <= 32 (larger sizes return
+ *     DM_ERR_UNSUPPORTED before any work), n < 2^30; X, Z, out are device
+ *     pointers as in the other calls; the work is issued on cuda_stream on
+ *     the current device.
+ *   - The first call on a device looks up the scratch's device address once
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - Every call shares the one scratch array and it keeps the last call's
+ *     contents (nothing in it needs to start at zero).  Calls that overlap on
+ *     the GPU -- on different streams, or from different host threads --
+ *     race on it and give wrong results: order them.
+ *   - Non-finite coordinates are not reported (there is no error word); the
+ *     result is then non-finite.  Launch failures return DM_ERR_CUDA. */
+dm_status dm_l2sq_matmat_noalloc(dm_dtype dtype, const void* X, int64_t n, int64_t d,
+                                 int64_t ldx, const void* Z, int64_t k, int64_t ldz,
+                                 void* out, int64_t ldo, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

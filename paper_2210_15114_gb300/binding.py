@@ -76,6 +76,7 @@ def load() -> ctypes.CDLL:
             "dm_launch_count": ([P], I64),
             "dm_profile_enable": ([P, I32], I32),
             "dm_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int), P, P, P], I32),
+            "dm_l2sq_matmat_noalloc": ([I32, P, I64, I64, I64, P, I64, I64, P, I64, P], I32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -324,3 +325,22 @@ def dm_profile_read(ctx: Context, max_groups: int = 32) -> dict:
         name = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
         out[name] = (int(launches[i]), float(total[i]))
     return out
+
+
+def dm_l2sq_matmat_noalloc(X, Z, out, stream=None) -> None:
+    """dm_l2sq_matmat_noalloc: the squared-l2 product A Z into the caller's
+    `out` without any allocation by the library (its scratch is a fixed
+    device array; see include/dm.h for the limits and the sharing rules)."""
+    import torch
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    Z2 = Z.reshape(-1, 1) if Z.ndim == 1 else Z
+    o2 = out.reshape(-1, 1) if out.ndim == 1 else out
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device).cuda_stream
+    n, d = X.shape
+    k = Z2.shape[1]
+    _check(load().dm_l2sq_matmat_noalloc(dtype_code(X.dtype), ctypes.c_void_p(_dev_ptr(X)), n, d,
+                                         _ld(X), ctypes.c_void_p(_dev_ptr(Z2)), k, _ld(Z2),
+                                         ctypes.c_void_p(_dev_ptr(o2)), _ld(o2),
+                                         ctypes.c_void_p(stream)), "dm_l2sq_matmat_noalloc")

@@ -98,6 +98,7 @@ struct ReduceArgs {
     void* partial;                       // scratch: blocks x (d+2) x k Wide
     void* res;                           // (d+2) x k Wide
     int num_sms;
+    int max_blocks;                      // 0: no cap beyond the default
 };
 bool reduce_supported(int64_t d, int64_t k);
 int reduce_blocks(const ReduceArgs& a);
@@ -114,7 +115,8 @@ struct L2PrepArgs {
     const void* X; int64_t n, d, ldx;
     void* partial;                       // scratch: blocks x d Wide
     void* mu;                            // d entries, V type
-    uint32_t* err;
+    uint32_t* err;                       // may be null (non-finite input not reported)
+    int max_blocks;                      // 0: no cap beyond the default
 };
 int l2prep_blocks(const L2PrepArgs& a);
 cudaError_t l2prep_launch(const L2PrepArgs& a, cudaStream_t s, int64_t* launches);

@@ -20,6 +20,7 @@
 // contraction does 2(d+2)k flops per (4d + 4k) bytes read, below the FP32
 // ALU ridge, so they run on the CUDA cores.
 #include <algorithm>
+#include <mutex>
 
 #include "dm_internal.h"
 
@@ -357,7 +358,7 @@ colsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int
         }
         __syncthreads();
     }
-    if (bad) set_error(err, kErrNonfinite);
+    if (bad && err) set_error(err, kErrNonfinite);
 }
 
 template <dm_dtype DT>
@@ -656,14 +657,18 @@ bool reduce_supported(int64_t d, int64_t k) {
 
 int reduce_blocks(const ReduceArgs& a) {
     const int sms = sm_count(a.num_sms);
+    int64_t cap = 3 * (int64_t)sms;
+    if (a.max_blocks > 0) cap = std::min<int64_t>(cap, a.max_blocks);
     const int64_t want = (a.n + 1023) / 1024;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 3 * sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
 
 int l2prep_blocks(const L2PrepArgs& a) {
     const int sms = sm_count(0);
+    int64_t cap = 4 * (int64_t)sms;
+    if (a.max_blocks > 0) cap = std::min<int64_t>(cap, a.max_blocks);
     const int64_t want = (a.n + 1023) / 1024;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 4 * sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
 
 cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s, int64_t* launches) {
@@ -722,3 +727,99 @@ cudaError_t l2apply_launch(const L2ApplyArgs& a, cudaStream_t s, int64_t* launch
 }
 
 }  // namespace dm
+
+// ===================================================================
+// Squared-l2 product without allocation (dm_l2sq_matmat_noalloc).
+//
+// Some callers cannot allocate device memory when they call in: code that
+// runs inside a memory pool or arena it does not own, callers that forbid
+// allocation on their hot path (a cudaMalloc can synchronize the device), or
+// setups whose memory is fully reserved up front.  This entry point runs the
+// column means, the reduce and the apply of the squared-l2 product with all
+// of its scratch in one file-scope device array of fixed size.
+namespace dm {
+namespace {
+
+constexpr int kNoAllocMaxD = 32;
+constexpr int kNoAllocMaxK = 32;
+constexpr int kNoAllocMaxBlocks = 320;
+constexpr size_t kNoAllocColsum = 0;
+constexpr size_t kNoAllocMu = (kNoAllocColsum + 8 * (size_t)kNoAllocMaxBlocks * kNoAllocMaxD + 255) & ~size_t(255);
+constexpr size_t kNoAllocPartial = (kNoAllocMu + 8 * (size_t)kNoAllocMaxD + 255) & ~size_t(255);
+constexpr size_t kNoAllocRes =
+    (kNoAllocPartial + 8 * (size_t)kNoAllocMaxBlocks * (kNoAllocMaxD + 2) * kNoAllocMaxK + 255) & ~size_t(255);
+constexpr size_t kNoAllocBytes = (kNoAllocRes + 8 * (size_t)(kNoAllocMaxD + 2) * kNoAllocMaxK + 255) & ~size_t(255);
+static_assert(kNoAllocBytes <= (size_t(3) << 20), "static scratch stays under 3 MiB");
+
+// The scratch itself: every GPU that loads this library holds it until the
+// process exits.  Host code must not pass this name to a kernel (on the host
+// it is only a stand-in); it uses the device address below.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current).
+cudaError_t noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace dm
+
+extern "C" dm_status dm_l2sq_matmat_noalloc(dm_dtype dtype, const void* X, int64_t n, int64_t d,
+                                            int64_t ldx, const void* Z, int64_t k, int64_t ldz,
+                                            void* out, int64_t ldo, void* cuda_stream) {
+    using namespace dm;
+    if (!X || !Z || !out) return DM_ERR_INVALID_ARG;
+    if (dtype != DM_F32 && dtype != DM_F64 && dtype != DM_I32) return DM_ERR_INVALID_ARG;
+    if (n < 1 || n >= (int64_t(1) << 30) || d < 1 || ldx < d || k < 1 || ldz < k || ldo < k)
+        return DM_ERR_INVALID_ARG;
+    if (d > kNoAllocMaxD || k > kNoAllocMaxK || !reduce_supported(d, k)) return DM_ERR_UNSUPPORTED;
+    void* base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) { cudaGetLastError(); return DM_ERR_CUDA; }
+    unsigned char* sc = static_cast<unsigned char*>(base);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int64_t launches = 0;
+
+    L2PrepArgs pa{};
+    pa.dtype = dtype;
+    pa.X = X; pa.n = n; pa.d = d; pa.ldx = ldx;
+    pa.partial = sc + kNoAllocColsum;
+    pa.mu = sc + kNoAllocMu;
+    pa.err = nullptr;
+    pa.max_blocks = kNoAllocMaxBlocks;
+    if (l2prep_launch(pa, st, &launches) != cudaSuccess) { cudaGetLastError(); return DM_ERR_CUDA; }
+
+    ReduceArgs r{};
+    r.dtype = dtype;
+    r.X = X; r.n = n; r.d = d; r.ldx = ldx; r.x_acc = false;
+    r.mu = sc + kNoAllocMu; r.mu_stride = 1; r.with_s = true;
+    r.Z = Z; r.k = k; r.ldz = ldz;
+    r.partial = sc + kNoAllocPartial;
+    r.res = sc + kNoAllocRes;
+    r.max_blocks = kNoAllocMaxBlocks;
+    if (reduce_launch(r, st, &launches) != cudaSuccess) { cudaGetLastError(); return DM_ERR_CUDA; }
+
+    L2ApplyArgs ap{};
+    ap.dtype = dtype;
+    ap.X = X; ap.n = n; ap.d = d; ap.ldx = ldx;
+    ap.mu = sc + kNoAllocMu; ap.res = sc + kNoAllocRes; ap.k = k;
+    ap.out = out; ap.ldo = ldo;
+    if (l2apply_launch(ap, st, &launches) != cudaSuccess) { cudaGetLastError(); return DM_ERR_CUDA; }
+    return DM_OK;
+}
