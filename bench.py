@@ -50,7 +50,7 @@ UNIT = "point*query*dim/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1 << 20)
@@ -86,7 +86,97 @@ def load_peaks():
 
 
 # ------------------------------------------------------------- clocks
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read in-process through NVML (read-only
+    queries) on a background thread every `interval_s`, between start() and
+    stop() -- enough samples even for a timed region of a few tens of ms."""
+    # clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device, interval_s: float = 0.01):
+        import ctypes
+        import threading
+        self.ok = False
+        self.interval = interval_s
+        self.samples = []          # (sm_mhz, reasons bitmask, power_mw)
+        self.stop_evt = threading.Event()
+        self.thread = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            self.lib = lib
+            self.h = ctypes.c_void_p()
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(torch_device).uuid)
+            if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+                idx = torch_device.index or 0
+                vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+                ids = [v for v in vis.split(",") if v.strip()]
+                if ids and ids[min(idx, len(ids) - 1)].strip().isdigit():
+                    idx = int(ids[min(idx, len(ids) - 1)])
+                if lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(self.h)) != 0:
+                    return
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) != 0:   # NVML_CLOCK_SM
+                return
+            self.max_mhz = mx.value
+            self.ok = True
+        except (OSError, AttributeError, RuntimeError):
+            self.ok = False
+
+    def _read(self):
+        import ctypes
+        mhz, rs, mw = ctypes.c_uint(), ctypes.c_ulonglong(), ctypes.c_uint()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz)) != 0:
+            return None
+        if self.lib.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(rs)) != 0:
+            rs.value = 0
+        if self.lib.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(mw)) != 0:
+            mw.value = 0
+        return mhz.value, rs.value, mw.value
+
+    def _loop(self):
+        while True:
+            r = self._read()
+            if r is not None:
+                self.samples.append(r)
+            if self.stop_evt.wait(self.interval):
+                return
+
+    def start(self):
+        import threading
+        if not self.ok:
+            return False
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+        return True
+
+    def stop(self):
+        if self.thread is None:
+            return None
+        self.stop_evt.set()
+        self.thread.join(timeout=5)
+        r = self._read()            # one reading at the end of the region as well
+        if r is not None:
+            self.samples.append(r)
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, bits, _ in self.samples:
+            for b, nm in self.REASONS.items():
+                if bits & b:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples), "sm_max_mhz": self.max_mhz,
+                "samples": len(self.samples), "source": "nvml", "interval_ms": self.interval * 1e3,
+                "power_w_median": statistics.median(s[2] for s in self.samples) / 1e3,
+                "reasons": sorted(reasons)}
+
+
 class ClockSampler:
+    """Fallback when NVML cannot be loaded: `nvidia-smi -lms`, started before
+    the timed region (its first line awaited) and stopped after it."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -98,10 +188,14 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -131,7 +225,14 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "source": "nvidia-smi", "reasons": sorted(reasons)}
+
+
+def start_clock_sampler(dev):
+    s = NvmlClockSampler(dev)
+    if s.start():
+        return s
+    return ClockSampler(dev.index or 0)
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -174,29 +275,27 @@ def cpu_baseline(n, d, k, d_sample):
 
 # ------------------------------------------------------------- algorithmic bytes
 def algorithmic_bytes(group, n, d, k, launches):
-    """Bytes the method itself moves per launch of a kernel group (FP32)."""
+    """Bytes the method itself moves per launch of a kernel group (FP32
+    elements), from the per-step figure of the group divided by the group's
+    launches per step."""
     nd = n * d
-    if group == "l1_query":     # key 4 + perm 4 + gathered Z row 4k + contribution 4k, + out 4k
-        return nd * (8 + 8 * k) + 4 * n * k
-    if group == "sort_onesweep":  # read key(+val) 8, write key+val 8 (first pass reads 4)
-        return (16 * nd * launches - 4 * nd) / launches
-    if group == "sort_keygen_hist":
-        return 8 * nd
-    if group == "l2_reduce":      # X and Z once
-        return 4 * nd + 4 * n * k
-    if group == "l2_apply":       # X once, out written
-        return 4 * nd + 4 * n * k
-    if group == "l1_aggregate":   # key 4 + perm 4 + gathered Z row 4k (tile sums)
-        return nd * (8 + 4 * k)
-    if group == "l1_prologue":    # read Z 4k + R 4, write the group-major copy 4k
-        return 8 * n * k + 4 * n
-    if group == "l1_finalize":    # read the partial output 4k + R 4, write out 4k
-        return 8 * n * k + 4 * n
-    if group == "l1_rowsum":
-        return 4 * nd + 4 * d + 4 * n
-    if group == "l2_prepare":     # column sums: X once
-        return 4 * nd / max(launches, 1)
-    return None
+    per_step = {
+        # key 4 + perm 4 + gathered Z row 4k + per-coordinate contribution 4k, + out 4k
+        "l1_query": nd * (8 + 8 * k) + 4 * n * k,
+        # read key(+payload) and write key+payload: 12 B on the first pass, 16 on the others
+        "sort_onesweep": 16 * nd * launches - 4 * nd,
+        "sort_keygen_hist": 8 * nd,                 # read X, write keys
+        "l2_reduce": 4 * nd + 4 * n * k,            # X and Z once
+        "l2_apply": 4 * nd + 4 * n * k,             # X once, out written
+        "l1_aggregate": nd * (8 + 4 * k),           # key + perm + gathered Z row (tile sums)
+        "l1_prologue": 8 * n * k + 4 * n,           # read Z and R, write the group-major copy
+        "l1_finalize": 8 * n * k + 4 * n,           # read the partial output and R, write out
+        "l1_rowsum": 4 * nd + 4 * d + 4 * n,
+        "l2_prepare": 4 * nd,                       # column sums: X once
+    }.get(group)
+    if per_step is None:
+        return None
+    return per_step / max(launches, 1)
 
 
 def traffic_record(group):
@@ -289,7 +388,7 @@ def main():
             torch.distributed.barrier()
 
     # ---- timed region
-    clocks = ClockSampler(local) if not a.profile_only else None
+    clocks = start_clock_sampler(dev) if not a.profile_only else None
     dm.dm_profile_enable(ctx, True)
     launches0 = dm.dm_launch_count(ctx)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -349,6 +448,12 @@ def main():
                           "alg_bytes_per_launch": b,
                           "alg_gbs": b / (per_launch_ms * 1e-3) / 1e9}
     dominant = max(kernels, key=lambda g: kernels[g]["ms_per_launch"] * kernels[g]["launches_per_step"])
+    # the whole l1 query (prologue, tile sums and scan, sorted pass, finalize)
+    # against the same algorithmic bytes as the sorted pass alone
+    q_all_ms = parts["l1_query_ms"]
+    q_bytes = algorithmic_bytes("l1_query", a.n, a.d, a.k, 1)
+    l1_query_all = {"ms": q_all_ms, "alg_gbs": q_bytes / (q_all_ms * 1e-3) / 1e9,
+                    "frac": q_bytes / (q_all_ms * 1e-3) / 1e9 / load_peaks()[0]}
     dk = kernels[dominant]
     roofline = {"kernel": dominant, "bound": "hbm", "achieved": dk["alg_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": dk["alg_gbs"] / peak,
@@ -390,7 +495,7 @@ def main():
             dm.dm_matmat_host(ctx, "l1", Xh, Zh, out_h)
             dm.dm_matmat_host(ctx, "l2sq", Xh, Zh, out_h)
         e_ms = []
-        for _ in range(max(3, a.steps // 2)):
+        for _ in range(min(10, max(3, a.steps // 2))):
             flush.zero_()
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.record(stream)
@@ -415,7 +520,7 @@ def main():
             "parallelism": "replicas" if world > 1 else "single GPU",
             "gpu_launches": launches, "launches_per_step": launches / a.steps,
             "wall_s_timed_region": t_wall,
-            "parts_ms": parts, "kernels": kernels, "roofline": roofline,
+            "parts_ms": parts, "kernels": kernels, "roofline": roofline, "l1_query_all_kernels": l1_query_all,
             "bruteforce": brute, "rel_err_sampled_rows": err,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)

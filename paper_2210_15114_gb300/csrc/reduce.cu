@@ -367,11 +367,16 @@ __global__ void mean_finalize_kernel(const typename Types<DT>::Wide* __restrict_
                                      typename Types<DT>::V* __restrict__ mu) {
     using Wide = typename Types<DT>::Wide;
     using V = typename Types<DT>::V;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    // One warp per column: lanes stride over the block partials, then a
+    // shuffle tree in a fixed order (the result does not depend on timing).
+    const int c = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (c >= d) return;
     Wide t = 0;
-    for (int b = 0; b < blocks; ++b) t += partial[(int64_t)b * d + c];
-    mu[c] = (V)(t / (Wide)n);
+    for (int b = lane; b < blocks; b += 32) t += partial[(int64_t)b * d + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) mu[c] = (V)(t / (Wide)n);
 }
 
 // ----------------------------------------------------------------- l2apply
@@ -564,7 +569,7 @@ rowsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int
               typename Types<DT>::Acc* __restrict__ R) {
     using Acc = typename Types<DT>::Acc;
     using V = typename Types<DT>::V;
-    constexpr int U = 4;
+    constexpr int U = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc* mu_s = reinterpret_cast<Acc*>(smem_raw);
     for (int c = threadIdx.x; c < d; c += kThreads) mu_s[c] = to_acc(mu[c * mu_stride], Acc());
@@ -604,7 +609,7 @@ cudaError_t l2prep_launch_t(const L2PrepArgs& a, cudaStream_t st, int64_t* launc
         static_cast<const V*>(a.X), a.n, (int)a.d, a.ldx, static_cast<Wide*>(a.partial), rpb, a.err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    mean_finalize_kernel<DT><<<(unsigned)((a.d + 127) / 128), 128, 0, st>>>(
+    mean_finalize_kernel<DT><<<(unsigned)((a.d + 3) / 4), 128, 0, st>>>(
         static_cast<const Wide*>(a.partial), blocks, (int)a.d, a.n, static_cast<V*>(a.mu));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 2;
@@ -688,7 +693,7 @@ cudaError_t rowsum_launch_t(const void* X, int64_t n, int64_t d, int64_t ldx, co
     auto kern = rowsum_kernel<DT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t warps = (n + 3) / 4;
+    const int64_t warps = (n + 7) / 8;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 8 * (int64_t)sm_count(0)));
     kern<<<(unsigned)blocks, kThreads, smem, s>>>(
         static_cast<const V*>(X), n, (int)d, ldx, static_cast<const V*>(mu), mu_stride,
