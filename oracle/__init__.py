@@ -15,6 +15,11 @@ Three forms, all plain and slow on purpose:
 * ``l1_sort`` -- Algorithm 1 (Preprocessing: sort each coordinate) followed by
   Algorithm 2 (Query for p = 1: prefix sums B_i of y_j x_j(i) and C_i of y_j
   in sorted order, then z(k) += x_k(i)(S3 - S4) + S2 - S1), in numpy.
+* ``l1_grad_rows`` / ``l2sq_grad_rows`` (C), ``l1_grad_sort`` and
+  ``l2sq_grad_closed`` (numpy) -- the gradient of w^T A(X) z with respect to
+  X, which the paper does not state: the chain rule on the definition, and
+  the same through the sorted order (l1) or the Gram decomposition (squared
+  l2).
 * ``l2sq_identity`` -- the p = 2 query of Appendix A (Theorem
   "l2_squared_upper_bound"), with the typos of the printed algorithm read as
   the proof's Gram decomposition (Section 1.2): (Ay)_k = ||x_k||^2 sum_j y_j
@@ -76,6 +81,11 @@ def _load():
                          "oracle_l1_rows_i64", "oracle_l2sq_rows_i64"):
                 fn = getattr(lib, name)
                 fn.argtypes = [p, i64, i64, p, i64, p, i64, p]
+                fn.restype = None
+            for name in ("oracle_l1_grad_rows_f64", "oracle_l2sq_grad_rows_f64",
+                         "oracle_l1_grad_rows_i64", "oracle_l2sq_grad_rows_i64"):
+                fn = getattr(lib, name)
+                fn.argtypes = [p, i64, i64, p, p, i64, p, i64, p]
                 fn.restype = None
             _lib = lib
     return _lib
@@ -182,6 +192,102 @@ def l2sq_identity(X, Z) -> np.ndarray:
     S2 = sq @ Z
     out = sq[:, None] * S1[None, :] + S2[None, :] - 2 * (X @ v)
     return out[:, 0] if squeeze else out
+
+
+def _prep_grad(X, W, Z):
+    X = np.asarray(X)
+    if X.ndim == 1:
+        X = X[:, None]
+    W = np.asarray(W)
+    Z = np.asarray(Z)
+    if W.ndim == 1:
+        W = W[:, None]
+    if Z.ndim == 1:
+        Z = Z[:, None]
+    if not (X.shape[0] == W.shape[0] == Z.shape[0]) or W.shape != Z.shape:
+        raise ValueError("X, W and Z must have n rows; W and Z the same shape")
+    integer = _is_int(X) and _is_int(W) and _is_int(Z)
+    dt = np.int64 if integer else np.float64
+    return (np.ascontiguousarray(X, dtype=dt), np.ascontiguousarray(W, dtype=dt),
+            np.ascontiguousarray(Z, dtype=dt), integer)
+
+
+def _grad_rows_call(kind: str, X, W, Z, rows):
+    X, W, Z, integer = _prep_grad(X, W, Z)
+    n, d = X.shape
+    k = W.shape[1]
+    if rows is None:
+        rows = np.arange(n, dtype=np.int64)
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    if rows.size and (rows.min() < 0 or rows.max() >= n):
+        raise IndexError("row index out of range")
+    G = np.zeros((rows.size, d), dtype=X.dtype)
+    fn = getattr(_load(), f"oracle_{kind}_grad_rows_{'i64' if integer else 'f64'}")
+    fn(X.ctypes.data, n, d, W.ctypes.data, Z.ctypes.data, k, rows.ctypes.data, rows.size,
+       G.ctypes.data)
+    return G
+
+
+def l1_grad_rows(X, W, Z, rows=None) -> np.ndarray:
+    """Gradient of L = sum_q w_q^T A(X) z_q with respect to X for the l1
+    matrix (the paper states none: the chain rule on the definition, with the
+    symmetric subgradient sgn(0) = 0):
+        dL/dx_i(c) = sum_q sum_j (w_iq z_jq + z_iq w_jq) sgn(x_i(c) - x_j(c)).
+    Rows ``rows`` of the n x d gradient (all when None); O(n d k) per row."""
+    return _grad_rows_call("l1", X, W, Z, rows)
+
+
+def l2sq_grad_rows(X, W, Z, rows=None) -> np.ndarray:
+    """Gradient of L = sum_q w_q^T A(X) z_q for the squared-l2 matrix:
+        dL/dx_i(c) = sum_q sum_j (w_iq z_jq + z_iq w_jq) 2 (x_i(c) - x_j(c))."""
+    return _grad_rows_call("l2sq", X, W, Z, rows)
+
+
+def l1_grad_sort(X, W, Z) -> np.ndarray:
+    """The l1 gradient of every row through the sorted order of each
+    coordinate (Algorithm 1's sort, with prefix sums as in Algorithm 2).
+
+    For a point at sorted position r whose value is shared by the tie group of
+    positions a..b, sum_j y_j sgn(x_r - x_j) is the sum of y over the strictly
+    smaller values minus the sum over the strictly larger ones:
+        S_y(r) = E_y[a] - (T_y - I_y[b]),
+    with E the exclusive and I the inclusive prefix sum of y in sorted order
+    and T the total.  Then dL/dx_i(c) = sum_q w_iq S_z(r) + z_iq S_w(r).
+    Integer inputs are computed in int64; others in FP64."""
+    X, W, Z, _ = _prep_grad(X, W, Z)
+    n, d = X.shape
+    G = np.zeros((n, d), dtype=X.dtype)
+    for c in range(d):
+        order = preprocessing_order(X[:, c])
+        xs = X[order, c]
+        head = np.ones(n, dtype=bool)
+        head[1:] = xs[1:] != xs[:-1]
+        gid = np.cumsum(head) - 1                  # tie group of each position
+        first = np.flatnonzero(head)               # a of each group
+        last = np.append(first[1:] - 1, n - 1)     # b of each group
+        a = first[gid]
+        b = last[gid]
+        for Y, other in ((Z, W), (W, Z)):
+            ys = Y[order]
+            inc = np.cumsum(ys, axis=0)
+            exc = inc - ys
+            S = exc[a] - (inc[-1][None, :] - inc[b])
+            G[order, c] += (other[order] * S).sum(axis=1)
+    return G
+
+
+def l2sq_grad_closed(X, W, Z) -> np.ndarray:
+    """The squared-l2 gradient in closed form, from the Gram decomposition of
+    Section 1.2 (sum over j of the definition, expanded):
+        dL/dx_i = 2 sum_q [ x_i (w_iq 1^T z_q + z_iq 1^T w_q)
+                            - w_iq X^T z_q - z_iq X^T w_q ]."""
+    X, W, Z, _ = _prep_grad(X, W, Z)
+    sz = Z.sum(axis=0)
+    sw = W.sum(axis=0)
+    XtZ = X.T @ Z                                   # d x k
+    XtW = X.T @ W
+    coef = W @ sz + Z @ sw                          # n
+    return 2 * (X * coef[:, None] - W @ XtZ.T - Z @ XtW.T)
 
 
 def relative_error(got, want) -> float:

@@ -96,3 +96,23 @@ def workload_integer(n: int = 1 << 20, d: int = 32, k: int = 16):
     X = integer_points(n, d, SEED_X, 0, 1 << 16)
     Z = integer_queries(n, k, SEED_Z, -100, 100)
     return X, Z
+
+
+SEED_W = 1     # the gradient's left vector w
+SEED_ZG = 2    # the gradient's right vector z
+
+
+def workload_gradient(n: int = 1 << 21, d: int = 64, k: int = 1, tie_heavy: bool = False):
+    """Points for the gradient of w^T A(X) z: FP32 coordinates uniform in
+    [0, 1), or -- the tie-heavy variant -- integers uniform in [0, 1023]
+    stored as FP32 (about n / 1024 points share each value of a coordinate);
+    w and z are FP32 N(0, 1) columns (k of each)."""
+    rng = np.random.default_rng(SEED_X)
+    if tie_heavy:
+        X = rng.integers(0, 1024, size=(n, d)).astype(np.float32)
+    else:
+        X = rng.uniform(0.0, 1.0, size=(n, d)).astype(np.float32)
+    W = gaussian_queries(n, k, SEED_W, dtype=np.float32)
+    Z = gaussian_queries(n, k, SEED_ZG, dtype=np.float32)
+    return X, W, Z
+
