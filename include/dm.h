@@ -118,6 +118,24 @@ dm_status dm_matvec_l2sq(dm_plan* plan, const void* z, void* out);
 dm_status dm_matmat(dm_plan* plan, const void* Z, int64_t k, int64_t ldz,
                     void* out, int64_t ldo);
 
+/* Gradient of L = sum_q w_q^T A(X) z_q with respect to the points X, for a
+ * plan of either metric (the paper states no gradient; this is the chain rule
+ * applied to the definition of A):
+ *     G[i, c] = sum_q sum_j (W[i,q] Z[j,q] + Z[i,q] W[j,q]) phi'(x_i(c) - x_j(c)),
+ * phi'(t) = sgn(t) for DM_L1, with sgn(0) = 0 (tied coordinates contribute
+ * nothing: the symmetric subgradient), and phi'(t) = 2t for DM_L2SQ.
+ *   W, Z: n x k (leading dimensions ldw, ldz >= k), 1 <= k <= 64, element type
+ *         of the plan (int32 for DM_I32 plans);
+ *   G:    n x d result (ldg >= d), element type of the plan's results (FP32,
+ *         FP64, or exact int64 for DM_I32).
+ * The l1 gradient runs through the plan's sorted coordinates (Algorithm 1)
+ * with prefix sums of w and z in sorted order (as in Algorithm 2), so its X
+ * need not be alive; the squared-l2 plan reads its recorded X.  DM_L2SQ
+ * returns DM_ERR_UNSUPPORTED where its reduce does not fit (large d * k).
+ * Asynchronous on the context's stream; scratch comes from the context. */
+dm_status dm_grad(dm_plan* plan, const void* W, int64_t ldw, const void* Z, int64_t ldz,
+                  int64_t k, void* G, int64_t ldg);
+
 /* Wait for the context's stream and return (then clear) the first device-side
  * error latched since the last dm_sync. */
 dm_status dm_sync(dm_ctx* ctx);
@@ -153,7 +171,9 @@ int64_t dm_launch_count(const dm_ctx* ctx);
 
 /* Kernel timing.  While enabled, every group of launches a call makes
  * ("sort_keygen_hist", "sort_onesweep", "l1_rowsum", "l1_prologue",
- * "l1_aggregate", "l1_query", "l1_finalize", "l2_prepare", "l2_reduce", "l2_apply", "bruteforce") is bracketed by two CUDA events
+ * "l1_aggregate", "l1_query", "l1_finalize", "l2_prepare", "l2_reduce",
+ * "l2_apply", "bruteforce", "grad_pack", "grad_l1_tiles", "grad_l1_scan",
+ * "grad_l1_eval", "grad_l2_reduce", "grad_l2_apply") is bracketed by two CUDA events
  * recorded on the context's stream.  Enabling (or disabling) clears what was
  * collected.  Off by default; costs two event records per group. */
 dm_status dm_profile_enable(dm_ctx* ctx, int enable);

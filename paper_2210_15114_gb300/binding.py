@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
             "dm_matvec_l1": ([P, P, P], I32),
             "dm_matvec_l2sq": ([P, P, P], I32),
             "dm_matmat": ([P, P, I64, I64, P, I64], I32),
+            "dm_grad": ([P, P, I64, P, I64, I64, P, I64], I32),
             "dm_sync": ([P], I32),
             "dm_status_string": ([I32], ctypes.c_char_p),
             "dm_plan_export": ([P, P, P], I32),
@@ -242,6 +243,23 @@ def dm_matmat(plan: Plan, Z, out=None):
     _check(load().dm_matmat(plan.handle, ctypes.c_void_p(_dev_ptr(Z)), k, _ld(Z) if Z.ndim == 2 else 1,
                             ctypes.c_void_p(_dev_ptr(out)), _ld(out) if out.ndim == 2 else 1),
            "dm_matmat")
+    return out
+
+
+def dm_grad(plan: Plan, W, Z, out=None):
+    """dm_grad: G = d(sum_q w_q^T A(X) z_q)/dX, n x d (W and Z: n or n x k)."""
+    import torch
+    if dtype_code(W.dtype) != plan.dtype or dtype_code(Z.dtype) != plan.dtype:
+        raise DMError(DM_ERR_INVALID_ARG, "W / Z element type differs from the plan's")
+    W2 = W.reshape(-1, 1) if W.ndim == 1 else W
+    Z2 = Z.reshape(-1, 1) if Z.ndim == 1 else Z
+    if W2.shape != Z2.shape:
+        raise DMError(DM_ERR_INVALID_ARG, "W and Z must have the same shape")
+    if out is None:
+        out = torch.empty((plan.n, plan.d), dtype=out_torch_dtype(plan.dtype), device=W.device)
+    _check(load().dm_grad(plan.handle, ctypes.c_void_p(_dev_ptr(W2)), _ld(W2),
+                          ctypes.c_void_p(_dev_ptr(Z2)), _ld(Z2), W2.shape[1],
+                          ctypes.c_void_p(_dev_ptr(out)), _ld(out)), "dm_grad")
     return out
 
 

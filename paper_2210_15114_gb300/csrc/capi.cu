@@ -426,6 +426,71 @@ dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* o
     return DM_OK;
 }
 
+// --------------------------------------------------------------- gradient
+dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64_t ldz, int64_t k,
+                    void* G, int64_t ldg) {
+    dm_ctx* ctx = p->ctx;
+    const dm_dtype t = p->dtype;
+    const int64_t n = p->n, d = p->d;
+    GradArgs a{};
+    a.dtype = t;
+    a.n = n; a.d = d;
+    a.W = W; a.ldw = ldw; a.Z = Z; a.ldz = ldz; a.k = k;
+    a.G = G; a.ldg = ldg;
+    a.num_sms = ctx->num_sms;
+    const size_t gbytes = up16(grad_scratch_bytes(t, n, d, k));
+    if (p->metric == DM_L1) {
+        DM_TRY(ensure_arena(ctx, gbytes));
+        a.scratch = ctx->arena;
+        a.xs = p->xs; a.perm = p->perm;
+        {
+            ProfScope ps(ctx, "grad_pack");
+            DM_TRY_CUDA(grad_pack_launch(a, ctx->stream, &ctx->launches));
+        }
+        {
+            ProfScope ps(ctx, "grad_l1_tiles");
+            DM_TRY_CUDA(grad_l1_launch(a, 0, ctx->stream, &ctx->launches));
+        }
+        {
+            ProfScope ps(ctx, "grad_l1_scan");
+            DM_TRY_CUDA(grad_l1_launch(a, 1, ctx->stream, &ctx->launches));
+        }
+        ProfScope ps(ctx, "grad_l1_eval");
+        DM_TRY_CUDA(grad_l1_launch(a, 2, ctx->stream, &ctx->launches));
+        return DM_OK;
+    }
+    // squared l2: [X - mu, 1]^T [z_q, w_q] by the reduce kernel, then the closed form
+    if (!reduce_supported(d, 2 * k)) return DM_ERR_UNSUPPORTED;
+    ReduceArgs r{};
+    r.dtype = t;
+    r.n = n; r.d = d;
+    r.k = 2 * k; r.ldz = 2 * k;
+    r.num_sms = ctx->num_sms;
+    const int blocks = reduce_blocks(r);
+    const size_t o_res = up16(gbytes + (size_t)blocks * (d + 2) * 2 * k * 8);
+    DM_TRY(ensure_arena(ctx, up16(o_res + (size_t)(d + 2) * 2 * k * 8)));
+    unsigned char* base = static_cast<unsigned char*>(ctx->arena);
+    a.scratch = base;
+    r.partial = base + gbytes;
+    r.res = base + o_res;
+    r.Z = grad_packed(a);
+    r.X = p->X; r.ldx = p->ldx; r.x_acc = false;
+    r.mu = p->mu; r.mu_stride = 1;
+    r.with_s = false;
+    a.X = p->X; a.ldx = p->ldx; a.mu = p->mu; a.res = r.res;
+    {
+        ProfScope ps(ctx, "grad_pack");
+        DM_TRY_CUDA(grad_pack_launch(a, ctx->stream, &ctx->launches));
+    }
+    {
+        ProfScope ps(ctx, "grad_l2_reduce");
+        DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
+    }
+    ProfScope ps(ctx, "grad_l2_apply");
+    DM_TRY_CUDA(grad_l2_apply_launch(a, ctx->stream, &ctx->launches));
+    return DM_OK;
+}
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -569,6 +634,14 @@ dm_status dm_matmat(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out
     if (!p || !Z || !out || k < 1 || ldz < k || ldo < k) return DM_ERR_INVALID_ARG;
     DeviceGuard g(p->ctx->device);
     return matmat_impl(p, Z, k, ldz, out, ldo);
+}
+
+dm_status dm_grad(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64_t ldz, int64_t k,
+                  void* G, int64_t ldg) {
+    if (!p || !W || !Z || !G || k < 1 || k > 64 || ldw < k || ldz < k || ldg < p->d)
+        return DM_ERR_INVALID_ARG;
+    DeviceGuard g(p->ctx->device);
+    return grad_impl(p, W, ldw, Z, ldz, k, G, ldg);
 }
 
 dm_status dm_matvec_l1(dm_plan* p, const void* z, void* out) {

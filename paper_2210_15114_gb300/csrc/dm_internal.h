@@ -165,4 +165,26 @@ struct BruteArgs {
 };
 cudaError_t brute_launch(const BruteArgs& a, cudaStream_t s, int64_t* launches);
 
+// Gradient of L = sum_q w_q^T A(X) z_q with respect to X (grad.cu).
+struct GradArgs {
+    dm_dtype dtype;
+    int64_t n, d;
+    const void* W; int64_t ldw;          // n x k
+    const void* Z; int64_t ldz;          // n x k
+    int64_t k;
+    void* G; int64_t ldg;                // n x d result (Out type)
+    void* scratch;                       // grad_scratch_bytes()
+    int num_sms;
+    // l1 plan
+    const void* xs; const int32_t* perm;
+    // squared-l2 plan
+    const void* X; int64_t ldx; const void* mu; const void* res;
+};
+size_t grad_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k);
+const void* grad_packed(const GradArgs& a);   // the packed (z_q, w_q) pairs, n x 2k
+cudaError_t grad_pack_launch(const GradArgs& a, cudaStream_t s, int64_t* launches);
+// stage 0: tile sums, 1: scan over tiles, 2: evaluation and scatter into G
+cudaError_t grad_l1_launch(const GradArgs& a, int stage, cudaStream_t s, int64_t* launches);
+cudaError_t grad_l2_apply_launch(const GradArgs& a, cudaStream_t s, int64_t* launches);
+
 }  // namespace dm

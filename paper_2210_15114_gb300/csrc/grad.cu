@@ -1,0 +1,597 @@
+// Gradient of L = sum_q w_q^T A(X) z_q with respect to the points X.
+//
+// The paper states no gradient.  By the chain rule on the definition of A,
+//
+//     dL/dx_i(c) = sum_q sum_j (w_iq z_jq + z_iq w_jq) phi'(x_i(c) - x_j(c)),
+//
+// phi' = sgn for l1 (sgn(0) = 0: tied coordinates contribute nothing) and
+// phi'(t) = 2t for squared l2.
+//
+// l1 reuses the plan's sorted coordinates (Algorithm 1).  For the point at
+// sorted position r of coordinate c, inside the tie group of positions a..b,
+//
+//     sum_j y_j sgn(x_r - x_j) = E_y(a) + I_y(b) - T_y,
+//
+// with E / I the exclusive / inclusive prefix sums of y in sorted order (as in
+// Algorithm 2) and T the total.  Three passes over tiles of sorted positions:
+//   grad_tile_kernel<aggregate>: per tile, the sums of z and w, the exclusive
+//       prefix at the tile's last tie-group head and the inclusive prefix at
+//       its first tie-group end, and the head / end positions;
+//   grad_scan_kernel: per (coordinate, column), the tile prefixes, E at the
+//       head of the group entering each tile and I at the end of the group
+//       leaving it (forward and backward scans over the tiles);
+//   grad_tile_kernel<eval>: in-tile scans, the head and end of every
+//       position's tie group, and G[perm[r], c] += w S_z + z S_w.
+// Tiles are claimed so that the coordinates sharing a 32-byte sector of a
+// row of G are processed together: the scattered writes of one sector then
+// meet in L2 before it is written back.
+//
+// Squared l2: with u = 1^T y and Y = (X - mu)^T y for y = z_q, w_q (the
+// reduce kernel on the packed columns), the sum over j expands to
+//     dL/dx_i = 2 sum_q [(x_i - mu)(w_iq u_zq + z_iq u_wq) - w_iq Y_zq - z_iq Y_wq].
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "dm_internal.h"
+
+namespace dm {
+namespace {
+
+constexpr int kGT = 256;                // threads per block
+constexpr int kGI = 8;                  // sorted positions per thread
+constexpr int kGTile = kGT * kGI;       // sorted positions per tile
+constexpr int kGW = kGT / 32;           // warps per block
+constexpr int kNone = INT_MAX;
+
+__device__ __forceinline__ float to_a(float v, float) { return v; }
+__device__ __forceinline__ double to_a(double v, double) { return v; }
+__device__ __forceinline__ long long to_a(int32_t v, long long) { return (long long)v; }
+
+// ---------------------------------------------------------------- scans
+// Exclusive prefix sums over the block (thread order) of two values per
+// thread; tz / tw receive the block totals.  ws: 4 * 32 entries.
+template <class A>
+__device__ __forceinline__ void block_excl_sum2(A& z, A& w, A* ws, A& tz, A& tw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    A iz = z, iw = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const A a = __shfl_up_sync(0xffffffffu, iz, o);
+        const A b = __shfl_up_sync(0xffffffffu, iw, o);
+        if (lane >= o) { iz += a; iw += b; }
+    }
+    if (lane == 31) { ws[warp] = iz; ws[32 + warp] = iw; }
+    __syncthreads();
+    if (warp == 0) {
+        A vz = lane < kGW ? ws[lane] : A(0), vw = lane < kGW ? ws[32 + lane] : A(0);
+#pragma unroll
+        for (int o = 1; o < kGW; o <<= 1) {
+            const A a = __shfl_up_sync(0xffffffffu, vz, o);
+            const A b = __shfl_up_sync(0xffffffffu, vw, o);
+            if (lane >= o) { vz += a; vw += b; }
+        }
+        ws[64 + lane] = vz;
+        ws[96 + lane] = vw;
+    }
+    __syncthreads();
+    const A bz = warp > 0 ? ws[64 + warp - 1] : A(0);
+    const A bw = warp > 0 ? ws[96 + warp - 1] : A(0);
+    tz = ws[64 + kGW - 1];
+    tw = ws[96 + kGW - 1];
+    z = bz + iz - z;
+    w = bw + iw - w;
+    __syncthreads();
+}
+
+// Exclusive prefix sum of one value per thread; t receives the block total.
+template <class A>
+__device__ __forceinline__ A block_excl_sum1(A v, A* ws, A& t) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    A iv = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const A a = __shfl_up_sync(0xffffffffu, iv, o);
+        if (lane >= o) iv += a;
+    }
+    if (lane == 31) ws[warp] = iv;
+    __syncthreads();
+    if (warp == 0) {
+        A x = lane < kGW ? ws[lane] : A(0);
+#pragma unroll
+        for (int o = 1; o < kGW; o <<= 1) {
+            const A a = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += a;
+        }
+        ws[32 + lane] = x;
+    }
+    __syncthreads();
+    const A b = warp > 0 ? ws[32 + warp - 1] : A(0);
+    t = ws[32 + kGW - 1];
+    __syncthreads();
+    return b + iv - v;
+}
+
+// Maximum over the threads before this one (-1 if none); *all = block max.
+__device__ __forceinline__ int block_excl_max(int v, int* ws, int* all) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int iv = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, iv, o);
+        if (lane >= o) iv = max(iv, a);
+    }
+    if (lane == 31) ws[warp] = iv;
+    __syncthreads();
+    int before = -1;
+    for (int w = 0; w < warp; ++w) before = max(before, ws[w]);
+    int tot = -1;
+    for (int w = 0; w < kGW; ++w) tot = max(tot, ws[w]);
+    const int prev = __shfl_up_sync(0xffffffffu, iv, 1);
+    const int ex = max(before, lane > 0 ? prev : -1);
+    __syncthreads();
+    *all = tot;
+    return ex;
+}
+
+// Minimum over the threads after this one (kNone if none); *all = block min.
+__device__ __forceinline__ int block_excl_suffix_min(int v, int* ws, int* all) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int iv = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_down_sync(0xffffffffu, iv, o);
+        if (lane + o < 32) iv = min(iv, a);
+    }
+    if (lane == 0) ws[warp] = iv;
+    __syncthreads();
+    int after = kNone;
+    for (int w = warp + 1; w < kGW; ++w) after = min(after, ws[w]);
+    int tot = kNone;
+    for (int w = 0; w < kGW; ++w) tot = min(tot, ws[w]);
+    const int next = __shfl_down_sync(0xffffffffu, iv, 1);
+    const int ex = min(after, lane < 31 ? next : kNone);
+    __syncthreads();
+    *all = tot;
+    return ex;
+}
+
+// ---------------------------------------------------------------- kernels
+template <dm_dtype DT>
+struct GradParams {
+    using V = typename Types<DT>::V;
+    using Wide = typename Types<DT>::Wide;
+    using Out = typename Types<DT>::Out;
+    const V* xs; const int32_t* perm; int64_t n; int d;
+    const V* P; int k;          // packed (z_q, w_q) pairs, n x 2k
+    int64_t T;                  // tiles per coordinate
+    int GS;                     // coordinates per 32-byte sector of a row of G
+    int4* flags;                // d x T: first head, last head, first end, last end
+    Wide* summ;                 // d x T x 2k x 3: sum, prefix at last head, at first end
+    const Wide* pre;            // d x T x 2k x 3: tile prefix, E entering, I leaving
+    const Wide* tot;            // d x 2k
+    Out* G; int64_t ldg;
+};
+
+// Block b -> (coordinate c, tile t): groups of GS coordinates, and within a
+// group the GS coordinates of one tile index on consecutive blocks.
+__device__ __forceinline__ void tile_of_block(int64_t b, int64_t T, int d, int GS, int* c, int64_t* t) {
+    const int64_t per_group = (int64_t)GS * T;
+    const int64_t g = b / per_group;
+    const int64_t rem = b - g * per_group;
+    const int gs = min(GS, d - (int)g * GS);
+    const int64_t tt = rem / gs;
+    *t = tt;
+    *c = (int)g * GS + (int)(rem - tt * gs);
+}
+
+template <class V, bool VEC>
+__device__ __forceinline__ void load_items(const V* __restrict__ src, int valid, int base, V* v) {
+    if (VEC && base + kGI <= valid) {
+        constexpr int E = 16 / (int)sizeof(V);
+#pragma unroll
+        for (int j = 0; j < kGI; j += E) {
+            const uint4 raw = __ldg(reinterpret_cast<const uint4*>(src + base + j));
+            memcpy(&v[j], &raw, 16);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) v[j] = base + j < valid ? src[base + j] : V(0);
+    }
+}
+
+template <dm_dtype DT, bool EVAL, bool VEC>
+__global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Wide = typename Types<DT>::Wide;
+    using Out = typename Types<DT>::Out;
+    __shared__ Acc Iz[EVAL ? kGTile : 1], Iw[EVAL ? kGTile : 1];
+    __shared__ Acc ws[128];
+    __shared__ int wsi[32];
+    __shared__ int red[4];
+
+    int c;
+    int64_t t;
+    tile_of_block(blockIdx.x, p.T, p.d, p.GS, &c, &t);
+    const int64_t ts = t * kGTile;
+    const int valid = (int)min64(kGTile, p.n - ts);
+    const int base = threadIdx.x * kGI;
+    const V* xc = p.xs + (int64_t)c * p.n + ts;
+    const int32_t* pc = p.perm + (int64_t)c * p.n + ts;
+
+    V x[kGI];
+    int32_t pi[kGI];
+    load_items<V, VEC>(xc, valid, base, x);
+    load_items<int32_t, VEC>(pc, valid, base, pi);
+    const V prevv = (ts + base > 0 && base < valid) ? xc[base - 1] : x[0];
+    const V nextv = (ts + base + kGI < p.n) ? xc[base + kGI] : x[kGI - 1];
+
+    // Tie-group heads and ends (equal values, -0 and +0 included, are a tie).
+    bool hd[kGI], en[kGI];
+#pragma unroll
+    for (int j = 0; j < kGI; ++j) {
+        const bool in = base + j < valid;
+        const int64_t r = ts + base + j;
+        const V left = j > 0 ? x[j - 1] : prevv;
+        const V right = j + 1 < kGI ? x[j + 1] : nextv;
+        hd[j] = in && (r == 0 || x[j] != left);
+        en[j] = in && (r == p.n - 1 || x[j] != right);
+    }
+    int lh = -1, fe = kNone;
+#pragma unroll
+    for (int j = 0; j < kGI; ++j) if (hd[j]) lh = base + j;
+#pragma unroll
+    for (int j = kGI - 1; j >= 0; --j) if (en[j]) fe = base + j;
+
+    int a[kGI], b[kGI];
+    int last_head, first_end;
+    {
+        int run = block_excl_max(lh, wsi, &last_head);
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) { if (hd[j]) run = base + j; a[j] = run; }
+        run = block_excl_suffix_min(fe, wsi, &first_end);
+#pragma unroll
+        for (int j = kGI - 1; j >= 0; --j) { if (en[j]) run = base + j; b[j] = run; }
+    }
+    if (!EVAL) {
+        int fh = kNone, le = -1;
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) {
+            if (hd[j]) fh = min(fh, base + j);
+            if (en[j]) le = max(le, base + j);
+        }
+        if (threadIdx.x == 0) { red[0] = kNone; red[1] = -1; }
+        __syncthreads();
+        if (fh != kNone) atomicMin(&red[0], fh);
+        if (le >= 0) atomicMax(&red[1], le);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            p.flags[(int64_t)c * p.T + t] = make_int4(red[0], last_head, first_end, red[1]);
+    }
+
+    const int K2 = 2 * p.k;
+    Acc g[kGI];
+#pragma unroll
+    for (int j = 0; j < kGI; ++j) g[j] = Acc(0);
+
+    for (int q = 0; q < p.k; ++q) {
+        Acc z[kGI], w[kGI], iz[kGI], iw[kGI];
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) {
+            if (base + j < valid) {
+                const V* pr = p.P + (int64_t)pi[j] * K2 + 2 * q;
+                z[j] = to_a(pr[0], Acc());
+                w[j] = to_a(pr[1], Acc());
+            } else {
+                z[j] = Acc(0);
+                w[j] = Acc(0);
+            }
+        }
+        Acc sz = 0, sw = 0;
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) { sz += z[j]; sw += w[j]; iz[j] = sz; iw[j] = sw; }
+        Acc oz = sz, ow = sw, tz, tw;
+        block_excl_sum2(oz, ow, ws, tz, tw);
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) { iz[j] += oz; iw[j] += ow; }
+
+        const int64_t slot = ((int64_t)c * p.T + t) * K2 + 2 * q;
+        if (!EVAL) {
+            // sums, exclusive prefix at the last head, inclusive at the first end
+            // The tile sum is the inclusive prefix at the tile's last position
+            // (not the block total, which sums in another order): a group
+            // that runs to the end of the tile then cancels exactly.
+            Wide* s = p.summ + slot * 3;
+            if (threadIdx.x == 0) {
+                if (last_head < 0) { s[1] = 0; s[4] = 0; }
+                if (first_end == kNone) { s[2] = 0; s[5] = 0; }
+            }
+#pragma unroll
+            for (int j = 0; j < kGI; ++j) {
+                if (base + j == valid - 1) { s[0] = (Wide)iz[j]; s[3] = (Wide)iw[j]; }
+                if (base + j == last_head) { s[1] = (Wide)(iz[j] - z[j]); s[4] = (Wide)(iw[j] - w[j]); }
+                if (base + j == first_end) { s[2] = (Wide)iz[j]; s[5] = (Wide)iw[j]; }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kGI; ++j) { Iz[base + j] = iz[j]; Iw[base + j] = iw[j]; }
+            __syncthreads();
+            const Wide* pz = p.pre + slot * 3;
+            const Wide* pw = pz + 3;
+            const Wide TZ = p.tot[(int64_t)c * K2 + 2 * q], TW = p.tot[(int64_t)c * K2 + 2 * q + 1];
+            // E(a) + I(b) - T with the parts that lie outside the tile taken
+            // from the scan: (head outside, end outside), (outside, inside),
+            // (inside, outside), (inside, inside)
+            const Acc z00 = (Acc)(pz[1] + pz[2] - TZ), w00 = (Acc)(pw[1] + pw[2] - TW);
+            const Acc z01 = (Acc)(pz[1] + pz[0] - TZ), w01 = (Acc)(pw[1] + pw[0] - TW);
+            const Acc z10 = (Acc)(pz[0] + pz[2] - TZ), w10 = (Acc)(pw[0] + pw[2] - TW);
+            const Acc z11 = (Acc)(2 * pz[0] - TZ), w11 = (Acc)(2 * pw[0] - TW);
+#pragma unroll
+            for (int j = 0; j < kGI; ++j) {
+                if (base + j >= valid) continue;
+                const bool ain = a[j] >= 0, bin = b[j] != kNone;
+                Acc Sz = ain ? (bin ? z11 : z10) : (bin ? z01 : z00);
+                Acc Sw = ain ? (bin ? w11 : w10) : (bin ? w01 : w00);
+                if (ain && a[j] > 0) { Sz += Iz[a[j] - 1]; Sw += Iw[a[j] - 1]; }
+                if (bin) { Sz += Iz[b[j]]; Sw += Iw[b[j]]; }
+                g[j] += w[j] * Sz + z[j] * Sw;
+            }
+            __syncthreads();
+        }
+    }
+    if (EVAL) {
+#pragma unroll
+        for (int j = 0; j < kGI; ++j)
+            if (base + j < valid) p.G[(int64_t)pi[j] * p.ldg + c] = (Out)g[j];
+    }
+}
+
+// One block per (coordinate, column, z or w): forward scan of the tile sums
+// (tile prefixes, E at the head of the group entering each tile), then a
+// backward scan (I at the end of the group leaving each tile).
+template <class W>
+__global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__ flags,
+                                                        const W* __restrict__ summ, W* pre, W* tot,
+                                                        int64_t n, int64_t T, int K2) {
+    __shared__ W vals[kGT];
+    __shared__ W ws[64];
+    __shared__ int wsi[32];
+    const int c = blockIdx.x / K2;
+    const int qy = blockIdx.x - c * K2;
+    const int tid = threadIdx.x;
+    W carry_tp = 0, carry_e = 0;
+    for (int64_t c0 = 0; c0 < T; c0 += kGT) {
+        const int64_t t = c0 + tid;
+        const bool in = t < T;
+        const int64_t slot = ((int64_t)c * T + t) * K2 + qy;
+        const int4 f = in ? flags[(int64_t)c * T + t] : make_int4(kNone, -1, kNone, -1);
+        const W sum = in ? summ[slot * 3] : W(0);
+        W chunk;
+        const W tp = carry_tp + block_excl_sum1(sum, ws, chunk);
+        const bool has_head = in && f.y >= 0;
+        vals[tid] = tp + (in ? summ[slot * 3 + 1] : W(0));
+        int last;
+        const int idx = block_excl_max(has_head ? tid : -1, wsi, &last);
+        const W el = (in && f.x == 0) ? tp : (idx >= 0 ? vals[idx] : carry_e);
+        if (in) { pre[slot * 3] = tp; pre[slot * 3 + 1] = el; }
+        if (last >= 0) carry_e = vals[last];
+        carry_tp += chunk;
+        __syncthreads();
+    }
+    if (tid == 0) tot[(int64_t)c * K2 + qy] = carry_tp;
+    __syncthreads();
+    W carry_i = 0;
+    for (int64_t c0 = ((T - 1) / kGT) * kGT; c0 >= 0; c0 -= kGT) {
+        const int64_t t = c0 + tid;
+        const bool in = t < T;
+        const int64_t slot = ((int64_t)c * T + t) * K2 + qy;
+        const int4 f = in ? flags[(int64_t)c * T + t] : make_int4(kNone, -1, kNone, -1);
+        const W tp = in ? pre[slot * 3] : W(0);
+        const bool has_end = in && f.z != kNone;
+        vals[tid] = tp + (in ? summ[slot * 3 + 2] : W(0));
+        int first;
+        const int idx = block_excl_suffix_min(has_end ? tid : kNone, wsi, &first);
+        const int valid = in ? (int)min64(kGTile, n - t * kGTile) : 0;
+        const bool end_at_last = in && f.w == valid - 1;
+        const W ir = end_at_last ? tp + summ[slot * 3] : (idx != kNone ? vals[idx] : carry_i);
+        if (in) pre[slot * 3 + 2] = ir;
+        if (first != kNone) carry_i = vals[first];
+        __syncthreads();
+    }
+}
+
+// P[i, 2q] = Z[i, q], P[i, 2q + 1] = W[i, q].
+template <class V>
+__global__ void grad_pack_kernel(const V* __restrict__ W, int64_t ldw, const V* __restrict__ Z,
+                                 int64_t ldz, int64_t n, int k, V* __restrict__ P) {
+    const int64_t total = n * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k;
+        const int q = (int)(e - i * k);
+        P[i * 2 * k + 2 * q] = Z[i * ldz + q];
+        P[i * 2 * k + 2 * q + 1] = W[i * ldw + q];
+    }
+}
+
+// Squared l2: one warp per row, lanes over the coordinates.
+template <dm_dtype DT>
+__global__ void __launch_bounds__(kGT)
+grad_l2_apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int64_t ldx,
+                     const typename Types<DT>::V* __restrict__ mu,
+                     const typename Types<DT>::Wide* __restrict__ res,
+                     const typename Types<DT>::V* __restrict__ P, int k,
+                     typename Types<DT>::Out* __restrict__ G, int64_t ldg) {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Out = typename Types<DT>::Out;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int K2 = 2 * k;
+    Acc* Y = reinterpret_cast<Acc*>(smem_raw);   // d x 2k: (X - mu)^T z_q, (X - mu)^T w_q
+    Acc* u = Y + (size_t)d * K2;                 // 2k: 1^T z_q, 1^T w_q
+    Acc* m = u + K2;                             // d
+    for (int e = threadIdx.x; e < d * K2; e += blockDim.x) Y[e] = (Acc)res[e];
+    for (int e = threadIdx.x; e < K2; e += blockDim.x) u[e] = (Acc)res[(size_t)d * K2 + e];
+    for (int e = threadIdx.x; e < d; e += blockDim.x) m[e] = to_a(mu[e], Acc());
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < n; i += nw) {
+        const V* pr = P + i * K2;
+        for (int c = lane; c < d; c += 32) {
+            const Acc xc = to_a(X[i * ldx + c], Acc()) - m[c];
+            Acc g = 0;
+            for (int q = 0; q < k; ++q) {
+                const Acc zq = to_a(pr[2 * q], Acc()), wq = to_a(pr[2 * q + 1], Acc());
+                g += xc * (wq * u[2 * q] + zq * u[2 * q + 1]) - wq * Y[c * K2 + 2 * q] -
+                     zq * Y[c * K2 + 2 * q + 1];
+            }
+            G[i * ldg + c] = (Out)(2 * g);
+        }
+    }
+}
+
+struct GradLayout {
+    int64_t T;
+    size_t p, flags, summ, pre, tot, total;
+};
+
+constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+GradLayout grad_layout(dm_dtype t, int64_t n, int64_t d, int64_t k) {
+    GradLayout L;
+    L.T = (n + kGTile - 1) / kGTile;
+    const size_t K2 = 2 * (size_t)k;
+    L.p = 0;
+    L.flags = al256(L.p + (size_t)n * K2 * dtype_size(t));
+    L.summ = al256(L.flags + 16 * (size_t)(d * L.T));
+    L.pre = al256(L.summ + 8 * 3 * K2 * (size_t)(d * L.T));
+    L.tot = al256(L.pre + 8 * 3 * K2 * (size_t)(d * L.T));
+    L.total = al256(L.tot + 8 * K2 * (size_t)d);
+    return L;
+}
+
+template <dm_dtype DT>
+cudaError_t grad_pack_t(const GradArgs& a, cudaStream_t s, int64_t* launches) {
+    using V = typename Types<DT>::V;
+    const GradLayout L = grad_layout(a.dtype, a.n, a.d, a.k);
+    V* P = reinterpret_cast<V*>(static_cast<unsigned char*>(a.scratch) + L.p);
+    const int64_t total = a.n * a.k;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8 * (int64_t)a.num_sms));
+    grad_pack_kernel<V><<<blocks, 256, 0, s>>>(static_cast<const V*>(a.W), a.ldw,
+                                               static_cast<const V*>(a.Z), a.ldz, a.n, (int)a.k, P);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+template <dm_dtype DT>
+GradParams<DT> make_params(const GradArgs& a) {
+    using V = typename Types<DT>::V;
+    using Wide = typename Types<DT>::Wide;
+    using Out = typename Types<DT>::Out;
+    const GradLayout L = grad_layout(a.dtype, a.n, a.d, a.k);
+    unsigned char* sc = static_cast<unsigned char*>(a.scratch);
+    GradParams<DT> p;
+    p.xs = static_cast<const V*>(a.xs);
+    p.perm = a.perm;
+    p.n = a.n;
+    p.d = (int)a.d;
+    p.P = reinterpret_cast<const V*>(sc + L.p);
+    p.k = (int)a.k;
+    p.T = L.T;
+    p.GS = (int)std::min<int64_t>(32 / (int64_t)sizeof(Out), a.d);
+    p.flags = reinterpret_cast<int4*>(sc + L.flags);
+    p.summ = reinterpret_cast<Wide*>(sc + L.summ);
+    p.pre = reinterpret_cast<const Wide*>(sc + L.pre);
+    p.tot = reinterpret_cast<const Wide*>(sc + L.tot);
+    p.G = static_cast<Out*>(a.G);
+    p.ldg = a.ldg;
+    return p;
+}
+
+template <dm_dtype DT>
+cudaError_t grad_l1_stage_t(const GradArgs& a, int stage, cudaStream_t s, int64_t* launches) {
+    using V = typename Types<DT>::V;
+    using Wide = typename Types<DT>::Wide;
+    GradParams<DT> p = make_params<DT>(a);
+    const GradLayout L = grad_layout(a.dtype, a.n, a.d, a.k);
+    unsigned char* sc = static_cast<unsigned char*>(a.scratch);
+    const int64_t blocks = a.d * L.T;
+    if (blocks > INT_MAX) return cudaErrorInvalidConfiguration;
+    // 16-byte loads of the sorted column need every column start aligned
+    const bool vec = (a.n % (16 / (int64_t)sizeof(V))) == 0 && (a.n % 4) == 0 &&
+                     reinterpret_cast<uintptr_t>(a.xs) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(a.perm) % 16 == 0;
+    if (stage == 0) {
+        if (vec) grad_tile_kernel<DT, false, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        else grad_tile_kernel<DT, false, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+    } else if (stage == 1) {
+        grad_scan_kernel<Wide><<<(unsigned)(a.d * 2 * a.k), kGT, 0, s>>>(
+            p.flags, p.summ, reinterpret_cast<Wide*>(sc + L.pre), reinterpret_cast<Wide*>(sc + L.tot),
+            a.n, L.T, (int)(2 * a.k));
+    } else {
+        if (vec) grad_tile_kernel<DT, true, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        else grad_tile_kernel<DT, true, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+    }
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+template <dm_dtype DT>
+cudaError_t grad_l2_apply_t(const GradArgs& a, cudaStream_t s, int64_t* launches) {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Wide = typename Types<DT>::Wide;
+    using Out = typename Types<DT>::Out;
+    const GradLayout L = grad_layout(a.dtype, a.n, a.d, a.k);
+    const V* P = reinterpret_cast<const V*>(static_cast<unsigned char*>(a.scratch) + L.p);
+    const size_t smem = sizeof(Acc) * ((size_t)a.d * 2 * a.k + 2 * a.k + a.d);
+    auto kern = grad_l2_apply_kernel<DT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t warps = a.n;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + kGW - 1) / kGW, 8 * (int64_t)a.num_sms));
+    kern<<<blocks, kGT, smem, s>>>(static_cast<const V*>(a.X), a.n, (int)a.d, a.ldx,
+                                   static_cast<const V*>(a.mu), static_cast<const Wide*>(a.res), P,
+                                   (int)a.k, static_cast<Out*>(a.G), a.ldg);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t grad_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k) {
+    return grad_layout(t, n, d, k).total;
+}
+
+const void* grad_packed(const GradArgs& a) {
+    return static_cast<const unsigned char*>(a.scratch) + grad_layout(a.dtype, a.n, a.d, a.k).p;
+}
+
+cudaError_t grad_pack_launch(const GradArgs& a, cudaStream_t s, int64_t* launches) {
+    switch (a.dtype) {
+        case DM_F32: return grad_pack_t<DM_F32>(a, s, launches);
+        case DM_F64: return grad_pack_t<DM_F64>(a, s, launches);
+        default: return grad_pack_t<DM_I32>(a, s, launches);
+    }
+}
+
+cudaError_t grad_l1_launch(const GradArgs& a, int stage, cudaStream_t s, int64_t* launches) {
+    switch (a.dtype) {
+        case DM_F32: return grad_l1_stage_t<DM_F32>(a, stage, s, launches);
+        case DM_F64: return grad_l1_stage_t<DM_F64>(a, stage, s, launches);
+        default: return grad_l1_stage_t<DM_I32>(a, stage, s, launches);
+    }
+}
+
+cudaError_t grad_l2_apply_launch(const GradArgs& a, cudaStream_t s, int64_t* launches) {
+    switch (a.dtype) {
+        case DM_F32: return grad_l2_apply_t<DM_F32>(a, s, launches);
+        case DM_F64: return grad_l2_apply_t<DM_F64>(a, s, launches);
+        default: return grad_l2_apply_t<DM_I32>(a, s, launches);
+    }
+}
+
+}  // namespace dm

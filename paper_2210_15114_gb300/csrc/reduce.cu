@@ -20,6 +20,7 @@
 // contraction does 2(d+2)k flops per (4d + 4k) bytes read, below the FP32
 // ALU ridge, so they run on the CUDA cores.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "dm_internal.h"
@@ -569,7 +570,7 @@ rowsum_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int
               typename Types<DT>::Acc* __restrict__ R) {
     using Acc = typename Types<DT>::Acc;
     using V = typename Types<DT>::V;
-    constexpr int U = 8;
+    constexpr int U = 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc* mu_s = reinterpret_cast<Acc*>(smem_raw);
     for (int c = threadIdx.x; c < d; c += kThreads) mu_s[c] = to_acc(mu[c * mu_stride], Acc());
@@ -684,16 +685,88 @@ cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s, int64_t* launches
     }
 }
 
+// The same row sums for rows of whole 16-byte vectors (d * sizeof(V) a
+// multiple of 16, rows 16-byte aligned, VPR = vectors per row a power of two
+// <= 32): a warp reads 32 / VPR consecutive rows with one 16-byte load per
+// lane, U such loads in flight, and reduces each row over its VPR lanes.
+template <dm_dtype DT, int VPR>
+__global__ void __launch_bounds__(kThreads)
+rowsum_vec_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64_t ldx,
+                  const typename Types<DT>::V* __restrict__ mu, int64_t mu_stride,
+                  typename Types<DT>::Acc* __restrict__ R) {
+    using Acc = typename Types<DT>::Acc;
+    using V = typename Types<DT>::V;
+    constexpr int E = 16 / (int)sizeof(V);       // elements per vector
+    constexpr int RPW = 32 / VPR;                // rows per warp load
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % VPR, rw = lane / VPR;
+    Acc m[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) m[e] = to_acc(mu[(int64_t)(sub * E + e) * mu_stride], Acc());
+    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t i0 = gw * (U * RPW); i0 < n; i0 += nw * (U * RPW)) {
+        V v[U][E];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * RPW + rw;
+            if (i < n) {
+                const uint4 raw = *reinterpret_cast<const uint4*>(X + i * ldx + sub * E);
+                memcpy(&v[u][0], &raw, 16);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[u][e] = V(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Acc x = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) x += to_acc(v[u][e], Acc()) - m[e];
+#pragma unroll
+            for (int o = VPR / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            const int64_t i = i0 + u * RPW + rw;
+            if (sub == 0 && i < n) R[i] = x;
+        }
+    }
+}
+
+template <dm_dtype DT, int VPR>
+cudaError_t rowsum_vec_launch(const void* X, int64_t n, int64_t ldx, const void* mu,
+                              int64_t mu_stride, void* R, cudaStream_t s) {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    const int64_t rows_per_warp_step = 4 * (32 / VPR);
+    const int64_t warps = (n + rows_per_warp_step - 1) / rows_per_warp_step;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 8 * (int64_t)sm_count(0)));
+    rowsum_vec_kernel<DT, VPR><<<(unsigned)blocks, kThreads, 0, s>>>(
+        static_cast<const V*>(X), n, ldx, static_cast<const V*>(mu), mu_stride, static_cast<Acc*>(R));
+    return cudaGetLastError();
+}
+
 template <dm_dtype DT>
 cudaError_t rowsum_launch_t(const void* X, int64_t n, int64_t d, int64_t ldx, const void* mu,
                             int64_t mu_stride, void* R, cudaStream_t s) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
+    if (rows16(X, ldx, d, sizeof(V))) {
+        const int64_t vpr = d * (int64_t)sizeof(V) / 16;
+        switch (vpr) {
+            case 1: return rowsum_vec_launch<DT, 1>(X, n, ldx, mu, mu_stride, R, s);
+            case 2: return rowsum_vec_launch<DT, 2>(X, n, ldx, mu, mu_stride, R, s);
+            case 4: return rowsum_vec_launch<DT, 4>(X, n, ldx, mu, mu_stride, R, s);
+            case 8: return rowsum_vec_launch<DT, 8>(X, n, ldx, mu, mu_stride, R, s);
+            case 16: return rowsum_vec_launch<DT, 16>(X, n, ldx, mu, mu_stride, R, s);
+            case 32: return rowsum_vec_launch<DT, 32>(X, n, ldx, mu, mu_stride, R, s);
+            default: break;
+        }
+    }
     const size_t smem = sizeof(Acc) * (size_t)d;
     auto kern = rowsum_kernel<DT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t warps = (n + 7) / 8;
+    const int64_t warps = (n + 3) / 4;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 8 * (int64_t)sm_count(0)));
     kern<<<(unsigned)blocks, kThreads, smem, s>>>(
         static_cast<const V*>(X), n, (int)d, ldx, static_cast<const V*>(mu), mu_stride,
