@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--no-brute", action="store_true", help="skip the brute-force comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--grad-n", type=int, default=1 << 21)
+    ap.add_argument("--grad-d", type=int, default=64)
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps only (for profiler captures); print nothing else")
     return ap.parse_args()
@@ -315,6 +318,61 @@ def traffic_record(group):
     return rec["bytes_per_launch"]
 
 
+def measure_gradient(dm, ctx, stream, flush, dev, peak, n=1 << 21, d=64, reps=10):
+    """dm_grad on its own workload, timed with CUDA events per call (L2
+    flushed between calls), with the library's per-kernel-group events."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2210_15114_gb300 import inputs
+    X, W, Z = inputs.workload_gradient(n=n, d=d)
+    Xd, Wd, Zd = (torch.from_numpy(t).to(dev) for t in (X, W, Z))
+    G = torch.empty((n, d), dtype=torch.float32, device=dev)
+    res = {"workload": f"uniform [0,1) n={n} d={d} k=1 fp32, w and z N(0,1)",
+           "units": "point*dim per second (n d per call)"}
+    rows = inputs.sample_rows(n, 4)
+    for metric in ("l1", "l2sq"):
+        plan = dm.dm_prepare(ctx, metric, Xd)
+        for _ in range(3):
+            dm.dm_grad(plan, Wd, Zd, out=G)
+        torch.cuda.synchronize(dev)
+        dm.dm_profile_enable(ctx, True)
+        ev = []
+        for _ in range(reps):
+            flush.zero_()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            dm.dm_grad(plan, Wd, Zd, out=G)
+            e_.record(stream)
+            ev.append((s_, e_))
+        torch.cuda.synchronize(dev)
+        prof = dm.dm_profile_read(ctx)
+        dm.dm_profile_enable(ctx, False)
+        ms = statistics.mean(s_.elapsed_time(e_) for s_, e_ in ev)
+        kern = {g: {"launches_per_call": l // reps, "ms_per_call": t / reps} for g, (l, t) in prof.items()}
+        ref = (oracle.l1_grad_rows if metric == "l1" else oracle.l2sq_grad_rows)(X, W, Z, rows)
+        err = oracle.relative_error(G.cpu().numpy()[rows], ref)
+        entry = {"ms": ms, "value": n * d / (ms * 1e-3), "kernels": kern, "rel_err_sampled_rows": err}
+        if metric == "l1" and "grad_l1_eval" in kern:
+            # the evaluation pass alone moves the method's bytes: sorted value
+            # 4 + perm 4 + gathered (z, w) 8 + gradient write 4 per element
+            b = n * d * 20
+            t_ms = kern["grad_l1_eval"]["ms_per_call"]
+            entry["roofline_eval"] = {"bound": "hbm", "alg_bytes": b, "achieved": b / (t_ms * 1e-3) / 1e9,
+                                      "peak": peak, "frac": b / (t_ms * 1e-3) / 1e9 / peak}
+            b_all = n * d * 20
+            entry["roofline_all"] = {"alg_bytes": b_all, "achieved": b_all / (ms * 1e-3) / 1e9,
+                                     "frac": b_all / (ms * 1e-3) / 1e9 / peak}
+        if metric == "l2sq":
+            # reduce reads X and (z, w); apply reads X and (z, w) and writes G
+            b = 4 * n * d * 3 + 16 * n
+            entry["roofline_all"] = {"bound": "hbm", "alg_bytes": b, "achieved": b / (ms * 1e-3) / 1e9,
+                                     "peak": peak, "frac": b / (ms * 1e-3) / 1e9 / peak}
+        res[metric] = entry
+        del plan
+    return res
+
+
 # ------------------------------------------------------------- reference arm
 def run_reference(a):
     rank, world, _ = dist_env()
@@ -460,6 +518,11 @@ def main():
                 "peak_kind": peak_kind + " HBM copy bandwidth",
                 "traffic": traffic_record(dominant)}
 
+    # ---- gradient of w^T A(X) z (n = 2^21, d = 64, k = 1, FP32 uniform [0, 1))
+    grad = None
+    if not a.no_grad:
+        grad = measure_gradient(dm, ctx, stream, flush, dev, peak, n=a.grad_n, d=a.grad_d)
+
     # ---- brute force (the plain method) and accuracy
     brute = None
     if not a.no_brute:
@@ -521,7 +584,7 @@ def main():
             "gpu_launches": launches, "launches_per_step": launches / a.steps,
             "wall_s_timed_region": t_wall,
             "parts_ms": parts, "kernels": kernels, "roofline": roofline, "l1_query_all_kernels": l1_query_all,
-            "bruteforce": brute, "rel_err_sampled_rows": err,
+            "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:

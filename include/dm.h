@@ -173,7 +173,8 @@ int64_t dm_launch_count(const dm_ctx* ctx);
  * ("sort_keygen_hist", "sort_onesweep", "l1_rowsum", "l1_prologue",
  * "l1_aggregate", "l1_query", "l1_finalize", "l2_prepare", "l2_reduce",
  * "l2_apply", "bruteforce", "grad_pack", "grad_l1_tiles", "grad_l1_scan",
- * "grad_l1_eval", "grad_l2_reduce", "grad_l2_apply") is bracketed by two CUDA events
+ * "grad_l1_eval", "grad_l1_transpose", "grad_l2_reduce", "grad_l2_apply") is
+ * bracketed by two CUDA events
  * recorded on the context's stream.  Enabling (or disabling) clears what was
  * collected.  Off by default; costs two event records per group. */
 dm_status dm_profile_enable(dm_ctx* ctx, int enable);

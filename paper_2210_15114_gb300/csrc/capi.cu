@@ -455,8 +455,12 @@ dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64
             ProfScope ps(ctx, "grad_l1_scan");
             DM_TRY_CUDA(grad_l1_launch(a, 1, ctx->stream, &ctx->launches));
         }
-        ProfScope ps(ctx, "grad_l1_eval");
-        DM_TRY_CUDA(grad_l1_launch(a, 2, ctx->stream, &ctx->launches));
+        {
+            ProfScope ps(ctx, "grad_l1_eval");
+            DM_TRY_CUDA(grad_l1_launch(a, 2, ctx->stream, &ctx->launches));
+        }
+        ProfScope ps(ctx, "grad_l1_transpose");
+        DM_TRY_CUDA(grad_l1_launch(a, 3, ctx->stream, &ctx->launches));
         return DM_OK;
     }
     // squared l2: [X - mu, 1]^T [z_q, w_q] by the reduce kernel, then the closed form

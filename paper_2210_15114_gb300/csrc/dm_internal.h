@@ -183,7 +183,8 @@ struct GradArgs {
 size_t grad_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k);
 const void* grad_packed(const GradArgs& a);   // the packed (z_q, w_q) pairs, n x 2k
 cudaError_t grad_pack_launch(const GradArgs& a, cudaStream_t s, int64_t* launches);
-// stage 0: tile sums, 1: scan over tiles, 2: evaluation and scatter into G
+// stage 0: tile sums, 1: scan over tiles, 2: evaluation and scatter into a
+// coordinate-major copy, 3: transpose of that copy into G
 cudaError_t grad_l1_launch(const GradArgs& a, int stage, cudaStream_t s, int64_t* launches);
 cudaError_t grad_l2_apply_launch(const GradArgs& a, cudaStream_t s, int64_t* launches);
 

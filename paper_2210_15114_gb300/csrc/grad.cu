@@ -21,10 +21,13 @@
 //       head of the group entering each tile and I at the end of the group
 //       leaving it (forward and backward scans over the tiles);
 //   grad_tile_kernel<eval>: in-tile scans, the head and end of every
-//       position's tie group, and G[perm[r], c] += w S_z + z S_w.
-// Tiles are claimed so that the coordinates sharing a 32-byte sector of a
-// row of G are processed together: the scattered writes of one sector then
-// meet in L2 before it is written back.
+//       position's tie group, and Gt[c, perm[r]] = sum_q w S_z + z S_w;
+//   grad_transpose_kernel: Gt (d x n) into the caller's G (n x d).
+// Tiles are claimed coordinate by coordinate, so the scattered writes of the
+// evaluation pass fall in one column of Gt at a time (a few MB, held in L2
+// until every sector is complete).  Only the per-tile scan works in FP64
+// (the FP64 pipe is narrow); it hands the evaluation pass its per-tile
+// constants already in the accumulation type.
 //
 // Squared l2: with u = 1^T y and Y = (X - mu)^T y for y = z_q, w_q (the
 // reduce kernel on the packed columns), the sum over j expands to
@@ -164,26 +167,14 @@ struct GradParams {
     using Out = typename Types<DT>::Out;
     const V* xs; const int32_t* perm; int64_t n; int d;
     const V* P; int k;          // packed (z_q, w_q) pairs, n x 2k
+    using Acc = typename Types<DT>::Acc;
     int64_t T;                  // tiles per coordinate
-    int GS;                     // coordinates per 32-byte sector of a row of G
     int4* flags;                // d x T: first head, last head, first end, last end
     Wide* summ;                 // d x T x 2k x 3: sum, prefix at last head, at first end
-    const Wide* pre;            // d x T x 2k x 3: tile prefix, E entering, I leaving
-    const Wide* tot;            // d x 2k
-    Out* G; int64_t ldg;
+    const Acc* cst;             // d x T x 2k x 4: E + I - T for (head, end) outside/inside
+    Out* Gt;                    // d x n
 };
 
-// Block b -> (coordinate c, tile t): groups of GS coordinates, and within a
-// group the GS coordinates of one tile index on consecutive blocks.
-__device__ __forceinline__ void tile_of_block(int64_t b, int64_t T, int d, int GS, int* c, int64_t* t) {
-    const int64_t per_group = (int64_t)GS * T;
-    const int64_t g = b / per_group;
-    const int64_t rem = b - g * per_group;
-    const int gs = min(GS, d - (int)g * GS);
-    const int64_t tt = rem / gs;
-    *t = tt;
-    *c = (int)g * GS + (int)(rem - tt * gs);
-}
 
 template <class V, bool VEC>
 __device__ __forceinline__ void load_items(const V* __restrict__ src, int valid, int base, V* v) {
@@ -211,9 +202,8 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
     __shared__ int wsi[32];
     __shared__ int red[4];
 
-    int c;
-    int64_t t;
-    tile_of_block(blockIdx.x, p.T, p.d, p.GS, &c, &t);
+    const int c = (int)(blockIdx.x / p.T);             // coordinate-major claim order
+    const int64_t t = blockIdx.x - (int64_t)c * p.T;
     const int64_t ts = t * kGTile;
     const int valid = (int)min64(kGTile, p.n - ts);
     const int base = threadIdx.x * kGI;
@@ -302,31 +292,35 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
             // The tile sum is the inclusive prefix at the tile's last position
             // (not the block total, which sums in another order): a group
             // that runs to the end of the tile then cancels exactly.
+            // Values are picked in the accumulation type and converted once,
+            // by the thread that owns them.
             Wide* s = p.summ + slot * 3;
             if (threadIdx.x == 0) {
                 if (last_head < 0) { s[1] = 0; s[4] = 0; }
                 if (first_end == kNone) { s[2] = 0; s[5] = 0; }
             }
+            Acc vz = 0, vw = 0, hz = 0, hw = 0, fz = 0, fw = 0;
+            bool has_v = false, has_h = false, has_f = false;
 #pragma unroll
             for (int j = 0; j < kGI; ++j) {
-                if (base + j == valid - 1) { s[0] = (Wide)iz[j]; s[3] = (Wide)iw[j]; }
-                if (base + j == last_head) { s[1] = (Wide)(iz[j] - z[j]); s[4] = (Wide)(iw[j] - w[j]); }
-                if (base + j == first_end) { s[2] = (Wide)iz[j]; s[5] = (Wide)iw[j]; }
+                if (base + j == valid - 1) { vz = iz[j]; vw = iw[j]; has_v = true; }
+                if (base + j == last_head) { hz = iz[j] - z[j]; hw = iw[j] - w[j]; has_h = true; }
+                if (base + j == first_end) { fz = iz[j]; fw = iw[j]; has_f = true; }
             }
+            if (has_v) { s[0] = (Wide)vz; s[3] = (Wide)vw; }
+            if (has_h) { s[1] = (Wide)hz; s[4] = (Wide)hw; }
+            if (has_f) { s[2] = (Wide)fz; s[5] = (Wide)fw; }
         } else {
 #pragma unroll
             for (int j = 0; j < kGI; ++j) { Iz[base + j] = iz[j]; Iw[base + j] = iw[j]; }
             __syncthreads();
-            const Wide* pz = p.pre + slot * 3;
-            const Wide* pw = pz + 3;
-            const Wide TZ = p.tot[(int64_t)c * K2 + 2 * q], TW = p.tot[(int64_t)c * K2 + 2 * q + 1];
             // E(a) + I(b) - T with the parts that lie outside the tile taken
             // from the scan: (head outside, end outside), (outside, inside),
             // (inside, outside), (inside, inside)
-            const Acc z00 = (Acc)(pz[1] + pz[2] - TZ), w00 = (Acc)(pw[1] + pw[2] - TW);
-            const Acc z01 = (Acc)(pz[1] + pz[0] - TZ), w01 = (Acc)(pw[1] + pw[0] - TW);
-            const Acc z10 = (Acc)(pz[0] + pz[2] - TZ), w10 = (Acc)(pw[0] + pw[2] - TW);
-            const Acc z11 = (Acc)(2 * pz[0] - TZ), w11 = (Acc)(2 * pw[0] - TW);
+            const Acc* kz = p.cst + slot * 4;
+            const Acc* kw = kz + 4;
+            const Acc z00 = kz[0], z01 = kz[1], z10 = kz[2], z11 = kz[3];
+            const Acc w00 = kw[0], w01 = kw[1], w10 = kw[2], w11 = kw[3];
 #pragma unroll
             for (int j = 0; j < kGI; ++j) {
                 if (base + j >= valid) continue;
@@ -343,17 +337,18 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
     if (EVAL) {
 #pragma unroll
         for (int j = 0; j < kGI; ++j)
-            if (base + j < valid) p.G[(int64_t)pi[j] * p.ldg + c] = (Out)g[j];
+            if (base + j < valid) p.Gt[(int64_t)c * p.n + pi[j]] = (Out)g[j];
     }
 }
 
 // One block per (coordinate, column, z or w): forward scan of the tile sums
 // (tile prefixes, E at the head of the group entering each tile), then a
 // backward scan (I at the end of the group leaving each tile).
-template <class W>
+template <class W, class A>
 __global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__ flags,
-                                                        const W* __restrict__ summ, W* pre, W* tot,
-                                                        int64_t n, int64_t T, int K2) {
+                                                        const W* __restrict__ summ, W* pre,
+                                                        A* __restrict__ cst, int64_t n, int64_t T,
+                                                        int K2) {
     __shared__ W vals[kGT];
     __shared__ W ws[64];
     __shared__ int wsi[32];
@@ -379,8 +374,7 @@ __global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__
         carry_tp += chunk;
         __syncthreads();
     }
-    if (tid == 0) tot[(int64_t)c * K2 + qy] = carry_tp;
-    __syncthreads();
+    const W total = carry_tp;
     W carry_i = 0;
     for (int64_t c0 = ((T - 1) / kGT) * kGT; c0 >= 0; c0 -= kGT) {
         const int64_t t = c0 + tid;
@@ -395,9 +389,38 @@ __global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__
         const int valid = in ? (int)min64(kGTile, n - t * kGTile) : 0;
         const bool end_at_last = in && f.w == valid - 1;
         const W ir = end_at_last ? tp + summ[slot * 3] : (idx != kNone ? vals[idx] : carry_i);
-        if (in) pre[slot * 3 + 2] = ir;
+        if (in) {
+            const W el = pre[slot * 3 + 1];
+            A* k4 = cst + slot * 4;
+            k4[0] = (A)(el + ir - total);
+            k4[1] = (A)(el + tp - total);
+            k4[2] = (A)(tp + ir - total);
+            k4[3] = (A)(2 * tp - total);
+        }
         if (first != kNone) carry_i = vals[first];
         __syncthreads();
+    }
+}
+
+// G (n x d, leading dimension ldg) = Gt^T (Gt: d x n), through 32 x 32 tiles
+// in shared memory: coalesced reads of Gt rows and writes of G rows.
+template <class Out>
+__global__ void __launch_bounds__(256) grad_transpose_kernel(const Out* __restrict__ Gt, int64_t n, int d,
+                                                             Out* __restrict__ G, int64_t ldg) {
+    __shared__ Out tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {
+        const int c = c0 + r;
+        const int64_t i = i0 + tx;
+        if (c < d && i < n) tile[r][tx] = Gt[(int64_t)c * n + i];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r;
+        const int c = c0 + tx;
+        if (c < d && i < n) G[i * ldg + c] = tile[tx][r];
     }
 }
 
@@ -455,7 +478,7 @@ grad_l2_apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int
 
 struct GradLayout {
     int64_t T;
-    size_t p, flags, summ, pre, tot, total;
+    size_t p, flags, summ, pre, cst, gt, total;
 };
 
 constexpr size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -468,8 +491,9 @@ GradLayout grad_layout(dm_dtype t, int64_t n, int64_t d, int64_t k) {
     L.flags = al256(L.p + (size_t)n * K2 * dtype_size(t));
     L.summ = al256(L.flags + 16 * (size_t)(d * L.T));
     L.pre = al256(L.summ + 8 * 3 * K2 * (size_t)(d * L.T));
-    L.tot = al256(L.pre + 8 * 3 * K2 * (size_t)(d * L.T));
-    L.total = al256(L.tot + 8 * K2 * (size_t)d);
+    L.cst = al256(L.pre + 8 * 3 * K2 * (size_t)(d * L.T));
+    L.gt = al256(L.cst + 8 * 4 * K2 * (size_t)(d * L.T));
+    L.total = al256(L.gt + out_size(t) * (size_t)n * (size_t)d);
     return L;
 }
 
@@ -489,6 +513,7 @@ cudaError_t grad_pack_t(const GradArgs& a, cudaStream_t s, int64_t* launches) {
 template <dm_dtype DT>
 GradParams<DT> make_params(const GradArgs& a) {
     using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
     const GradLayout L = grad_layout(a.dtype, a.n, a.d, a.k);
@@ -501,20 +526,19 @@ GradParams<DT> make_params(const GradArgs& a) {
     p.P = reinterpret_cast<const V*>(sc + L.p);
     p.k = (int)a.k;
     p.T = L.T;
-    p.GS = (int)std::min<int64_t>(32 / (int64_t)sizeof(Out), a.d);
     p.flags = reinterpret_cast<int4*>(sc + L.flags);
     p.summ = reinterpret_cast<Wide*>(sc + L.summ);
-    p.pre = reinterpret_cast<const Wide*>(sc + L.pre);
-    p.tot = reinterpret_cast<const Wide*>(sc + L.tot);
-    p.G = static_cast<Out*>(a.G);
-    p.ldg = a.ldg;
+    p.cst = reinterpret_cast<const Acc*>(sc + L.cst);
+    p.Gt = reinterpret_cast<Out*>(sc + L.gt);
     return p;
 }
 
 template <dm_dtype DT>
 cudaError_t grad_l1_stage_t(const GradArgs& a, int stage, cudaStream_t s, int64_t* launches) {
     using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
+    using Out = typename Types<DT>::Out;
     GradParams<DT> p = make_params<DT>(a);
     const GradLayout L = grad_layout(a.dtype, a.n, a.d, a.k);
     unsigned char* sc = static_cast<unsigned char*>(a.scratch);
@@ -528,12 +552,17 @@ cudaError_t grad_l1_stage_t(const GradArgs& a, int stage, cudaStream_t s, int64_
         if (vec) grad_tile_kernel<DT, false, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
         else grad_tile_kernel<DT, false, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
     } else if (stage == 1) {
-        grad_scan_kernel<Wide><<<(unsigned)(a.d * 2 * a.k), kGT, 0, s>>>(
-            p.flags, p.summ, reinterpret_cast<Wide*>(sc + L.pre), reinterpret_cast<Wide*>(sc + L.tot),
+        grad_scan_kernel<Wide, Acc><<<(unsigned)(a.d * 2 * a.k), kGT, 0, s>>>(
+            p.flags, p.summ, reinterpret_cast<Wide*>(sc + L.pre), reinterpret_cast<Acc*>(sc + L.cst),
             a.n, L.T, (int)(2 * a.k));
-    } else {
+    } else if (stage == 2) {
         if (vec) grad_tile_kernel<DT, true, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
         else grad_tile_kernel<DT, true, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+    } else {
+        const int64_t bx = (a.n + 31) / 32;
+        if (bx > INT_MAX) return cudaErrorInvalidConfiguration;
+        dim3 grid((unsigned)bx, (unsigned)((a.d + 31) / 32));
+        grad_transpose_kernel<Out><<<grid, 256, 0, s>>>(p.Gt, a.n, (int)a.d, static_cast<Out*>(a.G), a.ldg);
     }
     *launches += 1;
     return cudaGetLastError();

@@ -540,8 +540,8 @@ l1_aggregate_kernel(const typename Types<DT>::V* __restrict__ xs, const int32_t*
             for (int u = 0; u < U; ++u) { pe[u] = pe_n[u]; dx[u] = dx_n[u]; }
         }
         if (bad) set_error(err, kErrInternal);
-        const Wide bm = (Wide)b - (Wide)mu[(int64_t)c * mu_stride];
-        Wide mine = 0;
+        // Lane q keeps the sums of column q; lanes < NV then convert once.
+        Acc sel_a = 0, sel_x = 0;
 #pragma unroll
         for (int q = 0; q < KC; ++q) {
             Acc a = sz[q], x = sxz[q];
@@ -550,10 +550,18 @@ l1_aggregate_kernel(const typename Types<DT>::V* __restrict__ xs, const int32_t*
                 a += __shfl_xor_sync(0xffffffffu, a, o);
                 x += __shfl_xor_sync(0xffffffffu, x, o);
             }
-            if (lane == q) mine = (Wide)a;
-            if (lane == KC + q) mine = bm * (Wide)a + (Wide)x;
+            if (lane == q || lane == KC + q) { sel_a = a; sel_x = x; }
         }
-        if (lane < NV) agg[tile * NV + lane] = mine;
+        if (lane < NV) {
+            Wide mine;
+            if (lane < KC) {
+                mine = (Wide)sel_a;
+            } else {
+                const Wide bm = (Wide)b - (Wide)mu[(int64_t)c * mu_stride];
+                mine = bm * (Wide)sel_a + (Wide)sel_x;
+            }
+            agg[tile * NV + lane] = mine;
+        }
     }
 }
 
@@ -594,6 +602,12 @@ l1_finalize_kernel(const typename Types<DT>::Acc* __restrict__ outg,
                    typename Types<DT>::Out* __restrict__ out, int64_t ldo) {
     using Acc = typename Types<DT>::Acc;
     using Out = typename Types<DT>::Out;
+    // The per-column terms R^T Z and 1^T Z, converted once per block (a
+    // conversion from the wide type is an FP64-pipe instruction).
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc* rs = reinterpret_cast<Acc*>(smem_raw);      // [0, k): R^T Z, [k, 2k): 1^T Z
+    for (int j = threadIdx.x; j < 2 * k; j += kThreads) rs[j] = (Acc)res[j];
+    __syncthreads();
     const int nv = (k + VEC - 1) / VEC;
     const int64_t total = n * nv;
     for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < total;
@@ -615,7 +629,7 @@ l1_finalize_kernel(const typename Types<DT>::Acc* __restrict__ outg,
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
             const int j = min(j0 + q, k - 1);
-            o[q] = (Out)(v[q] + ((Acc)res[j] - Ri * (Acc)res[k + j]));
+            o[q] = (Out)(v[q] + (rs[j] - Ri * rs[k + j]));
         }
         if constexpr (VEC == 4 && sizeof(Out) == 4) {
             *reinterpret_cast<float4*>(out + i * ldo + j0) = make_float4(o[0], o[1], o[2], o[3]);
@@ -694,7 +708,7 @@ l1_prologue_kernel(const typename Types<DT>::V* __restrict__ Z, int64_t n, int k
                         cr[v] += rr[u] * (Acc)z[u][v];
                     }
                 }
-                if (++cnt == 16) {
+                if (++cnt == 32) {
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) { wu[v] += (Wide)cu[v]; wr[v] += (Wide)cr[v]; cu[v] = 0; cr[v] = 0; }
                     cnt = 0;
@@ -819,7 +833,10 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
         const int64_t fb = std::max<int64_t>(1, std::min<int64_t>((total + kThreads - 1) / kThreads,
                                                                    8 * (int64_t)a.num_sms));
         auto kern = vec ? l1_finalize_kernel<DT, KC, 4> : l1_finalize_kernel<DT, KC, 1>;
-        kern<<<(unsigned)fb, kThreads, 0, st>>>(
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(2 * a.k * sizeof(Acc)))) != cudaSuccess)
+            return e;
+        kern<<<(unsigned)fb, kThreads, 2 * (size_t)a.k * sizeof(Acc), st>>>(
             reinterpret_cast<const Acc*>(sc + L.outg), static_cast<const Acc*>(a.R),
             reinterpret_cast<const Wide*>(sc + L.res), a.n, (int)a.k,
             static_cast<typename Types<DT>::Out*>(a.out), a.ldo);
