@@ -79,6 +79,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replicas_value(ms_local, units_per_rank, world, device):
+    """Whole-job throughput of `world` independent replicas: every rank does
+    `units_per_rank` units per step; the job's step time is the slowest
+    rank's (max over ranks).  Returns (ms per step, units per second)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1e3)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -472,13 +486,8 @@ def main():
         return
 
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     units_step = 2 * a.n * a.d * a.k
-    value = world * units_step / (ms / 1e3)
+    ms, value = replicas_value(statistics.mean(step_ms), units_step, world, dev)
 
     if rank != 0:
         if world > 1:
