@@ -20,6 +20,9 @@ Three forms, all plain and slow on purpose:
   X, which the paper does not state: the chain rule on the definition, and
   the same through the sorted order (l1) or the Gram decomposition (squared
   l2).
+* ``block_krylov`` -- the randomized block Krylov iteration that the
+  paper's application section uses (through products A Z only) for the top
+  singular values and a low-rank approximation.
 * ``l2sq_identity`` -- the p = 2 query of Appendix A (Theorem
   "l2_squared_upper_bound"), with the typos of the printed algorithm read as
   the proof's Gram decomposition (Section 1.2): (Ay)_k = ||x_k||^2 sum_j y_j
@@ -288,6 +291,46 @@ def l2sq_grad_closed(X, W, Z) -> np.ndarray:
     XtW = X.T @ W
     coef = W @ sz + Z @ sw                          # n
     return 2 * (X * coef[:, None] - W @ XtZ.T - Z @ XtW.T)
+
+
+def block_krylov(product, Pi, q: int, rank: int):
+    """Randomized block Krylov iteration for the top `rank` singular values
+    and a rank-`rank` approximation of a symmetric matrix A that is reached
+    only through products Y = A Z (the application of Appendix C, Theorems
+    "musco" and "singular_values_system").  FP64, numpy.
+
+    Steps (for symmetric A the Krylov space of A^T A A Pi, ... is spanned
+    by powers of A): Q_1 = orth(A Pi); for i = 1..q: W = A Q_i, and -- while
+    i < q -- Q_{i+1} = orth(W minus its projections on Q_1..Q_i).  The
+    projections are removed twice, the block is orthonormalized (QR), and
+    the projections are removed twice more before a final QR: when A has
+    low rank the new block can be pure rounding noise, whose normalized
+    directions lean on the earlier blocks until they are projected out
+    again.  Then the Rayleigh-Ritz step M = Q^T (A Q)
+    on Q = [Q_1 .. Q_q] (the products A Q_i are reused), its eigenpairs
+    (theta, V), and the `rank` pairs of largest |theta|: singular values
+    |theta| and A ~ U diag(theta) U^T with U = Q V.
+    Returns (theta, U) ordered by decreasing |theta|."""
+    Pi = np.asarray(Pi, dtype=np.float64)
+    W = np.asarray(product(Pi), dtype=np.float64)
+    blocks, products = [], []
+    for i in range(q):
+        for _ in range(2):
+            for _ in range(2):
+                for B in blocks:
+                    W = W - B @ (B.T @ W)
+            W, _ = np.linalg.qr(W)
+        Qi = W
+        blocks.append(Qi)
+        W = np.asarray(product(Qi), dtype=np.float64)
+        products.append(W)
+    Q = np.concatenate(blocks, axis=1)
+    AQ = np.concatenate(products, axis=1)
+    M = Q.T @ AQ
+    M = 0.5 * (M + M.T)
+    theta, V = np.linalg.eigh(M)
+    order = np.argsort(-np.abs(theta))[:rank]
+    return theta[order], Q @ V[:, order]
 
 
 def relative_error(got, want) -> float:

@@ -116,3 +116,15 @@ def workload_gradient(n: int = 1 << 21, d: int = 64, k: int = 1, tie_heavy: bool
     Z = gaussian_queries(n, k, SEED_ZG, dtype=np.float32)
     return X, W, Z
 
+
+
+SEED_PI = 3    # the Gaussian start block of the Krylov iteration
+
+
+def workload_krylov(n: int = 1 << 22, d: int = 16, k: int = 40, clusters: int = 10):
+    """Points for the block Krylov row: a `clusters`-cluster Gaussian mixture
+    (means N(0, 10^2), sd 1) in FP32, and the FP32 N(0, 1) start block Pi
+    (n x k)."""
+    X = gaussian_mixture(n, d, clusters, SEED_X, 10.0, 1.0, dtype=np.float32)
+    Pi = gaussian_queries(n, k, SEED_PI, dtype=np.float32)
+    return X, Pi
