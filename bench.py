@@ -60,6 +60,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--no-krylov", action="store_true", help="skip the block Krylov measurement")
     ap.add_argument("--grad-n", type=int, default=1 << 21)
     ap.add_argument("--grad-d", type=int, default=64)
     ap.add_argument("--profile-only", action="store_true",
@@ -387,6 +388,63 @@ def measure_gradient(dm, ctx, stream, flush, dev, peak, n=1 << 21, d=64, reps=10
     return res
 
 
+def measure_krylov(dm, ctx, stream, dev, n=1 << 22, d=16, k=40, q=8, rank=32, reps=2):
+    """Top-32 singular values / rank-32 approximation by block Krylov
+    iteration (q + 1 products of k columns each), timed end to end with CUDA
+    events (prepare included), plus accuracy checks outside the timing."""
+    import numpy as np
+    import torch
+    from paper_2210_15114_gb300 import inputs
+    from paper_2210_15114_gb300.krylov import block_krylov
+    X, Pi = inputs.workload_krylov(n=n, d=d, k=k)
+    Xd, Pid = torch.from_numpy(X).to(dev), torch.from_numpy(Pi).to(dev)
+    res = {"workload": f"10-cluster mixture n={n} d={d} fp32; k={k}, q={q}, rank={rank}",
+           "products_per_run": q + 1}
+    for metric in ("l1", "l2sq"):
+        plan = dm.dm_prepare(ctx, metric, Xd)
+        block_krylov(plan, Pid, q, rank)            # warm-up
+        torch.cuda.synchronize(dev)
+        dm.dm_profile_enable(ctx, True)
+        times = []
+        for _ in range(reps):
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            plan = dm.dm_prepare(ctx, metric, Xd)
+            theta, U = block_krylov(plan, Pid, q, rank)
+            e_.record(stream)
+            e_.synchronize()
+            times.append(s_.elapsed_time(e_))
+        prof = dm.dm_profile_read(ctx)
+        dm.dm_profile_enable(ctx, False)
+        prep = ("sort_keygen_hist", "sort_onesweep", "l1_rowsum") if metric == "l1" else ("l2_prepare",)
+        prod_ms = sum(t for g, (l, t) in prof.items() if g not in prep) / reps
+        prep_ms = sum(t for g, (l, t) in prof.items() if g in prep) / reps
+        ms = statistics.mean(times)
+        entry = {"ms": ms, "prepare_ms": prep_ms, "products_ms": prod_ms,
+                 "dense_linear_algebra_ms": ms - prod_ms - prep_ms,
+                 "top_singular_values": [abs(float(t)) for t in theta[:8].cpu()]}
+        if metric == "l2sq":
+            Xc = X.astype(np.float64)
+            Xc -= Xc.mean(axis=0)
+            B = np.concatenate([np.ones((n, 1)), (Xc * Xc).sum(1, keepdims=True), Xc], axis=1)
+            C = np.zeros((d + 2, d + 2))
+            C[0, 1] = C[1, 0] = 1.0
+            C[2:, 2:] = -2 * np.eye(d)
+            L = np.linalg.cholesky(B.T @ B)
+            ev = np.linalg.eigvalsh(L.T @ C @ L)
+            ev = ev[np.argsort(-np.abs(ev))]
+            th = theta.cpu().numpy()
+            entry["max_rel_err_vs_compressed_form"] = float(np.max(np.abs(th[:d + 2] - ev) / np.abs(ev)))
+            entry["max_tail_over_top"] = float(np.max(np.abs(th[d + 2:])) / abs(th[0]))
+        else:
+            AU = dm.dm_matmat(plan, U.contiguous()).double()
+            r = torch.linalg.norm(AU[:, :8] - U.double()[:, :8] * theta[:8].to(AU.device), dim=0)
+            entry["top8_residual_over_theta1"] = float(r.max().item() / abs(theta[0].item()))
+        res[metric] = entry
+        del plan, U
+    return res
+
+
 # ------------------------------------------------------------- reference arm
 def run_reference(a):
     rank, world, _ = dist_env()
@@ -532,6 +590,11 @@ def main():
     if not a.no_grad:
         grad = measure_gradient(dm, ctx, stream, flush, dev, peak, n=a.grad_n, d=a.grad_d)
 
+    # ---- block Krylov rank-32 (n = 2^22, d = 16, k = 40, q = 8)
+    krylov = None
+    if not a.no_krylov:
+        krylov = measure_krylov(dm, ctx, stream, dev)
+
     # ---- brute force (the plain method) and accuracy
     brute = None
     if not a.no_brute:
@@ -593,7 +656,7 @@ def main():
             "gpu_launches": launches, "launches_per_step": launches / a.steps,
             "wall_s_timed_region": t_wall,
             "parts_ms": parts, "kernels": kernels, "roofline": roofline, "l1_query_all_kernels": l1_query_all,
-            "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad,
+            "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad, "krylov": krylov,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:
