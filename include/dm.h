@@ -136,6 +136,43 @@ dm_status dm_matmat(dm_plan* plan, const void* Z, int64_t k, int64_t ldz,
 dm_status dm_grad(dm_plan* plan, const void* W, int64_t ldw, const void* Z, int64_t ldz,
                   int64_t k, void* G, int64_t ldg);
 
+/* ------------------------------------------------------------- batches
+ * Many independent point sets, each with its own block of query vectors,
+ * processed as one unit: every run preprocesses every set (Algorithm 1 for
+ * DM_L1, the column means for DM_L2SQ) and computes out_s = A_s Z_s for each
+ * (Lemma "matrixmult" per set), all replayed from one CUDA graph.
+ *
+ * dm_batch_create takes host arrays of length nsets: sizes n[s], d[s], k[s],
+ * leading dimensions, and DEVICE pointers X[s] (n x d), Z[s] (n x k) and
+ * out[s] (n x k; element types as for dm_matmat).  The pointers are baked
+ * into the graph: later runs read whatever X[s] and Z[s] hold then, and the
+ * buffers must stay alive until dm_batch_destroy.  Creation allocates every
+ * plan and scratch buffer, spreads the sets over `lanes` concurrent streams
+ * (largest sets first, each to the least loaded lane) and captures the graph.
+ * lanes = 0 asks for the autotuner: it captures the batch with 1, 2, 4, 8
+ * and 16 lanes, times four replays of each, keeps the fastest (so creation
+ * runs the whole batch about 20 times) and remembers the choice for batches
+ * of the same shape in this process.  Inside the graph nothing synchronizes:
+ * all radix passes run (no histogram read-back) and non-finite coordinates
+ * are reported by dm_sync, not by the run.
+ *
+ * dm_batch_run launches the graph, ordered after earlier work on the
+ * context's stream and before later work there (asynchronous).  Runs of one
+ * batch must not overlap each other (they share the plans and scratch). */
+typedef struct dm_batch dm_batch;
+
+dm_status dm_batch_create(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, int64_t nsets,
+                          const int64_t* n, const int64_t* d, const void* const* X,
+                          const int64_t* ldx, const int64_t* k, const void* const* Z,
+                          const int64_t* ldz, void* const* out, const int64_t* ldo, int lanes,
+                          dm_batch** batch);
+dm_status dm_batch_run(dm_batch* batch);
+/* Number of concurrent lanes the batch runs on (the autotuner's choice when
+ * it was created with lanes = 0). */
+int dm_batch_lanes(const dm_batch* batch);
+/* Synchronize, then free the batch's graph, streams, plans and scratch. */
+void dm_batch_destroy(dm_batch* batch);
+
 /* Wait for the context's stream and return (then clear) the first device-side
  * error latched since the last dm_sync. */
 dm_status dm_sync(dm_ctx* ctx);

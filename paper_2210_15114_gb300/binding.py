@@ -69,6 +69,10 @@ def load() -> ctypes.CDLL:
             "dm_matvec_l2sq": ([P, P, P], I32),
             "dm_matmat": ([P, P, I64, I64, P, I64], I32),
             "dm_grad": ([P, P, I64, P, I64, I64, P, I64], I32),
+            "dm_batch_create": ([P, I32, I32, I64, P, P, P, P, P, P, P, P, P, I32, P], I32),
+            "dm_batch_run": ([P], I32),
+            "dm_batch_lanes": ([P], I32),
+            "dm_batch_destroy": ([P], None),
             "dm_sync": ([P], I32),
             "dm_status_string": ([I32], ctypes.c_char_p),
             "dm_plan_export": ([P, P, P], I32),
@@ -261,6 +265,70 @@ def dm_grad(plan: Plan, W, Z, out=None):
                           ctypes.c_void_p(_dev_ptr(Z2)), _ld(Z2), W2.shape[1],
                           ctypes.c_void_p(_dev_ptr(out)), _ld(out)), "dm_grad")
     return out
+
+
+class Batch:
+    """Owner of a dm_batch handle; keeps the set tensors alive (the graph
+    reads them by address)."""
+
+    def __init__(self, handle, ctx, Xs, Zs, outs):
+        self.handle = handle
+        self.ctx = ctx
+        self.Xs, self.Zs, self.outs = Xs, Zs, outs
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dm_batch_destroy(self.handle)
+            self.handle = None
+
+
+def dm_batch_create(ctx: Context, metric, Xs, Zs, outs=None, lanes: int = 0) -> Batch:
+    """dm_batch_create over lists of device tensors (X_s: n_s x d_s, Z_s:
+    n_s x k_s or n_s); outputs are allocated when `outs` is None."""
+    import torch
+    ns = len(Xs)
+    if ns != len(Zs) or ns < 1:
+        raise DMError(DM_ERR_INVALID_ARG, "Xs and Zs must be non-empty lists of equal length")
+    code = dtype_code(Xs[0].dtype)
+    X2 = [x.reshape(-1, 1) if x.ndim == 1 else x for x in Xs]
+    Z2 = [z.reshape(-1, 1) if z.ndim == 1 else z for z in Zs]
+    for x, z in zip(X2, Z2):
+        if dtype_code(x.dtype) != code or dtype_code(z.dtype) != code:
+            raise DMError(DM_ERR_INVALID_ARG, "all sets must share one element type")
+    if outs is None:
+        outs = [torch.empty((x.shape[0], z.shape[1]), dtype=out_torch_dtype(code), device=x.device)
+                for x, z in zip(X2, Z2)]
+    O2 = [o.reshape(-1, 1) if o.ndim == 1 else o for o in outs]
+    I64a = ctypes.c_int64 * ns
+    Pa = ctypes.c_void_p * ns
+    n = I64a(*[x.shape[0] for x in X2])
+    d = I64a(*[x.shape[1] for x in X2])
+    k = I64a(*[z.shape[1] for z in Z2])
+    ldx = I64a(*[_ld(x) for x in X2])
+    ldz = I64a(*[_ld(z) for z in Z2])
+    ldo = I64a(*[_ld(o) for o in O2])
+    xp = Pa(*[_dev_ptr(x) for x in X2])
+    zp = Pa(*[_dev_ptr(z) for z in Z2])
+    op = Pa(*[_dev_ptr(o) for o in O2])
+    h = ctypes.c_void_p()
+    _check(load().dm_batch_create(ctx.handle, METRICS[metric] if isinstance(metric, str) else int(metric), code, ns, n, d, xp, ldx, k, zp, ldz,
+                                  op, ldo, int(lanes), ctypes.byref(h)), "dm_batch_create")
+    return Batch(h.value, ctx, Xs, Zs, outs)
+
+
+def dm_batch_run(batch: Batch):
+    _check(load().dm_batch_run(batch.handle), "dm_batch_run")
+    return batch.outs
+
+
+def dm_batch_lanes(batch: Batch) -> int:
+    return int(load().dm_batch_lanes(batch.handle))
+
+
+def dm_batch_destroy(batch: Batch) -> None:
+    if batch.handle:
+        load().dm_batch_destroy(batch.handle)
+        batch.handle = None
 
 
 def dm_sync(ctx: Context) -> None:

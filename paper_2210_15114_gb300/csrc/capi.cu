@@ -2,6 +2,7 @@
 // the launch sequences of each call.  Host code only; kernels live in the
 // other translation units.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -58,6 +59,31 @@ struct dm_plan {
     void* mu = nullptr;
 };
 
+struct dm_batch {
+    dm_ctx* ctx = nullptr;
+    dm_metric metric = DM_L1;
+    dm_dtype dtype = DM_F32;
+    struct Set {
+        dm_plan* plan;
+        const void* X; int64_t ldx;
+        const void* Z; int64_t k, ldz;
+        void* out; int64_t ldo;
+        double cost;        // estimated bytes moved (scheduling weight)
+        int lane;
+    };
+    std::vector<Set> sets;
+    int lanes = 0;
+    cudaStream_t origin = nullptr;          // capture / launch stream
+    std::vector<cudaStream_t> streams;      // one per lane
+    std::vector<void*> scratch;             // one per lane
+    std::vector<size_t> scratch_bytes;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches_per_run = 0;
+};
+
 namespace {
 
 using namespace dm;
@@ -110,23 +136,40 @@ cudaEvent_t pool_event(dm_ctx* ctx) {
     return e;
 }
 
+// Where a launch sequence runs: the context (error word, launch count,
+// timing), a stream, a scratch buffer of known size, and whether the work is
+// being captured into a CUDA graph (then nothing may synchronize, allocate or
+// record timing events).
+struct Exec {
+    dm_ctx* ctx;
+    cudaStream_t stream;
+    unsigned char* scratch;
+    size_t scratch_bytes;
+    bool graph;
+};
+
 // Brackets one group of launches with events when timing is enabled.
 struct ProfScope {
     dm_ctx* ctx;
     const char* name;
+    cudaStream_t stream;
     cudaEvent_t start = nullptr;
     int64_t before = 0;
-    ProfScope(dm_ctx* c, const char* n) : ctx(c), name(n) {
-        if (!ctx->profiling) return;
+    bool on;
+    ProfScope(dm_ctx* c, const char* n) : ProfScope(c, n, c->stream, false) {}
+    ProfScope(const Exec& e, const char* n) : ProfScope(e.ctx, n, e.stream, e.graph) {}
+    ProfScope(dm_ctx* c, const char* n, cudaStream_t st, bool graph)
+        : ctx(c), name(n), stream(st), on(c->profiling && !graph) {
+        if (!on) return;
         start = pool_event(ctx);
         before = ctx->launches;
-        if (start) cudaEventRecord(start, ctx->stream);
+        if (start) cudaEventRecord(start, stream);
     }
     ~ProfScope() {
-        if (!ctx->profiling || !start) return;
+        if (!on || !start) return;
         cudaEvent_t stop = pool_event(ctx);
         if (!stop) { ctx->event_pool.push_back(start); return; }
-        cudaEventRecord(stop, ctx->stream);
+        cudaEventRecord(stop, stream);
         ctx->pending.push_back({name, start, stop, ctx->launches - before});
     }
 };
@@ -244,110 +287,148 @@ dm_status take_device_error(dm_ctx* ctx) {
 }
 
 // ------------------------------------------------------------- l1 prepare
-dm_status prepare_l1(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
-    const dm_dtype t = p->dtype;
-    const int64_t n = p->n, d = p->d;
+// Scratch of the sort: [hist | counters | lookback] (zeroed), then the key
+// and payload ping-pong buffers.
+struct SortLayout {
+    size_t hist, cnt, lb, zero_bytes, ka, kb, va, vb, total;
+};
+
+SortLayout sort_layout(dm_dtype t, int64_t n, int64_t d) {
     const size_t nd = (size_t)n * (size_t)d;
     const size_t key_bytes = key_bits(t) / 8;
+    SortLayout L;
+    L.hist = 0;
+    L.cnt = up16(L.hist + sort_hist_words(t, d) * 4);
+    L.lb = up16(L.cnt + 4 * (size_t)sort_passes(t));
+    L.zero_bytes = up16(L.lb + sort_lookback_words(t, n, d) * 4);
+    L.ka = L.zero_bytes;
+    L.kb = up16(L.ka + nd * key_bytes);
+    L.va = up16(L.kb + nd * key_bytes);
+    L.vb = up16(L.va + nd * 4);
+    L.total = up16(L.vb + nd * 4);
+    return L;
+}
+
+dm_status alloc_l1_plan(dm_plan* p) {
+    const size_t nd = (size_t)p->n * (size_t)p->d;
+    DM_TRY(plan_alloc(p, nd * dtype_size(p->dtype), &p->xs));
+    DM_TRY(plan_alloc(p, nd * 4, reinterpret_cast<void**>(&p->perm)));
+    DM_TRY(plan_alloc(p, (size_t)p->n * acc_size(p->dtype), &p->R));
+    return DM_OK;
+}
+
+// The sort of every column (Algorithm 1) and the row sums R.  Outside a
+// graph, the digit histograms are read back to skip digit positions that
+// are constant in every column (a stable pass over a constant digit is the
+// identity) and non-finite input is reported at once; in a graph every pass
+// runs and non-finite input is left in the error word for dm_sync.
+dm_status prepare_l1_run(const Exec& e, dm_plan* p, const void* X, int64_t ldx) {
+    dm_ctx* ctx = e.ctx;
+    const dm_dtype t = p->dtype;
+    const int64_t n = p->n, d = p->d;
     const int P = sort_passes(t);
     const size_t hist_words = sort_hist_words(t, d);
-    const size_t lb_words = sort_lookback_words(t, n, d);
-
-    DM_TRY(plan_alloc(p, nd * dtype_size(t), &p->xs));
-    DM_TRY(plan_alloc(p, nd * 4, reinterpret_cast<void**>(&p->perm)));
-
-    // arena: [hist | counters | lookback] (zeroed) then keys_a, keys_b, vals_a, vals_b
-    const size_t o_hist = 0;
-    const size_t o_cnt = up16(o_hist + hist_words * 4);
-    const size_t o_lb = up16(o_cnt + 4 * (size_t)P);
-    const size_t zero_bytes = up16(o_lb + lb_words * 4);
-    const size_t o_ka = zero_bytes;
-    const size_t o_kb = up16(o_ka + nd * key_bytes);
-    const size_t o_va = up16(o_kb + nd * key_bytes);
-    const size_t o_vb = up16(o_va + nd * 4);
-    const size_t total = up16(o_vb + nd * 4);
-    DM_TRY(ensure_arena(ctx, total));
-    unsigned char* base = static_cast<unsigned char*>(ctx->arena);
+    const SortLayout L = sort_layout(t, n, d);
+    if (e.scratch_bytes < L.total) return DM_ERR_INTERNAL;
+    unsigned char* base = e.scratch;
 
     SortArgs a{};
     a.dtype = t;
     a.X = X; a.n = n; a.d = d; a.ldx = ldx;
-    a.keys_a = base + o_ka; a.keys_b = base + o_kb;
-    a.vals_a = reinterpret_cast<int32_t*>(base + o_va);
-    a.vals_b = reinterpret_cast<int32_t*>(base + o_vb);
-    a.hist = reinterpret_cast<uint32_t*>(base + o_hist);
-    a.counters = reinterpret_cast<uint32_t*>(base + o_cnt);
-    a.lookback = reinterpret_cast<uint32_t*>(base + o_lb);
+    a.keys_a = base + L.ka; a.keys_b = base + L.kb;
+    a.vals_a = reinterpret_cast<int32_t*>(base + L.va);
+    a.vals_b = reinterpret_cast<int32_t*>(base + L.vb);
+    a.hist = reinterpret_cast<uint32_t*>(base + L.hist);
+    a.counters = reinterpret_cast<uint32_t*>(base + L.cnt);
+    a.lookback = reinterpret_cast<uint32_t*>(base + L.lb);
     a.sorted_out = p->xs;
     a.perm_out = p->perm;
     a.err = ctx->err;
 
-    DM_TRY_CUDA(cudaMemsetAsync(base, 0, zero_bytes, ctx->stream));
+    DM_TRY_CUDA(cudaMemsetAsync(base, 0, L.zero_bytes, e.stream));
     {
-        ProfScope ps(ctx, "sort_keygen_hist");
-        DM_TRY_CUDA(sort_launch_keygen(a, ctx->stream, &ctx->launches));
+        ProfScope ps(e, "sort_keygen_hist");
+        DM_TRY_CUDA(sort_launch_keygen(a, e.stream, &ctx->launches));
     }
-
-    // Read the histograms back: skip digit positions that are constant in
-    // every column (a stable pass over a constant digit is the identity).
-    if (ctx->host_hist_words < hist_words) {
-        if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
-        ctx->host_hist = nullptr;
-        ctx->host_hist_words = 0;
-        DM_TRY_CUDA(cudaMallocHost(reinterpret_cast<void**>(&ctx->host_hist), hist_words * 4));
-        ctx->host_hist_words = hist_words;
-    }
-    DM_TRY_CUDA(cudaMemcpyAsync(ctx->host_hist, a.hist, hist_words * 4, cudaMemcpyDeviceToHost,
-                                ctx->stream));
-    DM_TRY(take_device_error(ctx));   // synchronizes
     std::vector<int> passes;
-    for (int q = 0; q < P; ++q) {
-        bool needed = false;
-        for (int64_t c = 0; c < d && !needed; ++c) {
-            const uint32_t* h = ctx->host_hist + ((size_t)c * P + q) * 256;
-            bool constant = false;
-            for (int b = 0; b < 256; ++b)
-                if ((int64_t)h[b] == n) { constant = true; break; }
-            needed = !constant;
+    if (e.graph) {
+        for (int q = 0; q < P; ++q) passes.push_back(q);
+    } else {
+        if (ctx->host_hist_words < hist_words) {
+            if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
+            ctx->host_hist = nullptr;
+            ctx->host_hist_words = 0;
+            DM_TRY_CUDA(cudaMallocHost(reinterpret_cast<void**>(&ctx->host_hist), hist_words * 4));
+            ctx->host_hist_words = hist_words;
         }
-        if (needed) passes.push_back(q);
+        DM_TRY_CUDA(cudaMemcpyAsync(ctx->host_hist, a.hist, hist_words * 4, cudaMemcpyDeviceToHost,
+                                    e.stream));
+        DM_TRY(take_device_error(ctx));   // synchronizes
+        for (int q = 0; q < P; ++q) {
+            bool needed = false;
+            for (int64_t c = 0; c < d && !needed; ++c) {
+                const uint32_t* h = ctx->host_hist + ((size_t)c * P + q) * 256;
+                bool constant = false;
+                for (int b = 0; b < 256; ++b)
+                    if ((int64_t)h[b] == n) { constant = true; break; }
+                needed = !constant;
+            }
+            if (needed) passes.push_back(q);
+        }
+        if (passes.empty()) passes.push_back(0);   // still writes values + permutation
     }
-    if (passes.empty()) passes.push_back(0);   // still writes values + permutation
     {
-        ProfScope ps(ctx, "sort_onesweep");
-        DM_TRY_CUDA(sort_launch_passes(a, passes.data(), (int)passes.size(), ctx->stream,
+        ProfScope ps(e, "sort_onesweep");
+        DM_TRY_CUDA(sort_launch_passes(a, passes.data(), (int)passes.size(), e.stream,
                                        &ctx->launches));
     }
     // R_i for the part of the query that is linear in the point (shift: the
     // median of each column, xs[c * n + n / 2]).
-    DM_TRY(plan_alloc(p, (size_t)n * acc_size(t), &p->R));
     {
-        ProfScope ps(ctx, "l1_rowsum");
+        ProfScope ps(e, "l1_rowsum");
         DM_TRY_CUDA(rowsum_launch(t, X, n, d, ldx,
                                   static_cast<unsigned char*>(p->xs) + (size_t)(n / 2) * dtype_size(t),
-                                  n, p->R, ctx->stream, &ctx->launches));
+                                  n, p->R, e.stream, &ctx->launches));
     }
     return DM_OK;
 }
 
+Exec ctx_exec(dm_ctx* ctx) {
+    return Exec{ctx, ctx->stream, static_cast<unsigned char*>(ctx->arena), ctx->arena_bytes, false};
+}
+
+dm_status prepare_l1(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
+    DM_TRY(alloc_l1_plan(p));
+    DM_TRY(ensure_arena(ctx, sort_layout(p->dtype, p->n, p->d).total));
+    return prepare_l1_run(ctx_exec(ctx), p, X, ldx);
+}
+
 // ------------------------------------------------------------- l2 prepare
-dm_status prepare_l2(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
-    const dm_dtype t = p->dtype;
+size_t prepare_l2_scratch(dm_plan* p) {
+    L2PrepArgs a{};
+    a.n = p->n; a.d = p->d;
+    return (size_t)l2prep_blocks(a) * p->d * 8 + 16;
+}
+
+dm_status prepare_l2_run(const Exec& e, dm_plan* p, const void* X, int64_t ldx) {
+    dm_ctx* ctx = e.ctx;
     p->X = X;
     p->ldx = ldx;
-    DM_TRY(plan_alloc(p, (size_t)p->d * dtype_size(t), &p->mu));
     L2PrepArgs a{};
-    a.dtype = t;
+    a.dtype = p->dtype;
     a.X = X; a.n = p->n; a.d = p->d; a.ldx = ldx;
     a.mu = p->mu; a.err = ctx->err;
-    const int blocks = l2prep_blocks(a);
-    DM_TRY(ensure_arena(ctx, (size_t)blocks * p->d * 8 + 16));
-    a.partial = ctx->arena;
-    {
-        ProfScope ps(ctx, "l2_prepare");
-        DM_TRY_CUDA(l2prep_launch(a, ctx->stream, &ctx->launches));
-    }
+    if (e.scratch_bytes < prepare_l2_scratch(p)) return DM_ERR_INTERNAL;
+    a.partial = e.scratch;
+    ProfScope ps(e, "l2_prepare");
+    DM_TRY_CUDA(l2prep_launch(a, e.stream, &ctx->launches));
     return DM_OK;
+}
+
+dm_status prepare_l2(dm_ctx* ctx, dm_plan* p, const void* X, int64_t ldx) {
+    DM_TRY(plan_alloc(p, (size_t)p->d * dtype_size(p->dtype), &p->mu));
+    DM_TRY(ensure_arena(ctx, prepare_l2_scratch(p)));
+    return prepare_l2_run(ctx_exec(ctx), p, X, ldx);
 }
 
 void free_plan_buffers(dm_plan* p) {
@@ -356,15 +437,32 @@ void free_plan_buffers(dm_plan* p) {
 }
 
 // ------------------------------------------------------------------ query
-dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out, int64_t ldo) {
-    dm_ctx* ctx = p->ctx;
+// Query columns per reduce + apply round of the squared-l2 product (the
+// shared memory of the reduce bounds it; wider blocks run in column chunks).
+int64_t l2_chunk(const dm_plan* p, int64_t k) {
+    return std::min<int64_t>(k, reduce_max_k(p->dtype, p->d));
+}
+
+size_t matmat_scratch(const dm_plan* p, int64_t k) {
+    if (p->metric == DM_L1) return l1_query_scratch_bytes(p->dtype, p->n, p->d, k, p->ctx->num_sms);
+    k = std::max<int64_t>(1, l2_chunk(p, k));
+    ReduceArgs r{};
+    r.n = p->n; r.d = p->d; r.k = k;
+    r.num_sms = p->ctx->num_sms;
+    const size_t o_res = up16((size_t)reduce_blocks(r) * (p->d + 2) * k * 8);
+    return up16(o_res + (size_t)(p->d + 2) * k * 8);
+}
+
+dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out,
+                     int64_t ldo) {
+    dm_ctx* ctx = e.ctx;
     const dm_dtype t = p->dtype;
     const int64_t n = p->n, d = p->d;
+    if (e.scratch_bytes < matmat_scratch(p, k)) return DM_ERR_INTERNAL;
 
     if (p->metric == DM_L1) {
         // R^T Z, 1^T Z and the group-major copy of Z, then the sorted part
         // (Algorithm 2).
-        DM_TRY(ensure_arena(ctx, l1_query_scratch_bytes(t, n, d, k, ctx->num_sms)));
         L1QueryArgs q{};
         q.dtype = t;
         q.xs = p->xs; q.perm = p->perm; q.n = n; q.d = d;
@@ -373,57 +471,68 @@ dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* o
         q.mu_stride = n;
         q.Z = Z; q.k = k; q.ldz = ldz;
         q.out = out; q.ldo = ldo;
-        q.scratch = ctx->arena;
+        q.scratch = e.scratch;
         q.err = ctx->err;
         q.num_sms = ctx->num_sms;
         q.deterministic = ctx->deterministic;
         {
-            ProfScope ps(ctx, "l1_prologue");
-            DM_TRY_CUDA(l1_prologue_launch(q, ctx->stream, &ctx->launches));
+            ProfScope ps(e, "l1_prologue");
+            DM_TRY_CUDA(l1_prologue_launch(q, e.stream, &ctx->launches));
         }
         {
-            ProfScope ps(ctx, "l1_aggregate");
-            DM_TRY_CUDA(l1_aggregate_launch(q, ctx->stream, &ctx->launches));
+            ProfScope ps(e, "l1_aggregate");
+            DM_TRY_CUDA(l1_aggregate_launch(q, e.stream, &ctx->launches));
         }
         {
-            ProfScope ps(ctx, "l1_query");
-            DM_TRY_CUDA(l1_query_launch(q, ctx->stream, &ctx->launches));
+            ProfScope ps(e, "l1_query");
+            DM_TRY_CUDA(l1_query_launch(q, e.stream, &ctx->launches));
         }
         if (!q.deterministic) {
-            ProfScope ps(ctx, "l1_finalize");
-            DM_TRY_CUDA(l1_finalize_launch(q, ctx->stream, &ctx->launches));
+            ProfScope ps(e, "l1_finalize");
+            DM_TRY_CUDA(l1_finalize_launch(q, e.stream, &ctx->launches));
         }
         return DM_OK;
     }
 
-    if (!reduce_supported(d, k)) return DM_ERR_UNSUPPORTED;
-    ReduceArgs r{};
-    r.dtype = t;
-    r.n = n; r.d = d;
-    r.Z = Z; r.k = k; r.ldz = ldz;
-    r.num_sms = ctx->num_sms;
-    const int blocks = reduce_blocks(r);
-    const size_t o_res = up16((size_t)blocks * (d + 2) * k * 8);
-    DM_TRY(ensure_arena(ctx, up16(o_res + (size_t)(d + 2) * k * 8)));
-    unsigned char* base = static_cast<unsigned char*>(ctx->arena);
-    r.partial = base;
-    r.res = base + o_res;
-    r.X = p->X; r.ldx = p->ldx; r.x_acc = false;
-    r.mu = p->mu; r.mu_stride = 1;
-    r.with_s = true;
-    {
-        ProfScope ps(ctx, "l2_reduce");
-        DM_TRY_CUDA(reduce_launch(r, ctx->stream, &ctx->launches));
+    const int64_t kc = l2_chunk(p, k);
+    if (kc < 1) return DM_ERR_UNSUPPORTED;
+    for (int64_t j0 = 0; j0 < k; j0 += kc) {
+        const int64_t kk = std::min<int64_t>(kc, k - j0);
+        ReduceArgs r{};
+        r.dtype = t;
+        r.n = n; r.d = d;
+        r.Z = static_cast<const unsigned char*>(Z) + (size_t)j0 * dtype_size(t);
+        r.k = kk; r.ldz = ldz;
+        r.num_sms = ctx->num_sms;
+        const int blocks = reduce_blocks(r);
+        const size_t o_res = up16((size_t)blocks * (d + 2) * kk * 8);
+        unsigned char* base = e.scratch;
+        r.partial = base;
+        r.res = base + o_res;
+        r.X = p->X; r.ldx = p->ldx; r.x_acc = false;
+        r.mu = p->mu; r.mu_stride = 1;
+        r.with_s = true;
+        {
+            ProfScope ps(e, "l2_reduce");
+            DM_TRY_CUDA(reduce_launch(r, e.stream, &ctx->launches));
+        }
+        L2ApplyArgs ap{};
+        ap.dtype = t;
+        ap.X = p->X; ap.n = n; ap.d = d; ap.ldx = p->ldx;
+        ap.mu = p->mu; ap.res = r.res; ap.k = kk;
+        ap.out = static_cast<unsigned char*>(out) + (size_t)j0 * out_size(t);
+        ap.ldo = ldo;
+        ap.num_sms = ctx->num_sms;
+        ProfScope ps(e, "l2_apply");
+        DM_TRY_CUDA(l2apply_launch(ap, e.stream, &ctx->launches));
     }
-    L2ApplyArgs ap{};
-    ap.dtype = t;
-    ap.X = p->X; ap.n = n; ap.d = d; ap.ldx = p->ldx;
-    ap.mu = p->mu; ap.res = r.res; ap.k = k;
-    ap.out = out; ap.ldo = ldo;
-    ap.num_sms = ctx->num_sms;
-    ProfScope ps(ctx, "l2_apply");
-    DM_TRY_CUDA(l2apply_launch(ap, ctx->stream, &ctx->launches));
     return DM_OK;
+}
+
+dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out, int64_t ldo) {
+    if (p->metric == DM_L2SQ && l2_chunk(p, k) < 1) return DM_ERR_UNSUPPORTED;
+    DM_TRY(ensure_arena(p->ctx, matmat_scratch(p, k)));
+    return matmat_run(ctx_exec(p->ctx), p, Z, k, ldz, out, ldo);
 }
 
 // --------------------------------------------------------------- gradient
@@ -464,7 +573,7 @@ dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64
         return DM_OK;
     }
     // squared l2: [X - mu, 1]^T [z_q, w_q] by the reduce kernel, then the closed form
-    if (!reduce_supported(d, 2 * k)) return DM_ERR_UNSUPPORTED;
+    if (reduce_max_k(t, d) < 2 * k) return DM_ERR_UNSUPPORTED;
     ReduceArgs r{};
     r.dtype = t;
     r.n = n; r.d = d;
@@ -493,6 +602,182 @@ dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64
     ProfScope ps(ctx, "grad_l2_apply");
     DM_TRY_CUDA(grad_l2_apply_launch(a, ctx->stream, &ctx->launches));
     return DM_OK;
+}
+
+// ------------------------------------------------------------------ batch
+// Tear down the lanes and the graph (the plans stay).
+void batch_release_graph(dm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    for (auto st : b->streams) cudaStreamDestroy(st);
+    for (auto p : b->scratch) cudaFree(p);
+    for (auto ev : b->joins) cudaEventDestroy(ev);
+    b->streams.clear();
+    b->scratch.clear();
+    b->scratch_bytes.clear();
+    b->joins.clear();
+    b->lanes = 0;
+}
+
+// Spread the sets over L lanes (largest first, each to the least loaded
+// lane), give every lane a scratch buffer for its largest set, and capture
+// prepare + product of every set into one graph: the lanes fork from the
+// origin stream and join back into it.
+dm_status batch_build(dm_batch* b, int L) {
+    dm_ctx* ctx = b->ctx;
+    batch_release_graph(b);
+    std::vector<size_t> order(b->sets.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return b->sets[x].cost > b->sets[y].cost; });
+    std::vector<double> load((size_t)L, 0.0);
+    std::vector<size_t> need((size_t)L, 16);
+    for (size_t i : order) {
+        auto& st = b->sets[i];
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        st.lane = l;
+        load[(size_t)l] += st.cost;
+        dm_plan* p = st.plan;
+        const size_t prep = p->metric == DM_L1 ? sort_layout(p->dtype, p->n, p->d).total : prepare_l2_scratch(p);
+        need[(size_t)l] = std::max(need[(size_t)l], std::max(prep, matmat_scratch(p, st.k)));
+    }
+    for (int l = 0; l < L; ++l) {
+        cudaStream_t st = nullptr;
+        void* buf = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (st) cudaStreamDestroy(st);
+            batch_release_graph(b);
+            return DM_ERR_CUDA;
+        }
+        b->streams.push_back(st);
+        b->joins.push_back(ev);
+        if (cudaMalloc(&buf, need[(size_t)l]) != cudaSuccess) {
+            cudaGetLastError();
+            batch_release_graph(b);
+            return DM_ERR_OOM;
+        }
+        b->scratch.push_back(buf);
+        b->scratch_bytes.push_back(need[(size_t)l]);
+    }
+    b->lanes = L;
+
+    const int64_t launches0 = ctx->launches;
+    DM_TRY_CUDA(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
+    dm_status s = from_cuda(cudaEventRecord(b->fork, b->origin));
+    for (int l = 0; l < L && s == DM_OK; ++l) s = from_cuda(cudaStreamWaitEvent(b->streams[(size_t)l], b->fork, 0));
+    for (size_t i = 0; i < b->sets.size() && s == DM_OK; ++i) {
+        auto& st = b->sets[i];
+        const Exec e{ctx, b->streams[(size_t)st.lane], static_cast<unsigned char*>(b->scratch[(size_t)st.lane]),
+                     b->scratch_bytes[(size_t)st.lane], true};
+        s = st.plan->metric == DM_L1 ? prepare_l1_run(e, st.plan, st.X, st.ldx)
+                                     : prepare_l2_run(e, st.plan, st.X, st.ldx);
+        if (s == DM_OK) s = matmat_run(e, st.plan, st.Z, st.k, st.ldz, st.out, st.ldo);
+    }
+    for (int l = 0; l < L && s == DM_OK; ++l) {
+        s = from_cuda(cudaEventRecord(b->joins[(size_t)l], b->streams[(size_t)l]));
+        if (s == DM_OK) s = from_cuda(cudaStreamWaitEvent(b->origin, b->joins[(size_t)l], 0));
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->origin, &g);
+    if (s == DM_OK) s = from_cuda(ee);
+    if (s != DM_OK) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        batch_release_graph(b);
+        return s;
+    }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        batch_release_graph(b);
+        return DM_ERR_CUDA;
+    }
+    b->launches_per_run = ctx->launches - launches0;
+    ctx->launches = launches0;
+    return DM_OK;
+}
+
+dm_status batch_launch(dm_batch* b) {
+    dm_ctx* ctx = b->ctx;
+    DM_TRY_CUDA(cudaEventRecord(b->done, ctx->stream));
+    DM_TRY_CUDA(cudaStreamWaitEvent(b->origin, b->done, 0));
+    DM_TRY_CUDA(cudaGraphLaunch(b->exec, b->origin));
+    DM_TRY_CUDA(cudaEventRecord(b->done, b->origin));
+    DM_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, b->done, 0));
+    ctx->launches += b->launches_per_run;
+    return DM_OK;
+}
+
+// Lane counts tried by the autotuner and the choices it made, by shape.
+std::map<std::string, int>& lane_cache() {
+    static std::map<std::string, int> m;
+    return m;
+}
+
+std::string batch_key(const dm_batch* b) {
+    double sn = 0, snd = 0, snk = 0;
+    int64_t mx = 0;
+    for (auto& st : b->sets) {
+        sn += (double)st.plan->n;
+        snd += (double)st.plan->n * (double)st.plan->d;
+        snk += (double)st.plan->n * (double)st.k;
+        mx = std::max(mx, st.plan->n * st.plan->d);
+    }
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%d/%d/%d/%.0f/%.0f/%.0f/%lld/%d", (int)b->metric, (int)b->dtype,
+             (int)b->sets.size(), sn, snd, snk, (long long)mx, b->ctx->deterministic);
+    return buf;
+}
+
+// Time each candidate lane count on the batch (one warm-up and three timed
+// replays of its graph) and keep the fastest.
+dm_status batch_autotune(dm_batch* b) {
+    const std::string key = batch_key(b);
+    auto it = lane_cache().find(key);
+    if (it != lane_cache().end()) return batch_build(b, it->second);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    DM_TRY_CUDA(cudaEventCreate(&t0));
+    if (cudaEventCreate(&t1) != cudaSuccess) { cudaEventDestroy(t0); return DM_ERR_CUDA; }
+    int best = 1;
+    float best_ms = -1.0f;
+    dm_status s = DM_OK;
+    for (int L : {1, 2, 4, 8, 16}) {
+        if (L > (int)b->sets.size() && L > 1) break;
+        s = batch_build(b, L);
+        if (s != DM_OK) break;
+        s = batch_launch(b);
+        if (s == DM_OK) s = from_cuda(cudaEventRecord(t0, b->ctx->stream));
+        for (int r = 0; r < 3 && s == DM_OK; ++r) s = batch_launch(b);
+        if (s == DM_OK) s = from_cuda(cudaEventRecord(t1, b->ctx->stream));
+        if (s == DM_OK) s = from_cuda(cudaEventSynchronize(t1));
+        float ms = 0;
+        if (s == DM_OK) s = from_cuda(cudaEventElapsedTime(&ms, t0, t1));
+        if (s != DM_OK) break;
+        if (best_ms < 0 || ms < best_ms) { best_ms = ms; best = L; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (s != DM_OK) return s;
+    lane_cache()[key] = best;
+    return batch_build(b, best);
+}
+
+void batch_free(dm_batch* b) {
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
+    batch_release_graph(b);
+    for (auto& st : b->sets) {
+        if (st.plan) { free_plan_buffers(st.plan); delete st.plan; }
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
 }
 
 }  // namespace
@@ -646,6 +931,70 @@ dm_status dm_grad(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64_t
         return DM_ERR_INVALID_ARG;
     DeviceGuard g(p->ctx->device);
     return grad_impl(p, W, ldw, Z, ldz, k, G, ldg);
+}
+
+dm_status dm_batch_create(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, int64_t nsets,
+                          const int64_t* n, const int64_t* d, const void* const* X,
+                          const int64_t* ldx, const int64_t* k, const void* const* Z,
+                          const int64_t* ldz, void* const* out, const int64_t* ldo, int lanes,
+                          dm_batch** batch) {
+    if (!batch) return DM_ERR_INVALID_ARG;
+    *batch = nullptr;
+    if (!ctx || !valid_metric(metric) || !valid_dtype(dtype) || nsets < 1 || lanes < 0 || lanes > 64 ||
+        !n || !d || !X || !ldx || !k || !Z || !ldz || !out || !ldo)
+        return DM_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < nsets; ++i) {
+        if (!X[i] || !Z[i] || !out[i] || n[i] < 1 || n[i] > kMaxN || d[i] < 1 || ldx[i] < d[i] ||
+            k[i] < 1 || ldz[i] < k[i] || ldo[i] < k[i])
+            return DM_ERR_INVALID_ARG;
+        if ((double)n[i] * (double)d[i] >= 2147483648.0) return DM_ERR_UNSUPPORTED;
+        if (metric == DM_L2SQ && reduce_max_k(dtype, d[i]) < 1) return DM_ERR_UNSUPPORTED;
+    }
+    DeviceGuard g(ctx->device);
+    dm_batch* b = new (std::nothrow) dm_batch();
+    if (!b) return DM_ERR_OOM;
+    b->ctx = ctx;
+    b->metric = metric;
+    b->dtype = dtype;
+    dm_status s = DM_OK;
+    if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        s = DM_ERR_CUDA;
+    }
+    for (int64_t i = 0; i < nsets && s == DM_OK; ++i) {
+        dm_plan* p = new (std::nothrow) dm_plan();
+        if (!p) { s = DM_ERR_OOM; break; }
+        p->ctx = ctx; p->metric = metric; p->dtype = dtype; p->n = n[i]; p->d = d[i];
+        const double es = (double)dtype_size(dtype);
+        const double cost = metric == DM_L1 ? (double)n[i] * d[i] * (8.0 + 8.0 * k[i] + 64.0)
+                                            : (double)n[i] * (2.0 * d[i] * es + 2.0 * k[i] * es);
+        b->sets.push_back({p, X[i], ldx[i], Z[i], k[i], ldz[i], out[i], ldo[i], cost, 0});
+        s = metric == DM_L1 ? alloc_l1_plan(p) : plan_alloc(p, (size_t)d[i] * dtype_size(dtype), &p->mu);
+        if (metric == DM_L2SQ) { p->X = X[i]; p->ldx = ldx[i]; }
+    }
+    if (s == DM_OK) s = lanes > 0 ? batch_build(b, (int)std::min<int64_t>(lanes, nsets)) : batch_autotune(b);
+    if (s != DM_OK) {
+        batch_free(b);
+        return s;
+    }
+    *batch = b;
+    return DM_OK;
+}
+
+dm_status dm_batch_run(dm_batch* b) {
+    if (!b || !b->exec) return DM_ERR_INVALID_ARG;
+    DeviceGuard g(b->ctx->device);
+    return batch_launch(b);
+}
+
+int dm_batch_lanes(const dm_batch* b) { return b ? b->lanes : 0; }
+
+void dm_batch_destroy(dm_batch* b) {
+    if (!b) return;
+    DeviceGuard g(b->ctx->device);
+    batch_free(b);
 }
 
 dm_status dm_matvec_l1(dm_plan* p, const void* z, void* out) {

@@ -100,7 +100,8 @@ struct ReduceArgs {
     int num_sms;
     int max_blocks;                      // 0: no cap beyond the default
 };
-bool reduce_supported(int64_t d, int64_t k);
+bool reduce_supported(int64_t d, int64_t k);   // any element type (FP64 worst case)
+int64_t reduce_max_k(dm_dtype t, int64_t d);   // columns per launch for this type
 int reduce_blocks(const ReduceArgs& a);
 cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s, int64_t* launches);
 

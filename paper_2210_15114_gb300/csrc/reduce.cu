@@ -651,6 +651,27 @@ cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* lau
 
 }  // namespace
 
+// Largest number of query columns one reduce launch takes for d coordinates
+// of element type t (0 when even one column does not fit): the launch's
+// output blocks and its shared memory (the kernel's own layout) bound it.
+int64_t reduce_max_k(dm_dtype t, int64_t d) {
+    if (d < 1 || d > 4096) return 0;
+    int64_t best = 0;
+    for (int64_t k = 1; k <= 4096; ++k) {
+        const int64_t OB = ((d + 2 + RC - 1) / RC) * ((k + RJ - 1) / RJ);
+        if (OB > 4 * kThreads) break;
+        size_t smem = 0;
+        switch (t) {
+            case DM_F32: smem = reduce_smem<DM_F32, float>((int)d, (int)k); break;
+            case DM_F64: smem = reduce_smem<DM_F64, double>((int)d, (int)k); break;
+            default: smem = reduce_smem<DM_I32, int32_t>((int)d, (int)k); break;
+        }
+        if (smem > 220 * 1024) break;
+        best = k;
+    }
+    return best;
+}
+
 bool reduce_supported(int64_t d, int64_t k) {
     const int64_t OB = ((d + 2 + RC - 1) / RC) * ((k + RJ - 1) / RJ);
     if (OB > 4 * kThreads || d > 4096 || k > 4096) return false;

@@ -128,3 +128,27 @@ def workload_krylov(n: int = 1 << 22, d: int = 16, k: int = 40, clusters: int = 
     X = gaussian_mixture(n, d, clusters, SEED_X, 10.0, 1.0, dtype=np.float32)
     Pi = gaussian_queries(n, k, SEED_PI, dtype=np.float32)
     return X, Pi
+
+
+def workload_batch(nsets: int = 512, n_lo: int = 1024, n_hi: int = 262144, d_lo: int = 2,
+                   d_hi: int = 64, k_lo: int = 1, k_hi: int = 32, seed0: int = 1000,
+                   dtype=np.float32):
+    """Independent point sets of uneven size: set s draws from seed seed0 + s
+    its n (log-uniform in [n_lo, n_hi], rounded), d (uniform in
+    {d_lo..d_hi}), k (uniform in {k_lo..k_hi}), coordinates uniform in
+    [-1, 1) and queries N(0, 1).  Integer dtype: coordinates uniform in
+    [0, 2^16), queries in [-100, 100].  Returns a list of (X, Z)."""
+    out = []
+    for s in range(nsets):
+        rng = np.random.default_rng(seed0 + s)
+        n = int(round(float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))))
+        d = int(rng.integers(d_lo, d_hi + 1))
+        k = int(rng.integers(k_lo, k_hi + 1))
+        if np.issubdtype(np.dtype(dtype), np.integer):
+            X = rng.integers(0, 1 << 16, size=(n, d)).astype(dtype)
+            Z = rng.integers(-100, 101, size=(n, k)).astype(dtype)
+        else:
+            X = rng.uniform(-1.0, 1.0, size=(n, d)).astype(dtype)
+            Z = rng.normal(0.0, 1.0, size=(n, k)).astype(dtype)
+        out.append((X, Z))
+    return out

@@ -346,3 +346,16 @@ def test_full_size_symmetry(dm, ctx, metric, full_fp32):
     G = Zd.double().T @ out                       # G[a,b] = z_a^T A z_b
     asym = (G - G.T).abs().max().item()
     assert asym <= 1e-5 * G.abs().max().item()
+
+
+@pytest.mark.parametrize("dtype,d,k", [(np.float32, 64, 100), (np.float64, 40, 70), (np.int32, 64, 33)])
+def test_l2sq_wide_blocks_in_column_chunks(dm, ctx, dtype, d, k):
+    # wider blocks than one reduce launch takes run in column chunks
+    rng = np.random.default_rng(d + k)
+    if dtype == np.int32:
+        X = rng.integers(0, 1 << 16, size=(3000, d)).astype(dtype)
+        Z = rng.integers(-100, 101, size=(3000, k)).astype(dtype)
+    else:
+        X = rng.normal(0, 4, size=(3000, d)).astype(dtype)
+        Z = rng.normal(size=(3000, k)).astype(dtype)
+    check(gpu_product(dm, ctx, "l2sq", X, Z), reference("l2sq", X, Z), dtype)
