@@ -61,6 +61,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--no-krylov", action="store_true", help="skip the block Krylov measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch measurement")
     ap.add_argument("--grad-n", type=int, default=1 << 21)
     ap.add_argument("--grad-d", type=int, default=64)
     ap.add_argument("--profile-only", action="store_true",
@@ -445,6 +446,56 @@ def measure_krylov(dm, ctx, stream, dev, n=1 << 22, d=16, k=40, q=8, rank=32, re
     return res
 
 
+def measure_batch(dm, ctx, stream, dev, reps=5):
+    """512 point sets (n log-uniform in [1024, 262144], d in 2..64, k in
+    1..32, FP32 uniform [-1, 1), Z N(0, 1)): prepare + product of every set
+    per graph run, lanes chosen by the library's autotuner; the same sets as
+    one dm_prepare + dm_matmat call each, for comparison."""
+    import torch
+    from paper_2210_15114_gb300 import inputs
+    sets = inputs.workload_batch()
+    Xs = [torch.from_numpy(X).to(dev) for X, _ in sets]
+    Zs = [torch.from_numpy(Z).to(dev) for _, Z in sets]
+    units = sum(X.shape[0] * X.shape[1] * Z.shape[1] for X, Z in sets)
+    res = {"workload": "512 sets, n log-uniform [1024, 262144], d 2..64, k 1..32, fp32 U[-1,1), Z N(0,1)",
+           "sum_n": sum(X.shape[0] for X, _ in sets), "sum_ndk": units,
+           "units": "point*query*dim per second (sum over sets of n d k per run)"}
+    for metric in ("l1", "l2sq"):
+        t0 = time.perf_counter()
+        b = dm.dm_batch_create(ctx, metric, Xs, Zs, lanes=0)
+        torch.cuda.synchronize(dev)
+        create_s = time.perf_counter() - t0
+        dm.dm_batch_run(b)
+        torch.cuda.synchronize(dev)
+        l0 = dm.dm_launch_count(ctx)
+        ev = []
+        for _ in range(reps):
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            dm.dm_batch_run(b)
+            e_.record(stream)
+            ev.append((s_, e_))
+        torch.cuda.synchronize(dev)
+        launches = (dm.dm_launch_count(ctx) - l0) // reps
+        ms = statistics.mean(s_.elapsed_time(e_) for s_, e_ in ev)
+        dm.dm_sync(ctx)
+        lanes = dm.dm_batch_lanes(b)
+        dm.dm_batch_destroy(b)
+        # one call per set, no graph (dm_prepare for l1 synchronizes once per set)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for Xd, Zd in zip(Xs, Zs):
+            plan = dm.dm_prepare(ctx, metric, Xd)
+            dm.dm_matmat(plan, Zd)
+            del plan
+        torch.cuda.synchronize(dev)
+        single_ms = (time.perf_counter() - t0) * 1e3
+        res[metric] = {"ms_per_run": ms, "value": units / (ms * 1e-3), "lanes": lanes,
+                       "gpu_launches_per_run": launches, "create_and_autotune_s": create_s,
+                       "one_call_per_set_ms_wall": single_ms}
+    return res
+
+
 # ------------------------------------------------------------- reference arm
 def run_reference(a):
     rank, world, _ = dist_env()
@@ -595,6 +646,11 @@ def main():
     if not a.no_krylov:
         krylov = measure_krylov(dm, ctx, stream, dev)
 
+    # ---- 512 independent point sets replayed from one graph
+    batch = None
+    if not a.no_batch:
+        batch = measure_batch(dm, ctx, stream, dev)
+
     # ---- brute force (the plain method) and accuracy
     brute = None
     if not a.no_brute:
@@ -656,7 +712,7 @@ def main():
             "gpu_launches": launches, "launches_per_step": launches / a.steps,
             "wall_s_timed_region": t_wall,
             "parts_ms": parts, "kernels": kernels, "roofline": roofline, "l1_query_all_kernels": l1_query_all,
-            "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad, "krylov": krylov,
+            "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad, "krylov": krylov, "batch": batch,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:

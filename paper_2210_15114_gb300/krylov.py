@@ -11,10 +11,15 @@ cuSOLVER); they never touch A.
 
 For symmetric A the Krylov space of the iteration is spanned by powers of A:
 Q_1 = orth(A Pi); W = A Q_i; Q_{i+1} = orth(W minus its projections on
-Q_1..Q_i) with the projections removed twice before and twice after a QR
-(a low-rank A makes late blocks rounding noise, whose normalized directions
-must be projected out again).  The Rayleigh-Ritz matrix M = Q^T (A Q) reuses
-the products A Q_i.  Its eigenpairs (theta, V) of largest |theta| give the
+Q_1..Q_i), the projections removed twice before and twice after an
+orthonormalization (a low-rank A makes late blocks rounding noise, whose
+normalized directions must be projected out again; one pass each leaves
+the basis far from orthonormal in FP32).  Orthonormalization is
+Cholesky QR applied twice (Gram matrix W^T W, its Cholesky factor R in
+FP64, W R^-1): two skinny matrix products instead of a Householder QR of a
+tall block, with Householder QR as the fallback when the block is
+numerically rank deficient.  The Rayleigh-Ritz matrix M = Q^T (A Q) reuses the
+products A Q_i.  Its eigenpairs (theta, V) of largest |theta| give the
 singular values |theta| and A ~ U diag(theta) U^T with U = Q V.
 """
 from __future__ import annotations
@@ -44,7 +49,7 @@ def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
             if i:
                 for _ in range(2):
                     W = W - prev @ (prev.T @ W)
-            W = torch.linalg.qr(W).Q
+            W = _orthonormalize(W)
         Q[:, i * k:(i + 1) * k] = W
         binding.dm_matmat(plan, Q[:, i * k:(i + 1) * k], out=AQ[:, i * k:(i + 1) * k])
         W = AQ[:, i * k:(i + 1) * k].clone()
@@ -54,3 +59,23 @@ def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
     order = torch.argsort(theta.abs(), descending=True)[:rank]
     U = Q @ V[:, order].to(dt)
     return theta[order], U
+
+
+def _orthonormalize(W: torch.Tensor) -> torch.Tensor:
+    """Orthonormal basis of the columns of a tall block W (n x k): Cholesky
+    QR twice, or Householder QR when W is (numerically) rank deficient -- a
+    Gram matrix that is not positive definite, or a Cholesky diagonal spread
+    beyond 1e3, past which a Gram matrix formed in the block's precision no
+    longer resolves the smallest direction."""
+    Q = W
+    for _ in range(2):
+        G = (Q.T @ Q).double()
+        R, info = torch.linalg.cholesky_ex(G, upper=True)
+        dg = torch.diagonal(R).abs()
+        if int(info.item()) != 0 or float(dg.min()) < 1e-3 * float(dg.max()):
+            return torch.linalg.qr(W).Q
+        Rinv = torch.linalg.solve_triangular(R, torch.eye(R.shape[0], dtype=R.dtype, device=R.device),
+                                             upper=True)
+        Q = Q @ Rinv.to(Q.dtype)
+    return Q
+
