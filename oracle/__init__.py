@@ -23,6 +23,10 @@ Three forms, all plain and slow on purpose:
 * ``block_krylov`` -- the randomized block Krylov iteration that the
   paper's application section uses (through products A Z only) for the top
   singular values and a low-rank approximation.
+* ``tv_rows``, ``lpp_rows`` / ``lpp_even_expansion``, ``l2_embed`` /
+  ``l2_approx`` -- the variants of Appendix A: total variation (half the l1
+  product), ||x - y||_p^p by definition and by the even-p expansion, and the
+  approximate l2 product through the Gaussian l2 -> l1 embedding.
 * ``l2sq_identity`` -- the p = 2 query of Appendix A (Theorem
   "l2_squared_upper_bound"), with the typos of the printed algorithm read as
   the proof's Gram decomposition (Section 1.2): (Ay)_k = ||x_k||^2 sum_j y_j
@@ -331,6 +335,86 @@ def block_krylov(product, Pi, q: int, rank: int):
     theta, V = np.linalg.eigh(M)
     order = np.argsort(-np.abs(theta))[:rank]
     return theta[order], Q @ V[:, order]
+
+
+def tv_rows(X, Z, rows=None) -> np.ndarray:
+    """Total variation distance of distributions x_i over d outcomes
+    (Appendix A, "Distances for Distributions", Theorem "tv"):
+    TV(x, y) = (1/2) ||x - y||_1, so the product is half the l1 product."""
+    return 0.5 * l1_rows(X, Z, rows)
+
+
+def lpp_rows(X, Z, p: int, rows=None) -> np.ndarray:
+    """Definition of the product for f(x, y) = ||x - y||_p^p (Appendix A,
+    "General p"), any integer p >= 1: a direct double loop in numpy, FP64
+    (int64 for integer inputs, exact when the result fits)."""
+    X = np.asarray(X)
+    Z = np.asarray(Z)
+    if X.ndim == 1:
+        X = X[:, None]
+    squeeze = Z.ndim == 1
+    if squeeze:
+        Z = Z[:, None]
+    integer = _is_int(X) and _is_int(Z)
+    dt = np.int64 if integer else np.float64
+    X = X.astype(dt)
+    Z = Z.astype(dt)
+    if rows is None:
+        rows = np.arange(len(X))
+    out = np.zeros((len(rows), Z.shape[1]), dtype=dt)
+    for r, i in enumerate(np.asarray(rows)):
+        diff = np.abs(X[i][None, :] - X)
+        dist = (diff ** p).sum(axis=1)
+        out[r] = dist @ Z
+    return out[:, 0] if squeeze else out
+
+
+def lpp_even_expansion(X, Z, p: int) -> np.ndarray:
+    """The query for even p of Appendix A in its corrected reading: with
+    S_{i,t} = C(p, t) sum_j y_j (-x_j(i))^(p-t) for t = 0..p,
+    (Ay)(k) = sum_i sum_t x_k(i)^t S_{i,t}.  (The printed algorithm omits
+    y_j and the binomial coefficients and starts t at 1.)  FP64 / int64."""
+    if p % 2:
+        raise ValueError("p must be even")
+    X = np.asarray(X)
+    Z = np.asarray(Z)
+    if X.ndim == 1:
+        X = X[:, None]
+    squeeze = Z.ndim == 1
+    if squeeze:
+        Z = Z[:, None]
+    integer = _is_int(X) and _is_int(Z)
+    dt = np.int64 if integer else np.float64
+    X = X.astype(dt)
+    Z = Z.astype(dt)
+    out = np.zeros((len(X), Z.shape[1]), dtype=dt)
+    from math import comb
+    for i in range(X.shape[1]):
+        x = X[:, i]
+        for t in range(p + 1):
+            S = comb(p, t) * (((-x) ** (p - t))[None, :] @ Z)      # 1 x k
+            out += (x ** t)[:, None] * S
+    return out[:, 0] if squeeze else out
+
+
+L2_EMBED_BETA = float(np.sqrt(2.0 / np.pi))
+
+
+def l2_embed(X, G) -> np.ndarray:
+    """The linear map of Theorem "l2embed": T(x)_i = (1/(beta m)) sum_j
+    G_ij x_j with beta = sqrt(2/pi) and G an m x d matrix of N(0, 1)
+    entries, applied to every point (rows of X); FP64."""
+    X = np.asarray(X, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    return X @ G.T / (L2_EMBED_BETA * G.shape[0])
+
+
+def l2_approx(X, G, Z) -> np.ndarray:
+    """Approximate l2 product of Appendix A ("Approximate Matrix-Vector Query
+    for l2"): the l1 product (Algorithms 1 and 2) of the embedded points."""
+    return l1_sort(l2_embed(X, G), Z)
 
 
 def relative_error(got, want) -> float:

@@ -152,3 +152,17 @@ def workload_batch(nsets: int = 512, n_lo: int = 1024, n_hi: int = 262144, d_lo:
             Z = rng.normal(0.0, 1.0, size=(n, k)).astype(dtype)
         out.append((X, Z))
     return out
+
+
+SEED_G = 4     # the Gaussian matrix of the l2 -> l1 embedding
+
+
+def embedding_matrix(m: int, d: int, dtype=np.float32) -> np.ndarray:
+    """The m x d N(0, 1) matrix G of the l2 -> l1 embedding (seed 4)."""
+    return np.random.default_rng(SEED_G).normal(0.0, 1.0, size=(m, d)).astype(dtype)
+
+
+def simplex_points(n: int, d: int, seed: int = SEED_X, dtype=np.float32) -> np.ndarray:
+    """Discrete distributions over d outcomes (Dirichlet(1, ..., 1) rows),
+    the inputs of the total-variation product."""
+    return np.random.default_rng(seed).dirichlet(np.ones(d), size=n).astype(dtype)
