@@ -53,7 +53,12 @@ typedef enum {
 } dm_status;
 
 typedef enum { DM_F32 = 0, DM_F64 = 1, DM_I32 = 2 } dm_dtype;
-typedef enum { DM_L1 = 0, DM_L2SQ = 1 } dm_metric;
+/* DM_L1: ||x - y||_1 (Section 2).  DM_L2SQ: ||x - y||_2^2 (Appendix A).
+ * DM_TV: total variation of distributions, ||x - y||_1 / 2 (Appendix A,
+ * Theorem "tv"; FP32/FP64 only).  DM_LPP: ||x - y||_p^p for an even p
+ * (Appendix A, "General p"; plans from dm_prepare_lpp).  DM_L2_EMBED: the
+ * approximate ||x - y||_2 of Appendix A (plans from dm_prepare_l2_embed). */
+typedef enum { DM_L1 = 0, DM_L2SQ = 1, DM_TV = 2, DM_LPP = 3, DM_L2_EMBED = 4 } dm_metric;
 
 typedef struct dm_ctx dm_ctx;     /* opaque: device, stream, scratch, error word */
 typedef struct dm_plan dm_plan;   /* opaque: one preprocessed point set          */
@@ -97,6 +102,31 @@ dm_status dm_set_deterministic(dm_ctx* ctx, int on);
  * non-finite coordinates through dm_sync. */
 dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* X,
                      int64_t n, int64_t d, int64_t ldx, dm_plan** plan);
+/* (dm_prepare takes DM_L1, DM_L2SQ and DM_TV; DM_TV plans are l1 plans whose
+ * products and gradients are halved.) */
+
+/* ||x - y||_p^p plan for an even p, 2 <= p <= 16 (Appendix A, "General p";
+ * the printed query is read with the binomial coefficients C(p, t) and the
+ * weights y_j, t = 0..p): the plan records X (kept alive by the caller, as
+ * for DM_L2SQ) and its column means; dm_matmat forms the moments
+ * sum_j y_j (x_j(c) - mu_c)^s, s = 0..p, and evaluates
+ * (Ay)_k = sum_c sum_t C(p,t) (-1)^(p-t) (x_k(c) - mu_c)^t M_{c,p-t}.
+ * Exact for DM_I32 when the result fits in int64 (wrap-around arithmetic);
+ * FP32 results lose accuracy as p grows (the expansion cancels).
+ * DM_ERR_UNSUPPORTED when d * p exceeds what one reduce launch holds. */
+dm_status dm_prepare_lpp(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, int64_t d,
+                         int64_t ldx, int p, dm_plan** plan);
+
+/* Approximate ||x - y||_2 plan (Appendix A, "Approximate Matrix-Vector
+ * Query for l2"): the points are mapped by T(x) = G x / (beta m) with
+ * beta = sqrt(2/pi) (Theorem "l2embed") and the plan is the l1 plan of the
+ * mapped points, so A Z is approximated by B Z with B_ij = ||T x_i - T x_j||_1.
+ * G: m x d row-major device matrix (caller-drawn N(0, 1) entries, element
+ * type of the plan; only read during this call).  FP32/FP64 only;
+ * DM_ERR_UNSUPPORTED when G does not fit in shared memory (m * (d + 1)
+ * elements beyond about 200 KB). */
+dm_status dm_prepare_l2_embed(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, int64_t d,
+                              int64_t ldx, const void* G, int64_t m, dm_plan** plan);
 
 /* Release a plan.  Its device buffers go back to the context, which reuses
  * them for later plans in stream order (no wait; buffers beyond 8 GiB per
@@ -123,7 +153,8 @@ dm_status dm_matmat(dm_plan* plan, const void* Z, int64_t k, int64_t ldz,
  * applied to the definition of A):
  *     G[i, c] = sum_q sum_j (W[i,q] Z[j,q] + Z[i,q] W[j,q]) phi'(x_i(c) - x_j(c)),
  * phi'(t) = sgn(t) for DM_L1, with sgn(0) = 0 (tied coordinates contribute
- * nothing: the symmetric subgradient), and phi'(t) = 2t for DM_L2SQ.
+ * nothing: the symmetric subgradient), phi'(t) = sgn(t) / 2 for DM_TV and
+ * phi'(t) = 2t for DM_L2SQ (DM_LPP and DM_L2_EMBED: DM_ERR_UNSUPPORTED).
  *   W, Z: n x k (leading dimensions ldw, ldz >= k), 1 <= k <= 64, element type
  *         of the plan (int32 for DM_I32 plans);
  *   G:    n x d result (ldg >= d), element type of the plan's results (FP32,
@@ -210,7 +241,8 @@ int64_t dm_launch_count(const dm_ctx* ctx);
  * ("sort_keygen_hist", "sort_onesweep", "l1_rowsum", "l1_prologue",
  * "l1_aggregate", "l1_query", "l1_finalize", "l2_prepare", "l2_reduce",
  * "l2_apply", "bruteforce", "grad_pack", "grad_l1_tiles", "grad_l1_scan",
- * "grad_l1_eval", "grad_l1_transpose", "grad_l2_reduce", "grad_l2_apply") is
+ * "grad_l1_eval", "grad_l1_transpose", "grad_l2_reduce", "grad_l2_apply",
+ * "tv_scale", "lpp_features", "lpp_reduce", "lpp_apply", "l2_embed_project") is
  * bracketed by two CUDA events
  * recorded on the context's stream.  Enabling (or disabling) clears what was
  * collected.  Off by default; costs two event records per group. */

@@ -28,7 +28,8 @@ DM_ERR_INTERNAL = 7
 DM_F32, DM_F64, DM_I32 = 0, 1, 2
 DM_L1, DM_L2SQ = 0, 1
 
-METRICS = {"l1": DM_L1, "l2sq": DM_L2SQ}
+METRICS = {"l1": DM_L1, "l2sq": DM_L2SQ, "tv": 2}
+DM_LPP, DM_L2_EMBED = 3, 4
 
 _lock = threading.Lock()
 _lib = None
@@ -69,6 +70,8 @@ def load() -> ctypes.CDLL:
             "dm_matvec_l2sq": ([P, P, P], I32),
             "dm_matmat": ([P, P, I64, I64, P, I64], I32),
             "dm_grad": ([P, P, I64, P, I64, I64, P, I64], I32),
+            "dm_prepare_lpp": ([P, I32, P, I64, I64, I64, I32, P], I32),
+            "dm_prepare_l2_embed": ([P, I32, P, I64, I64, I64, P, I64, P], I32),
             "dm_batch_create": ([P, I32, I32, I64, P, P, P, P, P, P, P, P, P, I32, P], I32),
             "dm_batch_run": ([P], I32),
             "dm_batch_lanes": ([P], I32),
@@ -209,6 +212,38 @@ def dm_prepare(ctx: Context, metric, X) -> Plan:
     plan = Plan(h.value, ctx, m, code, n, d)
     plan.X = X if m == DM_L2SQ else None   # the squared-l2 plan borrows X
     return plan
+
+
+def dm_prepare_lpp(ctx: Context, X, p: int) -> Plan:
+    """dm_prepare_lpp: ||x - y||_p^p plan (even p) on a CUDA tensor X (n x d)."""
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    code = dtype_code(X.dtype)
+    n, d = X.shape
+    h = ctypes.c_void_p()
+    _check(load().dm_prepare_lpp(ctx.handle, code, ctypes.c_void_p(_dev_ptr(X)), n, d, _ld(X), int(p),
+                                 ctypes.byref(h)), "dm_prepare_lpp")
+    plan = Plan(h.value, ctx, DM_LPP, code, n, d)
+    plan.X = X
+    return plan
+
+
+def dm_prepare_l2_embed(ctx: Context, X, G) -> Plan:
+    """dm_prepare_l2_embed: approximate l2 plan through the map
+    T(x) = G x / (beta m), G an m x d CUDA tensor of N(0, 1) entries."""
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    code = dtype_code(X.dtype)
+    if dtype_code(G.dtype) != code or G.ndim != 2 or G.shape[1] != X.shape[1]:
+        raise DMError(DM_ERR_INVALID_ARG, "G must be m x d with the points' element type")
+    G = G.contiguous()
+    n, d = X.shape
+    m = G.shape[0]
+    h = ctypes.c_void_p()
+    _check(load().dm_prepare_l2_embed(ctx.handle, code, ctypes.c_void_p(_dev_ptr(X)), n, d, _ld(X),
+                                      ctypes.c_void_p(_dev_ptr(G)), m, ctypes.byref(h)),
+           "dm_prepare_l2_embed")
+    return Plan(h.value, ctx, DM_L2_EMBED, code, n, m)
 
 
 def dm_plan_destroy(plan: Plan) -> None:

@@ -53,10 +53,12 @@ struct dm_plan {
     void* xs = nullptr;
     int32_t* perm = nullptr;
     void* R = nullptr;            // R_i = sum_c (x_i(c) - mu_c), mu_c = column median
-    // squared l2
+    // squared l2 and ||.||_p^p
     const void* X = nullptr;
     int64_t ldx = 0;
     void* mu = nullptr;
+    int p = 0;                    // DM_LPP: the even power
+    int64_t d_in = 0;             // DM_L2_EMBED: dimension of the input points (d is m)
 };
 
 struct dm_batch {
@@ -122,6 +124,8 @@ dm_status from_cuda(cudaError_t e) {
 
 bool valid_dtype(dm_dtype t) { return t == DM_F32 || t == DM_F64 || t == DM_I32; }
 bool valid_metric(dm_metric m) { return m == DM_L1 || m == DM_L2SQ; }
+// Metrics whose plan is the sorted coordinates of Algorithm 1.
+bool sorted_metric(dm_metric m) { return m == DM_L1 || m == DM_TV || m == DM_L2_EMBED; }
 
 size_t acc_size(dm_dtype t) { return t == DM_F32 ? 4 : 8; }
 
@@ -444,13 +448,62 @@ int64_t l2_chunk(const dm_plan* p, int64_t k) {
 }
 
 size_t matmat_scratch(const dm_plan* p, int64_t k) {
-    if (p->metric == DM_L1) return l1_query_scratch_bytes(p->dtype, p->n, p->d, k, p->ctx->num_sms);
-    k = std::max<int64_t>(1, l2_chunk(p, k));
+    if (sorted_metric(p->metric)) return l1_query_scratch_bytes(p->dtype, p->n, p->d, k, p->ctx->num_sms);
+    size_t feat = 0;
+    int64_t D = p->d;
+    if (p->metric == DM_LPP) {
+        feat = up16(lpp_feature_bytes(p->dtype, p->n, p->d, p->p));
+        D = p->d * p->p;
+        k = std::max<int64_t>(1, std::min<int64_t>(k, reduce_max_k(p->dtype, D)));
+    } else {
+        k = std::max<int64_t>(1, l2_chunk(p, k));
+    }
     ReduceArgs r{};
-    r.n = p->n; r.d = p->d; r.k = k;
+    r.n = p->n; r.d = D; r.k = k;
     r.num_sms = p->ctx->num_sms;
-    const size_t o_res = up16((size_t)reduce_blocks(r) * (p->d + 2) * k * 8);
-    return up16(o_res + (size_t)(p->d + 2) * k * 8);
+    const size_t o_res = up16((size_t)reduce_blocks(r) * (D + 2) * k * 8);
+    return feat + up16(o_res + (size_t)(D + 2) * k * 8);
+}
+
+// ||x - y||_p^p for even p: powers of the centred coordinates, their moments
+// against Z (the reduce kernel, in column chunks), then the binomial sum.
+dm_status lpp_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out,
+                  int64_t ldo) {
+    dm_ctx* ctx = e.ctx;
+    const dm_dtype t = p->dtype;
+    const int64_t n = p->n, d = p->d, D = d * p->p;
+    const int64_t kc = std::min<int64_t>(k, reduce_max_k(t, D));
+    if (kc < 1) return DM_ERR_UNSUPPORTED;
+    unsigned char* F = e.scratch;
+    unsigned char* base = e.scratch + up16(lpp_feature_bytes(t, n, d, p->p));
+    {
+        ProfScope ps(e, "lpp_features");
+        DM_TRY_CUDA(lpp_features_launch(t, p->X, n, d, p->ldx, p->mu, p->p, F, ctx->num_sms, e.stream,
+                                        &ctx->launches));
+    }
+    for (int64_t j0 = 0; j0 < k; j0 += kc) {
+        const int64_t kk = std::min<int64_t>(kc, k - j0);
+        ReduceArgs r{};
+        r.dtype = t;
+        r.n = n; r.d = D;
+        r.X = F; r.ldx = D; r.x_acc = true;
+        r.mu = nullptr; r.mu_stride = 1; r.with_s = false;
+        r.Z = static_cast<const unsigned char*>(Z) + (size_t)j0 * dtype_size(t);
+        r.k = kk; r.ldz = ldz;
+        r.num_sms = ctx->num_sms;
+        const size_t o_res = up16((size_t)reduce_blocks(r) * (D + 2) * kk * 8);
+        r.partial = base;
+        r.res = base + o_res;
+        {
+            ProfScope ps(e, "lpp_reduce");
+            DM_TRY_CUDA(reduce_launch(r, e.stream, &ctx->launches));
+        }
+        ProfScope ps(e, "lpp_apply");
+        DM_TRY_CUDA(lpp_apply_launch(t, p->X, n, d, p->ldx, p->mu, r.res, p->p, kk,
+                                     static_cast<unsigned char*>(out) + (size_t)j0 * out_size(t), ldo,
+                                     ctx->num_sms, e.stream, &ctx->launches));
+    }
+    return DM_OK;
 }
 
 dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out,
@@ -460,7 +513,8 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
     const int64_t n = p->n, d = p->d;
     if (e.scratch_bytes < matmat_scratch(p, k)) return DM_ERR_INTERNAL;
 
-    if (p->metric == DM_L1) {
+    if (p->metric == DM_LPP) return lpp_run(e, p, Z, k, ldz, out, ldo);
+    if (sorted_metric(p->metric)) {
         // R^T Z, 1^T Z and the group-major copy of Z, then the sorted part
         // (Algorithm 2).
         L1QueryArgs q{};
@@ -490,6 +544,10 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
         if (!q.deterministic) {
             ProfScope ps(e, "l1_finalize");
             DM_TRY_CUDA(l1_finalize_launch(q, e.stream, &ctx->launches));
+        }
+        if (p->metric == DM_TV) {   // TV(x, y) = ||x - y||_1 / 2
+            ProfScope ps(e, "tv_scale");
+            DM_TRY_CUDA(scale_launch(t, out, n, k, ldo, 0.5, ctx->num_sms, e.stream, &ctx->launches));
         }
         return DM_OK;
     }
@@ -531,6 +589,9 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
 
 dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out, int64_t ldo) {
     if (p->metric == DM_L2SQ && l2_chunk(p, k) < 1) return DM_ERR_UNSUPPORTED;
+    if (p->metric == DM_LPP && reduce_max_k(p->dtype, p->d * p->p) < 1) return DM_ERR_UNSUPPORTED;
+    if (p->metric == DM_LPP && lpp_apply_smem(p->dtype, p->d, p->p, std::min<int64_t>(k, reduce_max_k(p->dtype, p->d * p->p))) > 200 * 1024)
+        return DM_ERR_UNSUPPORTED;
     DM_TRY(ensure_arena(p->ctx, matmat_scratch(p, k)));
     return matmat_run(ctx_exec(p->ctx), p, Z, k, ldz, out, ldo);
 }
@@ -548,7 +609,8 @@ dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64
     a.G = G; a.ldg = ldg;
     a.num_sms = ctx->num_sms;
     const size_t gbytes = up16(grad_scratch_bytes(t, n, d, k));
-    if (p->metric == DM_L1) {
+    if (p->metric == DM_LPP || p->metric == DM_L2_EMBED) return DM_ERR_UNSUPPORTED;
+    if (p->metric == DM_L1 || p->metric == DM_TV) {
         DM_TRY(ensure_arena(ctx, gbytes));
         a.scratch = ctx->arena;
         a.xs = p->xs; a.perm = p->perm;
@@ -568,8 +630,14 @@ dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64
             ProfScope ps(ctx, "grad_l1_eval");
             DM_TRY_CUDA(grad_l1_launch(a, 2, ctx->stream, &ctx->launches));
         }
-        ProfScope ps(ctx, "grad_l1_transpose");
-        DM_TRY_CUDA(grad_l1_launch(a, 3, ctx->stream, &ctx->launches));
+        {
+            ProfScope ps(ctx, "grad_l1_transpose");
+            DM_TRY_CUDA(grad_l1_launch(a, 3, ctx->stream, &ctx->launches));
+        }
+        if (p->metric == DM_TV) {
+            ProfScope ps(ctx, "tv_scale");
+            DM_TRY_CUDA(scale_launch(t, G, n, d, ldg, 0.5, ctx->num_sms, ctx->stream, &ctx->launches));
+        }
         return DM_OK;
     }
     // squared l2: [X - mu, 1]^T [z_q, w_q] by the reduce kernel, then the closed form
@@ -640,7 +708,7 @@ dm_status batch_build(dm_batch* b, int L) {
         st.lane = l;
         load[(size_t)l] += st.cost;
         dm_plan* p = st.plan;
-        const size_t prep = p->metric == DM_L1 ? sort_layout(p->dtype, p->n, p->d).total : prepare_l2_scratch(p);
+        const size_t prep = sorted_metric(p->metric) ? sort_layout(p->dtype, p->n, p->d).total : prepare_l2_scratch(p);
         need[(size_t)l] = std::max(need[(size_t)l], std::max(prep, matmat_scratch(p, st.k)));
     }
     for (int l = 0; l < L; ++l) {
@@ -674,8 +742,8 @@ dm_status batch_build(dm_batch* b, int L) {
         auto& st = b->sets[i];
         const Exec e{ctx, b->streams[(size_t)st.lane], static_cast<unsigned char*>(b->scratch[(size_t)st.lane]),
                      b->scratch_bytes[(size_t)st.lane], true};
-        s = st.plan->metric == DM_L1 ? prepare_l1_run(e, st.plan, st.X, st.ldx)
-                                     : prepare_l2_run(e, st.plan, st.X, st.ldx);
+        s = sorted_metric(st.plan->metric) ? prepare_l1_run(e, st.plan, st.X, st.ldx)
+                                           : prepare_l2_run(e, st.plan, st.X, st.ldx);
         if (s == DM_OK) s = matmat_run(e, st.plan, st.Z, st.k, st.ldz, st.out, st.ldo);
     }
     for (int l = 0; l < L && s == DM_OK; ++l) {
@@ -889,7 +957,9 @@ dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* 
                      int64_t d, int64_t ldx, dm_plan** plan) {
     if (!plan) return DM_ERR_INVALID_ARG;
     *plan = nullptr;
-    if (!ctx || !X || !valid_metric(metric) || !valid_dtype(dtype)) return DM_ERR_INVALID_ARG;
+    if (!ctx || !X || !(valid_metric(metric) || metric == DM_TV) || !valid_dtype(dtype))
+        return DM_ERR_INVALID_ARG;
+    if (metric == DM_TV && dtype == DM_I32) return DM_ERR_UNSUPPORTED;   // half-integer results
     if (n < 1 || n > kMaxN || d < 1 || ldx < d) return DM_ERR_INVALID_ARG;
     if ((double)n * (double)d >= 2147483648.0) return DM_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
@@ -900,7 +970,78 @@ dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* 
     p->dtype = dtype;
     p->n = n;
     p->d = d;
-    const dm_status s = metric == DM_L1 ? prepare_l1(ctx, p, X, ldx) : prepare_l2(ctx, p, X, ldx);
+    const dm_status s = sorted_metric(metric) ? prepare_l1(ctx, p, X, ldx) : prepare_l2(ctx, p, X, ldx);
+    if (s != DM_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaGetLastError();
+        free_plan_buffers(p);
+        delete p;
+        return s;
+    }
+    *plan = p;
+    return DM_OK;
+}
+
+dm_status dm_prepare_lpp(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, int64_t d, int64_t ldx,
+                         int pw, dm_plan** plan) {
+    if (!plan) return DM_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!ctx || !X || !valid_dtype(dtype) || pw < 2 || pw > 16 || (pw & 1)) return DM_ERR_INVALID_ARG;
+    if (n < 1 || n > kMaxN || d < 1 || ldx < d) return DM_ERR_INVALID_ARG;
+    if ((double)n * (double)d * pw >= 2147483648.0) return DM_ERR_UNSUPPORTED;
+    if (reduce_max_k(dtype, d * pw) < 1 || lpp_apply_smem(dtype, d, pw, 1) > 200 * 1024) return DM_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    dm_plan* p = new (std::nothrow) dm_plan();
+    if (!p) return DM_ERR_OOM;
+    p->ctx = ctx; p->metric = DM_LPP; p->dtype = dtype; p->n = n; p->d = d; p->p = pw;
+    const dm_status s = prepare_l2(ctx, p, X, ldx);     // records X, column means mu
+    if (s != DM_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaGetLastError();
+        free_plan_buffers(p);
+        delete p;
+        return s;
+    }
+    *plan = p;
+    return DM_OK;
+}
+
+dm_status dm_prepare_l2_embed(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, int64_t d,
+                              int64_t ldx, const void* G, int64_t m, dm_plan** plan) {
+    if (!plan) return DM_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (!ctx || !X || !G || (dtype != DM_F32 && dtype != DM_F64) || m < 1) return DM_ERR_INVALID_ARG;
+    if (n < 1 || n > kMaxN || d < 1 || ldx < d) return DM_ERR_INVALID_ARG;
+    if ((double)n * (double)m >= 2147483648.0) return DM_ERR_UNSUPPORTED;
+    if (project_smem(dtype, d, m) > 200 * 1024) return DM_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    dm_plan* p = new (std::nothrow) dm_plan();
+    if (!p) return DM_ERR_OOM;
+    p->ctx = ctx; p->metric = DM_L2_EMBED; p->dtype = dtype; p->n = n; p->d = m; p->d_in = d;
+    // T(X) into a buffer of the plan, the l1 plan of T(X), then the buffer
+    // goes back to the context (the plan keeps only the sorted coordinates).
+    void* Xp = nullptr;
+    dm_status s = plan_alloc(p, (size_t)n * m * dtype_size(dtype), &Xp);
+    if (s == DM_OK) {
+        ProfScope ps(ctx, "l2_embed_project");
+        s = from_cuda(project_launch(dtype, X, n, d, ldx, G, m, Xp, ctx->num_sms, ctx->stream, &ctx->launches));
+    }
+    if (s == DM_OK) s = prepare_l1(ctx, p, Xp, m);
+    if (s == DM_OK) {
+        for (size_t i = 0; i < p->owned.size(); ++i) {
+            if (p->owned[i].first == Xp) {
+                if (ctx->pool_bytes + p->owned[i].second <= kPoolCap) {
+                    ctx->pool.push_back({Xp, p->owned[i].second});
+                    ctx->pool_bytes += p->owned[i].second;
+                } else {
+                    cudaStreamSynchronize(ctx->stream);
+                    cudaFree(Xp);
+                }
+                p->owned.erase(p->owned.begin() + (long)i);
+                break;
+            }
+        }
+    }
     if (s != DM_OK) {
         cudaStreamSynchronize(ctx->stream);
         cudaGetLastError();
@@ -940,7 +1081,8 @@ dm_status dm_batch_create(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, int64_t
                           dm_batch** batch) {
     if (!batch) return DM_ERR_INVALID_ARG;
     *batch = nullptr;
-    if (!ctx || !valid_metric(metric) || !valid_dtype(dtype) || nsets < 1 || lanes < 0 || lanes > 64 ||
+    if (!ctx || !(valid_metric(metric) || metric == DM_TV) || !valid_dtype(dtype) || nsets < 1 || lanes < 0 ||
+        lanes > 64 ||
         !n || !d || !X || !ldx || !k || !Z || !ldz || !out || !ldo)
         return DM_ERR_INVALID_ARG;
     for (int64_t i = 0; i < nsets; ++i) {
@@ -968,10 +1110,11 @@ dm_status dm_batch_create(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, int64_t
         if (!p) { s = DM_ERR_OOM; break; }
         p->ctx = ctx; p->metric = metric; p->dtype = dtype; p->n = n[i]; p->d = d[i];
         const double es = (double)dtype_size(dtype);
-        const double cost = metric == DM_L1 ? (double)n[i] * d[i] * (8.0 + 8.0 * k[i] + 64.0)
+        if (metric == DM_TV && dtype == DM_I32) { s = DM_ERR_UNSUPPORTED; delete p; break; }
+        const double cost = sorted_metric(metric) ? (double)n[i] * d[i] * (8.0 + 8.0 * k[i] + 64.0)
                                             : (double)n[i] * (2.0 * d[i] * es + 2.0 * k[i] * es);
         b->sets.push_back({p, X[i], ldx[i], Z[i], k[i], ldz[i], out[i], ldo[i], cost, 0});
-        s = metric == DM_L1 ? alloc_l1_plan(p) : plan_alloc(p, (size_t)d[i] * dtype_size(dtype), &p->mu);
+        s = sorted_metric(metric) ? alloc_l1_plan(p) : plan_alloc(p, (size_t)d[i] * dtype_size(dtype), &p->mu);
         if (metric == DM_L2SQ) { p->X = X[i]; p->ldx = ldx[i]; }
     }
     if (s == DM_OK) s = lanes > 0 ? batch_build(b, (int)std::min<int64_t>(lanes, nsets)) : batch_autotune(b);
@@ -1016,7 +1159,7 @@ dm_status dm_sync(dm_ctx* ctx) {
 }
 
 dm_status dm_plan_export(dm_plan* p, void* sorted_values, int32_t* perm) {
-    if (!p || p->metric != DM_L1 || !sorted_values || !perm) return DM_ERR_INVALID_ARG;
+    if (!p || !sorted_metric(p->metric) || !sorted_values || !perm) return DM_ERR_INVALID_ARG;
     DeviceGuard g(p->ctx->device);
     const size_t nd = (size_t)p->n * (size_t)p->d;
     DM_TRY_CUDA(cudaMemcpyAsync(sorted_values, p->xs, nd * dtype_size(p->dtype),

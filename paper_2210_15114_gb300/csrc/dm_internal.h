@@ -189,4 +189,19 @@ cudaError_t grad_pack_launch(const GradArgs& a, cudaStream_t s, int64_t* launche
 cudaError_t grad_l1_launch(const GradArgs& a, int stage, cudaStream_t s, int64_t* launches);
 cudaError_t grad_l2_apply_launch(const GradArgs& a, cudaStream_t s, int64_t* launches);
 
+// Variants (variants.cu).
+cudaError_t scale_launch(dm_dtype t, void* out, int64_t n, int64_t k, int64_t ldo, double s,
+                         int num_sms, cudaStream_t st, int64_t* launches);
+size_t lpp_feature_bytes(dm_dtype t, int64_t n, int64_t d, int p);
+cudaError_t lpp_features_launch(dm_dtype t, const void* X, int64_t n, int64_t d, int64_t ldx,
+                                const void* mu, int p, void* F, int num_sms, cudaStream_t st,
+                                int64_t* launches);
+size_t lpp_apply_smem(dm_dtype t, int64_t d, int p, int64_t k);
+cudaError_t lpp_apply_launch(dm_dtype t, const void* X, int64_t n, int64_t d, int64_t ldx,
+                             const void* mu, const void* res, int p, int64_t k, void* out, int64_t ldo,
+                             int num_sms, cudaStream_t st, int64_t* launches);
+size_t project_smem(dm_dtype t, int64_t d, int64_t m);
+cudaError_t project_launch(dm_dtype t, const void* X, int64_t n, int64_t d, int64_t ldx, const void* G,
+                           int64_t m, void* Xp, int num_sms, cudaStream_t st, int64_t* launches);
+
 }  // namespace dm
