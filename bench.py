@@ -62,6 +62,7 @@ def parse_args():
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--no-krylov", action="store_true", help="skip the block Krylov measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the variant measurements")
     ap.add_argument("--grad-n", type=int, default=1 << 21)
     ap.add_argument("--grad-d", type=int, default=64)
     ap.add_argument("--profile-only", action="store_true",
@@ -496,6 +497,52 @@ def measure_batch(dm, ctx, stream, dev, reps=5):
     return res
 
 
+def measure_variants(dm, ctx, stream, dev, X, Z, Xd, Zd, reps=5):
+    """Prepare and query times of the variants on the step's workload
+    (n d k units per query), with sampled-row errors against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2210_15114_gb300 import inputs
+    n, d = X.shape
+    k = Z.shape[1]
+    rows = inputs.sample_rows(n, 8)
+    P = inputs.simplex_points(n, d)
+    Pd = torch.from_numpy(P).to(dev)
+    G = inputs.embedding_matrix(256, d)
+    Gd = torch.from_numpy(G).to(dev)
+    cases = {
+        "tv": (lambda: dm.dm_prepare(ctx, "tv", Pd), lambda: oracle.tv_rows(P, Z, rows)),
+        "lpp_p4": (lambda: dm.dm_prepare_lpp(ctx, Xd, 4), lambda: oracle.lpp_rows(X, Z, 4, rows)),
+        "l2_embed_m256": (lambda: dm.dm_prepare_l2_embed(ctx, Xd, Gd),
+                          lambda: oracle.l1_rows(oracle.l2_embed(X, G), Z, rows)),
+    }
+    res = {"workload": f"n={n} d={d} k={k} fp32 (tv: Dirichlet(1) rows; others: the step's mixture)",
+           "units": "point*query*dim per second of the query (n d k)"}
+    for name, (prep, ref) in cases.items():
+        plan = prep()
+        out = dm.dm_matmat(plan, Zd)
+        torch.cuda.synchronize(dev)
+        pe, qe = [], []
+        for _ in range(reps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            plan = prep()
+            e1.record(stream)
+            dm.dm_matmat(plan, Zd, out=out)
+            e2.record(stream)
+            pe.append((e0, e1))
+            qe.append((e1, e2))
+        torch.cuda.synchronize(dev)
+        p_ms = statistics.mean(a.elapsed_time(b) for a, b in pe)
+        q_ms = statistics.mean(a.elapsed_time(b) for a, b in qe)
+        err = oracle.relative_error(out.cpu().numpy()[rows], ref())
+        res[name] = {"prepare_ms": p_ms, "query_ms": q_ms, "value": n * d * k / (q_ms * 1e-3),
+                     "rel_err_sampled_rows": err}
+        del plan
+    return res
+
+
 # ------------------------------------------------------------- reference arm
 def run_reference(a):
     rank, world, _ = dist_env()
@@ -651,6 +698,11 @@ def main():
     if not a.no_batch:
         batch = measure_batch(dm, ctx, stream, dev)
 
+    # ---- variants: total variation, ||.||_4^4, approximate l2 (m = 256)
+    variants = None
+    if not a.no_variants:
+        variants = measure_variants(dm, ctx, stream, dev, X, Z, Xd, Zd)
+
     # ---- brute force (the plain method) and accuracy
     brute = None
     if not a.no_brute:
@@ -712,7 +764,7 @@ def main():
             "gpu_launches": launches, "launches_per_step": launches / a.steps,
             "wall_s_timed_region": t_wall,
             "parts_ms": parts, "kernels": kernels, "roofline": roofline, "l1_query_all_kernels": l1_query_all,
-            "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad, "krylov": krylov, "batch": batch,
+            "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad, "krylov": krylov, "batch": batch, "variants": variants,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:

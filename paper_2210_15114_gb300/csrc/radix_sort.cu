@@ -104,10 +104,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 // CTA = RB rows x DB columns of X.  All loads of a thread are issued first
 // (RB*DB/256 values in registers), the keys go to a padded shared tile, then
 // each warp histograms one column's keys into a private shared histogram
-// (no contention between warps; lanes that share a digit in the two highest
-// digit positions -- where sign and exponent bits make digits collide -- add
-// once through a warp match), and finally the tile is written column-major
-// and the histograms are added to the global counts.
+// (no contention between warps; lanes of one warp that hit the same bin --
+// frequent in the two highest digit positions, where sign and exponent bits
+// collide -- are serialized by the shared-memory unit, which costs less than
+// forming peer masks on the saturated integer pipe), and finally the tile is
+// written column-major and the histograms are added to the global counts.
 template <dm_dtype DT>
 struct KeygenCfg {
     using Ty = Types<DT>;
@@ -174,15 +175,10 @@ keygen_hist_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64
             for (int r = rbeg + lane; r < rbeg + rows_per; r += 32) {
                 const bool ok = colok && r < nr;
                 const Key key = ok ? tile[c * TS + r] : Key(0);
+                if (ok) {
 #pragma unroll
-                for (int q = 0; q < P; ++q) {
-                    const uint32_t digit = (uint32_t)(key >> (8 * q)) & 0xffu;
-                    if (q >= P - 2) {
-                        const uint32_t peers = digit_peers(digit, ok);
-                        if (ok && lane == __ffs(peers) - 1) atomicAdd(&hw[q * kRadix + digit], (uint32_t)__popc(peers));
-                    } else if (ok) {
-                        atomicAdd(&hw[q * kRadix + digit], 1u);
-                    }
+                    for (int q = 0; q < P; ++q)
+                        atomicAdd(&hw[q * kRadix + ((uint32_t)(key >> (8 * q)) & 0xffu)], 1u);
                 }
             }
         }
