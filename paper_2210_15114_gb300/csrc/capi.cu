@@ -24,8 +24,11 @@ struct dm_ctx {
     size_t host_hist_words = 0;
     int64_t launches = 0;
     int deterministic = 0;           // dm_set_deterministic
-    // Device buffers of dm_matmat_host (grown on demand).
+    // Device buffers of dm_matmat_host (grown on demand), and the stream and
+    // event its copy of Z uses to overlap the preprocessing.
     void* hx = nullptr; size_t hx_bytes = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t aux_done = nullptr;
     void* hz = nullptr; size_t hz_bytes = 0;
     void* ho = nullptr; size_t ho_bytes = 0;
     // Kernel timing (dm_profile_enable / dm_profile_read).
@@ -901,6 +904,8 @@ void dm_destroy(dm_ctx* ctx) {
     if (ctx->hx) cudaFree(ctx->hx);
     if (ctx->hz) cudaFree(ctx->hz);
     if (ctx->ho) cudaFree(ctx->ho);
+    if (ctx->aux) { cudaStreamSynchronize(ctx->aux); cudaStreamDestroy(ctx->aux); }
+    if (ctx->aux_done) cudaEventDestroy(ctx->aux_done);
     if (ctx->err) cudaFree(ctx->err);
     if (ctx->host_err) cudaFreeHost(ctx->host_err);
     if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
@@ -1193,14 +1198,26 @@ dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const vo
     DeviceGuard g(ctx->device);
     const size_t es = dtype_size(dtype), os = out_size(dtype);
     DM_TRY(ensure_buffer(ctx, &ctx->hx, &ctx->hx_bytes, (size_t)n * d * es));
+    if (ctx->aux) DM_TRY_CUDA(cudaStreamSynchronize(ctx->aux));   // an earlier copy may still target hz
     DM_TRY(ensure_buffer(ctx, &ctx->hz, &ctx->hz_bytes, (size_t)n * k * es));
     DM_TRY(ensure_buffer(ctx, &ctx->ho, &ctx->ho_bytes, (size_t)n * k * os));
-    DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hx, d * es, Xh, ldx * es, d * es, n, cudaMemcpyHostToDevice,
-                                  ctx->stream));
+    if (!ctx->aux) {
+        DM_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        DM_TRY_CUDA(cudaEventCreateWithFlags(&ctx->aux_done, cudaEventDisableTiming));
+    }
+    // Z travels on the second stream while X is copied and preprocessed; the
+    // product waits for it.  (The second stream first waits for earlier work
+    // on the context's stream, which may still read the previous Z.)
+    DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->stream));
+    DM_TRY_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->aux_done, 0));
     DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hz, k * es, Zh, ldz * es, k * es, n, cudaMemcpyHostToDevice,
+                                  ctx->aux));
+    DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->aux));
+    DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hx, d * es, Xh, ldx * es, d * es, n, cudaMemcpyHostToDevice,
                                   ctx->stream));
     dm_plan* p = nullptr;
     DM_TRY(dm_prepare(ctx, metric, dtype, ctx->hx, n, d, d, &p));
+    DM_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->aux_done, 0));
     dm_status s = dm_matmat(p, ctx->hz, k, k, ctx->ho, k);
     if (s == DM_OK) {
         cudaError_t e = cudaMemcpy2DAsync(outh, ldo * os, ctx->ho, k * os, k * os, n,

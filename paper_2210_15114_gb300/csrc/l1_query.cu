@@ -258,8 +258,11 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
     constexpr int QW = Cfg::QW, NQ = Cfg::NQ;
     constexpr int SPW = 32 / NQ;   // segments per warp
 
-    __shared__ Acc wt[kWarps][NV];
-    __shared__ Acc ag_s[4][KC];
+    // Double-buffered by the iteration's slot: a warp writes buffer b of the
+    // next-but-one iteration only after the first barrier of the iteration in
+    // between, which every warp reaches only after its last read of b.
+    __shared__ Acc wt[2][kWarps][NV];
+    __shared__ Acc ag_s[2][4][KC];
     __shared__ uint32_t s_claim[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -347,7 +350,7 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
             Acc ez = __shfl_up_sync(0xffffffffu, iz, NQ);
             Acc exz = __shfl_up_sync(0xffffffffu, ixz, NQ);
             if (lane < NQ) { ez = 0; exz = 0; }
-            if (lane >= 32 - NQ) { wt[warp][col0 + q] = iz; wt[warp][KC + col0 + q] = ixz; }
+            if (lane >= 32 - NQ) { wt[slot][warp][col0 + q] = iz; wt[slot][warp][KC + col0 + q] = ixz; }
             Lz[q] = ez;
             Lxz[q] = exz;
         }
@@ -356,12 +359,12 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
             const Wide bm = (Wide)b - (Wide)p.mu[(int64_t)c * p.mu_stride];
             const Wide* pr = p.pre + (((int64_t)g * d + c) * T + t) * NV;
             const Wide Pz = pr[tid], Pxz = pr[KC + tid];
-            ag_s[0][tid] = (Acc)Pz;
-            ag_s[1][tid] = (Acc)(Pxz - bm * Pz);
+            ag_s[slot][0][tid] = (Acc)Pz;
+            ag_s[slot][1][tid] = (Acc)(Pxz - bm * Pz);
             if (MODE == kOrdered && c == 0) {
                 const int gc = g * KC + tid;
-                ag_s[2][tid] = gc < k ? (Acc)p.res[gc] : Acc(0);       // R^T Z
-                ag_s[3][tid] = gc < k ? (Acc)p.res[k + gc] : Acc(0);   // 1^T Z
+                ag_s[slot][2][tid] = gc < k ? (Acc)p.res[gc] : Acc(0);       // R^T Z
+                ag_s[slot][3][tid] = gc < k ? (Acc)p.res[k + gc] : Acc(0);   // 1^T Z
             }
         }
         // D. (ordered) coordinate order: wait for every tile of coordinate c-1
@@ -378,7 +381,7 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
             Acc pz = 0, pxz = 0;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) {
-                const Acc a = wt[w][col0 + q], bb = wt[w][KC + col0 + q];
+                const Acc a = wt[slot][w][col0 + q], bb = wt[slot][w][KC + col0 + q];
                 if (w < warp) { pz += a; pxz += bb; }
             }
             Lz[q] += pz;
@@ -389,7 +392,7 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
         {
             Acc al[QW], gm[QW];
 #pragma unroll
-            for (int q = 0; q < QW; ++q) { al[q] = ag_s[0][col0 + q]; gm[q] = ag_s[1][col0 + q]; }
+            for (int q = 0; q < QW; ++q) { al[q] = ag_s[slot][0][col0 + q]; gm[q] = ag_s[slot][1][col0 + q]; }
             Acc* og = p.outg + (int64_t)g * p.n * KC + col0;
             if constexpr (MODE == kAtomic) {
 #pragma unroll
@@ -410,8 +413,8 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
                 Acc rz[QW], uz[QW];
 #pragma unroll
                 for (int q = 0; q < QW; ++q) {
-                    rz[q] = first ? ag_s[2][col0 + q] : Acc(0);
-                    uz[q] = first ? ag_s[3][col0 + q] : Acc(0);
+                    rz[q] = first ? ag_s[slot][2][col0 + q] : Acc(0);
+                    uz[q] = first ? ag_s[slot][3][col0 + q] : Acc(0);
                 }
                 Out* oc = static_cast<Out*>(p.out) + (int64_t)g * KC + col0;
                 Acc old[SEG_LEN][QW];
@@ -452,13 +455,12 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
             }
         }
 
-        // F. this tile's values are in place (the barrier also frees wt/ag_s)
+        // F. (ordered) this tile's values are in place before it is counted;
+        // the L2-reduction mode needs no barrier here (double buffers)
         if constexpr (MODE == kOrdered) {
             __threadfence();
             __syncthreads();
             if (tid == 0) red_release_add(p.done + (int64_t)g * d + c, 1u);
-        } else {
-            __syncthreads();
         }
         claim = next;
         slot ^= 1;
