@@ -42,7 +42,7 @@ namespace dm {
 namespace {
 
 constexpr int kGT = 256;                // threads per block
-constexpr int kGI = 8;                  // sorted positions per thread
+constexpr int kGI = 4;                  // sorted positions per thread
 constexpr int kGTile = kGT * kGI;       // sorted positions per tile
 constexpr int kGW = kGT / 32;           // warps per block
 constexpr int kNone = INT_MAX;
