@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -784,10 +785,27 @@ dm_status batch_launch(dm_batch* b) {
     return DM_OK;
 }
 
-// Lane counts tried by the autotuner and the choices it made, by shape.
+// The autotuner's choices, by batch shape (process-wide, shared by threads).
 std::map<std::string, int>& lane_cache() {
     static std::map<std::string, int> m;
     return m;
+}
+std::mutex& lane_cache_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+
+bool lane_cache_find(const std::string& key, int* lanes) {
+    std::lock_guard<std::mutex> lock(lane_cache_mutex());
+    auto it = lane_cache().find(key);
+    if (it == lane_cache().end()) return false;
+    *lanes = it->second;
+    return true;
+}
+
+void lane_cache_store(const std::string& key, int lanes) {
+    std::lock_guard<std::mutex> lock(lane_cache_mutex());
+    lane_cache()[key] = lanes;
 }
 
 std::string batch_key(const dm_batch* b) {
@@ -809,8 +827,8 @@ std::string batch_key(const dm_batch* b) {
 // replays of its graph) and keep the fastest.
 dm_status batch_autotune(dm_batch* b) {
     const std::string key = batch_key(b);
-    auto it = lane_cache().find(key);
-    if (it != lane_cache().end()) return batch_build(b, it->second);
+    int cached = 0;
+    if (lane_cache_find(key, &cached)) return batch_build(b, cached);
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     DM_TRY_CUDA(cudaEventCreate(&t0));
     if (cudaEventCreate(&t1) != cudaSuccess) { cudaEventDestroy(t0); return DM_ERR_CUDA; }
@@ -834,7 +852,7 @@ dm_status batch_autotune(dm_batch* b) {
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (s != DM_OK) return s;
-    lane_cache()[key] = best;
+    lane_cache_store(key, best);
     return batch_build(b, best);
 }
 

@@ -89,6 +89,20 @@ def test_batch_matches_oracle(dm, ctx, metric, dtype, lanes):
     dm.dm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batch_total_variation(dm, ctx, dtype):
+    sets = [(inputs.simplex_points(n, d, seed=s, dtype=dtype), inputs.gaussian_queries(n, k, seed=s, dtype=dtype))
+            for s, (n, d, k) in enumerate([(1, 3, 1), (700, 5, 2), (5000, 8, 3), (2049, 2, 4)])]
+    Xs = [torch.from_numpy(X).cuda() for X, _ in sets]
+    Zs = [torch.from_numpy(Z).cuda() for _, Z in sets]
+    b = dm.dm_batch_create(ctx, "tv", Xs, Zs, lanes=2)
+    outs = dm.dm_batch_run(b)
+    dm.dm_sync(ctx)
+    for (X, Z), o in zip(sets, outs):
+        check(o.cpu().numpy(), oracle.tv_rows(X, Z), dtype)
+    dm.dm_batch_destroy(b)
+
+
 def test_batch_equals_single_calls_exactly_on_integers(dm, ctx):
     sets = small_sets(np.int32, nsets=10)
     Xs = [torch.from_numpy(X).cuda() for X, _ in sets]

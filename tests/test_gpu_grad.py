@@ -185,7 +185,7 @@ def test_autograd_matches_oracle_and_gradcheck(dm):
     ctx = dm.dm_create(0)
     dm.dm_set_deterministic(ctx, True)
     rng = np.random.default_rng(21)
-    for metric in ("l1", "l2sq"):
+    for metric in ("l1", "l2sq", "tv"):
         X = torch.tensor(rng.normal(size=(40, 3)), device="cuda", requires_grad=True)
         Z = torch.tensor(rng.normal(size=(40, 2)), device="cuda", requires_grad=True)
         assert torch.autograd.gradcheck(lambda a, b: DistanceProduct.apply(a, b, metric, ctx), (X, Z),
@@ -194,6 +194,8 @@ def test_autograd_matches_oracle_and_gradcheck(dm):
         Wt = torch.tensor(rng.normal(size=(40, 2)), device="cuda")
         (out * Wt).sum().backward()
         Xn, Zn, Wn = (t.detach().cpu().numpy() for t in (X, Z, Wt))
-        np.testing.assert_allclose(X.grad.cpu().numpy(), GRAD[metric](Xn, Wn, Zn), rtol=0, atol=1e-9)
-        AW = (oracle.l1_rows if metric == "l1" else oracle.l2sq_rows)(Xn, Wn)
+        scale = 0.5 if metric == "tv" else 1.0
+        base = "l1" if metric == "tv" else metric
+        np.testing.assert_allclose(X.grad.cpu().numpy(), scale * GRAD[base](Xn, Wn, Zn), rtol=0, atol=1e-9)
+        AW = scale * (oracle.l1_rows if base == "l1" else oracle.l2sq_rows)(Xn, Wn)
         np.testing.assert_allclose(Z.grad.cpu().numpy(), AW, rtol=0, atol=1e-9)
