@@ -31,7 +31,9 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("dm_create", "dm_destroy", "dm_prepare", "dm_plan_destroy", "dm_matvec_l1",
                      "dm_matvec_l2sq", "dm_matmat", "dm_sync", "dm_status_string",
-                     "dm_bruteforce", "dm_matmat_host", "dm_plan_export"):
+                     "dm_bruteforce", "dm_matmat_host", "dm_plan_export", "dm_grad",
+                     "dm_batch_create", "dm_batch_run", "dm_batch_lanes", "dm_batch_destroy",
+                     "dm_prepare_lpp", "dm_prepare_l2_embed", "dm_l2sq_matmat_noalloc"):
         assert required in names
 
 
@@ -66,6 +68,20 @@ def test_argument_checks_without_device(lib):
     assert lib.dm_sync(None) == 1
     assert lib.dm_matvec_l1(None, None, None) == 1
     assert lib.dm_bruteforce(None, 0, 0, None, 1, 1, 1, None, 1, 1, None, 1) == 1
+    assert lib.dm_grad(None, None, 1, None, 1, 1, None, 1) == 1
+    assert lib.dm_prepare_lpp(None, 0, None, 1, 1, 1, 4, ctypes.byref(h)) == 1
+    assert lib.dm_prepare_l2_embed(None, 0, None, 1, 1, 1, None, 8, ctypes.byref(h)) == 1
+    assert lib.dm_batch_create(None, 0, 0, 1, None, None, None, None, None, None, None, None, None,
+                               0, ctypes.byref(h)) == 1
+    assert lib.dm_batch_run(None) == 1
+    assert lib.dm_batch_lanes(None) == 0
+    lib.dm_batch_destroy(None)                                     # no-op
+    # the no-alloc entry checks its arguments before touching the device
+    dummy = P(16)
+    assert lib.dm_l2sq_matmat_noalloc(0, None, 10, 2, 2, dummy, 1, 1, dummy, 1, None) == 1
+    assert lib.dm_l2sq_matmat_noalloc(0, dummy, 0, 2, 2, dummy, 1, 1, dummy, 1, None) == 1
+    assert lib.dm_l2sq_matmat_noalloc(0, dummy, 10, 33, 33, dummy, 1, 1, dummy, 1, None) == 2
+    assert lib.dm_l2sq_matmat_noalloc(0, dummy, 10, 2, 2, dummy, 33, 33, dummy, 33, None) == 2
 
 
 def test_create_without_gpu_fails_cleanly(lib):
