@@ -135,6 +135,27 @@ __device__ __forceinline__ void stage_rows(T* dst, const T* src, int64_t ld, int
     }
 }
 
+// The same with a destination row pitch (elements) larger than the width:
+// 16-byte copies need w and the pitch to be whole 16-byte pieces.
+template <class T>
+__device__ __forceinline__ void stage_rows_pitched(T* dst, int pitch, const T* src, int64_t ld, int w,
+                                                   int64_t base, int rows, int nr, bool vec16) {
+    if (vec16) {
+        const int pr = w * (int)sizeof(T) / 16;
+        for_each_rc(rows, pr, [&](int r, int q) {
+            const bool ok = r < nr;
+            cp_async16(reinterpret_cast<char*>(dst + r * pitch) + 16 * q,
+                       reinterpret_cast<const char*>(src + (ok ? (base + r) * ld : 0)) + 16 * q,
+                       ok ? 16 : 0);
+        });
+    } else {
+        for_each_rc(rows, w, [&](int r, int c) {
+            const bool ok = r < nr;
+            cp_async<sizeof(T)>(dst + r * pitch + c, src + (ok ? (base + r) * ld + c : 0), ok);
+        });
+    }
+}
+
 // Stage rows [base, base + nr) of X and Z (raw element types) into one buffer.
 template <class XT, class V>
 __device__ __forceinline__ void stage_chunk(XT* xr, V* zr, const XT* X, int64_t ldx, int d,
@@ -381,36 +402,36 @@ __global__ void mean_finalize_kernel(const typename Types<DT>::Wide* __restrict_
 }
 
 // ----------------------------------------------------------------- l2apply
-// Persistent CTAs over tiles of kApplyRows rows; each tile of X arrives by
-// cp.async into a double buffer while the previous tile is computed.  Thread
-// (row pair, column quad) accumulates s_i u + v - 2 (x_i - mu) . W.
-constexpr int kApplyRows = 128;
-
-template <dm_dtype DT, bool VST>
+// Persistent CTAs over tiles of R rows; each tile of X arrives by cp.async
+// into a double buffer (rows at a padded pitch: conflict-free reads) while
+// the previous tile is computed.  Thread (row quad, column quad) forms, in
+// one sweep over the coordinates, x_i - mu on the fly, its squared norm s_i
+// and -2 (x_i - mu) . W for four rows (q, q + R/4, q + R/2, q + 3R/4: the
+// items of a warp read consecutive rows) and four columns, then writes
+// s_i u + v - 2 (x_i - mu) . W.  XV4: rows are whole 16-byte pieces (read as
+// vectors at pitch d + 4, so eight consecutive rows fall in distinct banks);
+// otherwise scalar reads at pitch d + 1.
+template <dm_dtype DT, bool VST, bool XV4>
 __global__ void __launch_bounds__(kThreads)
 l2apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, int64_t ldx,
                const typename Types<DT>::V* __restrict__ mu,
                const typename Types<DT>::Wide* __restrict__ res, int k,
-               typename Types<DT>::Out* __restrict__ out, int64_t ldo, int xv16) {
+               typename Types<DT>::Out* __restrict__ out, int64_t ldo, int R) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Out = typename Types<DT>::Out;
-    constexpr int R = kApplyRows;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int DP = round4(d) + 4, KP = round4(k);   // DP: 16-byte rows, bank-spread
-    const int DR = round4(d);                         // columns read (zero padded)
+    const int XP = XV4 ? d + 4 : d + 1;
+    const int KP = round4(k), DR = round4(d);
+    auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
     size_t off = 0;
-    V* xraw = reinterpret_cast<V*>(smem_raw);                      // [2][R*d]
-    off += ((2 * (size_t)R * d * sizeof(V)) + 15) & ~size_t(15);
-    Acc* Wm2 = reinterpret_cast<Acc*>(smem_raw + off);             // -2 W, d x KP (zero padded)
-    off += (((size_t)d * KP * sizeof(Acc)) + 15) & ~size_t(15);
+    V* xraw = reinterpret_cast<V*>(smem_raw);                      // [2][R][XP]
+    off += up(2 * (size_t)R * XP * sizeof(V));
+    Acc* Wm2 = reinterpret_cast<Acc*>(smem_raw + off);             // -2 W, DR x KP (zero padded)
+    off += up((size_t)DR * KP * sizeof(Acc));
     Acc* uv = reinterpret_cast<Acc*>(smem_raw + off);              // u (KP), v (KP)
-    off += (((size_t)2 * KP * sizeof(Acc)) + 15) & ~size_t(15);
-    Acc* xt = reinterpret_cast<Acc*>(smem_raw + off);              // R x DP shifted rows
-    off += (((size_t)R * DP * sizeof(Acc)) + 15) & ~size_t(15);
-    Acc* mu_s = reinterpret_cast<Acc*>(smem_raw + off);
-    off += (((size_t)d * sizeof(Acc)) + 15) & ~size_t(15);
-    Acc* s_s = reinterpret_cast<Acc*>(smem_raw + off);             // R
+    off += up((size_t)2 * KP * sizeof(Acc));
+    Acc* mu_s = reinterpret_cast<Acc*>(smem_raw + off);            // DR (zero padded)
 
     for (int i = threadIdx.x; i < DR * KP; i += kThreads) {
         const int c = i / KP, j = i % KP;
@@ -420,19 +441,21 @@ l2apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, in
         const int h = i / KP, j = i % KP;
         uv[i] = j < k ? (Acc)res[d * k + h * k + j] : Acc(0);
     }
-    for (int c = threadIdx.x; c < d; c += kThreads) mu_s[c] = to_acc(mu[c], Acc());
+    for (int c = threadIdx.x; c < DR; c += kThreads) mu_s[c] = c < d ? to_acc(mu[c], Acc()) : Acc(0);
 
     const int64_t tiles = (n + R - 1) / R;
     auto stage = [&](int64_t tile, int buf) {
         const int64_t row0 = tile * R;
         const int nr = (int)min64(R, n - row0);
-        stage_rows(xraw + (size_t)buf * R * d, X, ldx, d, row0, R, nr, xv16 != 0);
+        stage_rows_pitched(xraw + (size_t)buf * R * XP, XP, X, ldx, d, row0, R, nr, XV4);
         cp_commit();
     };
     int64_t tile = blockIdx.x;
     if (tile < tiles) stage(tile, 0);
     int buf = 0;
-    const int QJ = KP / RJ;                           // column quads
+    const int QJ = KP / 4;                            // column quads
+    const int RQ = R / 4;                             // row quads; row h of quad q is q + h * RQ
+    const int items = RQ * QJ;
     for (; tile < tiles; tile += gridDim.x, buf ^= 1) {
         const int64_t next = tile + gridDim.x;
         if (next < tiles) { stage(next, buf ^ 1); cp_wait<1>(); }
@@ -440,53 +463,69 @@ l2apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int d, in
         __syncthreads();
         const int64_t row0 = tile * R;
         const int nr = (int)min64(R, n - row0);
-        const V* xr = xraw + (size_t)buf * R * d;
-        for_each_rc(R, DR, [&](int r, int c) {
-            xt[r * DP + c] = (r < nr && c < d) ? to_acc(xr[r * d + c], Acc()) - mu_s[c] : Acc(0);
-        });
-        __syncthreads();
-        for (int r = threadIdx.x >> 2; r < R; r += kThreads / 4) {
-            const Acc sq = row_sqnorm4(xt + r * DP, d, threadIdx.x & 3);
-            if ((threadIdx.x & 3) == 0) s_s[r] = sq;
-        }
-        __syncthreads();
-        for (int w = threadIdx.x; w < (R / 2) * QJ; w += kThreads) {
-            const int rp = w / QJ, jq = w % QJ;
-            const int ra = 2 * rp, jb = jq * RJ;
-            Acc acc[2][RJ], u4[RJ], v4[RJ];
-            load4(uv + jb, u4);
-            load4(uv + KP + jb, v4);
-            const Acc s0 = s_s[ra], s1 = s_s[ra + 1];
+        const V* xb = xraw + (size_t)buf * R * XP;
+        for (int it = threadIdx.x; it < items; it += kThreads) {
+            const int rq = it % RQ, jb = (it / RQ) * 4;
+            Acc acc[4][4], sq[4];
 #pragma unroll
-            for (int q = 0; q < RJ; ++q) {
-                acc[0][q] = fma_acc(s0, u4[q], v4[q]);
-                acc[1][q] = fma_acc(s1, u4[q], v4[q]);
+            for (int h = 0; h < 4; ++h) {
+                sq[h] = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[h][q] = 0;
             }
             for (int c0 = 0; c0 < DR; c0 += 4) {
-                Acc x0[4], x1[4];
-                load4(xt + ra * DP + c0, x0);
-                load4(xt + (ra + 1) * DP + c0, x1);
+                Acc xv[4][4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const V* xr = xb + (rq + h * RQ) * XP + c0;
+                    if constexpr (XV4) {
+                        V raw[4];
+                        const uint4 u = *reinterpret_cast<const uint4*>(xr);
+                        static_assert(sizeof(V) == 4 || !XV4 || true, "");
+                        if constexpr (sizeof(V) == 4) {
+                            memcpy(raw, &u, 16);
+                        } else {
+                            const uint4 u2 = *reinterpret_cast<const uint4*>(xr + 2);
+                            memcpy(raw, &u, 16);
+                            memcpy(raw + 2, &u2, 16);
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) xv[h][cc] = to_acc(raw[cc], Acc()) - mu_s[c0 + cc];
+                    } else {
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc)
+                            xv[h][cc] = c0 + cc < d ? to_acc(xr[cc], Acc()) - mu_s[c0 + cc] : Acc(0);
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) sq[h] = fma_acc(xv[h][cc], xv[h][cc], sq[h]);
+                }
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
-                    Acc wv[RJ];
+                    Acc wv[4];
                     load4(Wm2 + (c0 + cc) * KP + jb, wv);
 #pragma unroll
-                    for (int q = 0; q < RJ; ++q) {
-                        acc[0][q] = fma_acc(x0[cc], wv[q], acc[0][q]);
-                        acc[1][q] = fma_acc(x1[cc], wv[q], acc[1][q]);
-                    }
+                    for (int h = 0; h < 4; ++h)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[h][q] = fma_acc(xv[h][cc], wv[q], acc[h][q]);
                 }
             }
+            Acc u4[4], v4[4];
+            load4(uv + jb, u4);
+            load4(uv + KP + jb, v4);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (ra + h >= nr) break;
-                Out* o = out + (row0 + ra + h) * ldo + jb;
+            for (int h = 0; h < 4; ++h) {
+                const int r = rq + h * RQ;
+                if (r >= nr) continue;
+                Acc o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = fma_acc(sq[h], u4[q], v4[q]) + acc[h][q];
+                Out* dst = out + (row0 + r) * ldo + jb;
                 if constexpr (VST) {
-                    *reinterpret_cast<float4*>(o) = make_float4(acc[h][0], acc[h][1], acc[h][2], acc[h][3]);
+                    *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < RJ; ++q)
-                        if (jb + q < k) o[q] = (Out)acc[h][q];
+                    for (int q = 0; q < 4; ++q)
+                        if (jb + q < k) dst[q] = (Out)o[q];
                 }
             }
         }
@@ -624,15 +663,19 @@ cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* lau
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
     auto up = [](size_t x) { return (x + 15) & ~size_t(15); };
-    const int R = kApplyRows;
+    const bool xv4 = (a.d % 4 == 0) && rows16(a.X, a.ldx, a.d, sizeof(V));
+    const int XP = xv4 ? (int)a.d + 4 : (int)a.d + 1;
     const int KP = round4((int)a.k);
     const int DR = round4((int)a.d);
-    const size_t smem = up(2 * (size_t)R * a.d * sizeof(V)) + up((size_t)DR * KP * sizeof(Acc)) +
-                        up(2 * (size_t)KP * sizeof(Acc)) + up((size_t)R * (DR + 4) * sizeof(Acc)) +
-                        up((size_t)a.d * sizeof(Acc)) + (size_t)R * sizeof(Acc);
+    // Rows per tile: the double buffer within about 96 KB, a multiple of 4.
+    int R = (int)std::min<int64_t>(256, (96 * 1024) / (2 * (int64_t)XP * (int64_t)sizeof(V)));
+    R = std::max(4, R & ~3);
+    const size_t smem = up(2 * (size_t)R * XP * sizeof(V)) + up((size_t)DR * KP * sizeof(Acc)) +
+                        up(2 * (size_t)KP * sizeof(Acc)) + up((size_t)DR * sizeof(Acc));
     const bool vst = sizeof(Out) == 4 && a.k % 4 == 0 && a.ldo % 4 == 0 &&
                      reinterpret_cast<uintptr_t>(a.out) % 16 == 0;
-    auto kern = vst ? l2apply_kernel<DT, true> : l2apply_kernel<DT, false>;
+    auto kern = vst ? (xv4 ? l2apply_kernel<DT, true, true> : l2apply_kernel<DT, true, false>)
+                    : (xv4 ? l2apply_kernel<DT, false, true> : l2apply_kernel<DT, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -642,8 +685,7 @@ cudaError_t l2apply_launch_t(const L2ApplyArgs& a, cudaStream_t st, int64_t* lau
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(occ, 1) * num_sms));
     kern<<<(unsigned)blocks, kThreads, smem, st>>>(
         static_cast<const V*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const V*>(a.mu),
-        static_cast<const Wide*>(a.res), (int)a.k, static_cast<Out*>(a.out), a.ldo,
-        rows16(a.X, a.ldx, a.d, sizeof(V)) ? 1 : 0);
+        static_cast<const Wide*>(a.res), (int)a.k, static_cast<Out*>(a.out), a.ldo, R);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
     return cudaSuccess;
