@@ -458,20 +458,38 @@ grad_l2_apply_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int
     for (int e = threadIdx.x; e < K2; e += blockDim.x) u[e] = (Acc)res[(size_t)d * K2 + e];
     for (int e = threadIdx.x; e < d; e += blockDim.x) m[e] = to_a(mu[e], Acc());
     __syncthreads();
+    // U rows per warp step, every load of the step issued before the
+    // arithmetic (enough bytes in flight to keep HBM busy).
+    constexpr int U = 8;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = gw; i < n; i += nw) {
-        const V* pr = P + i * K2;
-        for (int c = lane; c < d; c += 32) {
-            const Acc xc = to_a(X[i * ldx + c], Acc()) - m[c];
-            Acc g = 0;
-            for (int q = 0; q < k; ++q) {
-                const Acc zq = to_a(pr[2 * q], Acc()), wq = to_a(pr[2 * q + 1], Acc());
-                g += xc * (wq * u[2 * q] + zq * u[2 * q + 1]) - wq * Y[c * K2 + 2 * q] -
-                     zq * Y[c * K2 + 2 * q + 1];
+    for (int64_t i0 = gw * U; i0 < n; i0 += nw * U) {
+        for (int c = lane; c - lane < d; c += 32) {
+            Acc xc[U];
+#pragma unroll
+            for (int u2 = 0; u2 < U; ++u2) {
+                const int64_t i = i0 + u2;
+                xc[u2] = (i < n && c < d) ? to_a(X[i * ldx + c], Acc()) - m[c] : Acc(0);
             }
-            G[i * ldg + c] = (Out)(2 * g);
+            Acc g[U];
+#pragma unroll
+            for (int u2 = 0; u2 < U; ++u2) g[u2] = 0;
+            for (int q = 0; q < k; ++q) {
+                const Acc yz = c < d ? Y[c * K2 + 2 * q] : Acc(0);
+                const Acc yw = c < d ? Y[c * K2 + 2 * q + 1] : Acc(0);
+#pragma unroll
+                for (int u2 = 0; u2 < U; ++u2) {
+                    const int64_t i = min64(i0 + u2, n - 1);
+                    const Acc zq = to_a(P[i * K2 + 2 * q], Acc()), wq = to_a(P[i * K2 + 2 * q + 1], Acc());
+                    g[u2] += xc[u2] * (wq * u[2 * q] + zq * u[2 * q + 1]) - wq * yz - zq * yw;
+                }
+            }
+#pragma unroll
+            for (int u2 = 0; u2 < U; ++u2) {
+                const int64_t i = i0 + u2;
+                if (i < n && c < d) G[i * ldg + c] = (Out)(2 * g[u2]);
+            }
         }
     }
 }
@@ -580,7 +598,7 @@ cudaError_t grad_l2_apply_t(const GradArgs& a, cudaStream_t s, int64_t* launches
     auto kern = grad_l2_apply_kernel<DT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t warps = a.n;
+    const int64_t warps = (a.n + 7) / 8;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + kGW - 1) / kGW, 8 * (int64_t)a.num_sms));
     kern<<<blocks, kGT, smem, s>>>(static_cast<const V*>(a.X), a.n, (int)a.d, a.ldx,
                                    static_cast<const V*>(a.mu), static_cast<const Wide*>(a.res), P,
