@@ -26,7 +26,8 @@ Three forms, all plain and slow on purpose:
 * ``tv_rows``, ``lpp_rows`` / ``lpp_even_expansion``, ``l2_embed`` /
   ``l2_approx`` -- the variants of Appendix A: total variation (half the l1
   product), ||x - y||_p^p by definition and by the even-p expansion, and the
-  approximate l2 product through the Gaussian l2 -> l1 embedding.
+  approximate l2 product through the Gaussian l2 -> l1 embedding; odd p
+  through the sorted order (``lpp_odd_sort``).
 * ``l2sq_identity`` -- the p = 2 query of Appendix A (Theorem
   "l2_squared_upper_bound"), with the typos of the printed algorithm read as
   the proof's Gram decomposition (Section 1.2): (Ay)_k = ||x_k||^2 sum_j y_j
@@ -394,6 +395,51 @@ def lpp_even_expansion(X, Z, p: int) -> np.ndarray:
         for t in range(p + 1):
             S = comb(p, t) * (((-x) ** (p - t))[None, :] @ Z)      # 1 x k
             out += (x ** t)[:, None] * S
+    return out[:, 0] if squeeze else out
+
+
+def lpp_odd_sort(X, Z, p: int) -> np.ndarray:
+    """||x - y||_p^p for odd p through the sorted order (Theorem "odd_p":
+    the p = 1 technique with p + 1 prefix sums per coordinate).  For the
+    point at sorted position r of coordinate i, inside the tie group a..b,
+    with sums over the strictly smaller (L) and strictly larger (R) values,
+        sum_j y_j |x - x_j|^p = sum_t C(p, t) x^t (L_{p-t} - R_{p-t}),
+        L_s = sum_{x_j < x} y_j (-x_j)^s,  R_s = sum_{x_j > x} y_j (-x_j)^s
+    (ties contribute |0|^p = 0).  FP64 / int64."""
+    if p % 2 == 0:
+        raise ValueError("p must be odd")
+    from math import comb
+    X = np.asarray(X)
+    Z = np.asarray(Z)
+    if X.ndim == 1:
+        X = X[:, None]
+    squeeze = Z.ndim == 1
+    if squeeze:
+        Z = Z[:, None]
+    integer = _is_int(X) and _is_int(Z)
+    dt = np.int64 if integer else np.float64
+    X = X.astype(dt)
+    Z = Z.astype(dt)
+    n, d = X.shape
+    out = np.zeros((n, Z.shape[1]), dtype=dt)
+    for i in range(d):
+        order = preprocessing_order(X[:, i])
+        xs = X[order, i]
+        head = np.ones(n, dtype=bool)
+        head[1:] = xs[1:] != xs[:-1]
+        gid = np.cumsum(head) - 1
+        first = np.flatnonzero(head)
+        last = np.append(first[1:] - 1, n - 1)
+        a, b = first[gid], last[gid]
+        ys = Z[order]
+        acc = np.zeros_like(ys)
+        for t in range(p + 1):
+            w = ys * ((-xs) ** (p - t))[:, None]
+            inc = np.cumsum(w, axis=0)
+            exc = inc - w
+            S = exc[a] - (inc[-1][None, :] - inc[b])
+            acc += comb(p, t) * (xs ** t)[:, None] * S
+        out[order] += acc
     return out[:, 0] if squeeze else out
 
 

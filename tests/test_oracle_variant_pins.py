@@ -107,3 +107,28 @@ def test_embedding_norm_and_matrix_error():
     Tb = oracle.l2_embed(X, G) * np.sqrt(2 / np.pi)
     B_wrong = oracle.l1_sort(Tb, np.eye(120))
     assert np.linalg.norm(B_wrong - exact) / np.linalg.norm(exact) > 0.15
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_odd_p_sorted_form_matches_definition(p):
+    rng = np.random.default_rng(p + 40)
+    X = rng.integers(-20, 20, size=(90, 3))          # many ties
+    Z = rng.integers(-9, 10, size=(90, 2))
+    np.testing.assert_array_equal(oracle.lpp_odd_sort(X, Z, p), oracle.lpp_rows(X, Z, p))
+    Xf = rng.normal(size=(90, 3))
+    Zf = rng.normal(size=(90, 2))
+    assert oracle.relative_error(oracle.lpp_odd_sort(Xf, Zf, p), oracle.lpp_rows(Xf, Zf, p)) < 1e-12
+    if p == 1:
+        np.testing.assert_array_equal(oracle.lpp_odd_sort(X, Z, 1), oracle.l1_rows(X, Z))
+
+
+def test_odd_p_grid_closed_form():
+    # sum_{m=1}^{N} m^3 = (N (N + 1) / 2)^2
+    n = 400
+    X = np.arange(n).reshape(n, 1)
+    i = np.arange(n)
+    cube = lambda N: (N * (N + 1) // 2) ** 2
+    want = cube(i) + cube(n - 1 - i)
+    np.testing.assert_array_equal(oracle.lpp_odd_sort(X, np.ones(n, dtype=np.int64), 3), want)
+    np.testing.assert_array_equal(oracle.lpp_rows(X, np.ones(n, dtype=np.int64), 3), want)
+
