@@ -55,7 +55,7 @@ typedef enum {
 typedef enum { DM_F32 = 0, DM_F64 = 1, DM_I32 = 2 } dm_dtype;
 /* DM_L1: ||x - y||_1 (Section 2).  DM_L2SQ: ||x - y||_2^2 (Appendix A).
  * DM_TV: total variation of distributions, ||x - y||_1 / 2 (Appendix A,
- * Theorem "tv"; FP32/FP64 only).  DM_LPP: ||x - y||_p^p for an even p
+ * Theorem "tv"; FP32/FP64 only).  DM_LPP: ||x - y||_p^p, 2 <= p <= 16
  * (Appendix A, "General p"; plans from dm_prepare_lpp).  DM_L2_EMBED: the
  * approximate ||x - y||_2 of Appendix A (plans from dm_prepare_l2_embed). */
 typedef enum { DM_L1 = 0, DM_L2SQ = 1, DM_TV = 2, DM_LPP = 3, DM_L2_EMBED = 4 } dm_metric;
@@ -105,16 +105,27 @@ dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* 
 /* (dm_prepare takes DM_L1, DM_L2SQ and DM_TV; DM_TV plans are l1 plans whose
  * products and gradients are halved.) */
 
-/* ||x - y||_p^p plan for an even p, 2 <= p <= 16 (Appendix A, "General p";
- * the printed query is read with the binomial coefficients C(p, t) and the
- * weights y_j, t = 0..p): the plan records X (kept alive by the caller, as
- * for DM_L2SQ) and its column means; dm_matmat forms the moments
+/* ||x - y||_p^p plan, 2 <= p <= 16 (Appendix A, "General p").
+ *
+ * Even p (the printed query read with the binomial coefficients C(p, t) and
+ * the weights y_j, t = 0..p): the plan records X (kept alive by the caller,
+ * as for DM_L2SQ) and its column means; dm_matmat forms the moments
  * sum_j y_j (x_j(c) - mu_c)^s, s = 0..p, and evaluates
  * (Ay)_k = sum_c sum_t C(p,t) (-1)^(p-t) (x_k(c) - mu_c)^t M_{c,p-t}.
+ * DM_ERR_UNSUPPORTED when d * p exceeds what one reduce launch holds.
+ *
+ * Odd p, 3 <= p <= 15 (Theorem "odd_p"): the plan is an l1 plan (sorted
+ * coordinates, Algorithm 1; X is not kept).  With x~ = x - m_c, m_c the
+ * coordinate's median, and for the point at sorted position r inside the tie
+ * group a..b, dm_matmat evaluates
+ *     sum_j y_j |x~ - x~_j|^p = sum_s C(p, s) x~^(p-s) (L_s - R_s),
+ * L_s / R_s the sums of y_j (-x~_j)^s over the strictly smaller / larger
+ * values (prefix sums in sorted order, p + 1 per query column).  The result
+ * block is written with atomic adds (summation order not fixed).
+ *
  * Exact for DM_I32 when the result fits in int64 (wrap-around arithmetic).
- * The expansion cancels more as p grows; on centred Gaussian data FP32
- * results stayed near 1e-7 relative up to p = 8.
- * DM_ERR_UNSUPPORTED when d * p exceeds what one reduce launch holds. */
+ * Both expansions cancel more as p grows; on centred Gaussian data FP32
+ * results stayed near 1e-7 relative up to p = 8 (even). */
 dm_status dm_prepare_lpp(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, int64_t d,
                          int64_t ldx, int p, dm_plan** plan);
 
@@ -212,10 +223,11 @@ dm_status dm_sync(dm_ctx* ctx);
 /* Static, human-readable name of a status code. */
 const char* dm_status_string(dm_status status);
 
-/* Copy an l1 plan's sorted coordinates (d x n, element type of the plan) and
+/* Copy a sorted plan's coordinates (d x n, element type of the plan) and
  * sorting permutation (d x n int32; row c lists the point indices in
  * ascending order of coordinate c, ties in index order) into caller device
- * buffers.  DM_ERR_INVALID_ARG for a squared-l2 plan. */
+ * buffers.  Sorted plans: DM_L1, DM_TV, DM_L2_EMBED (the mapped points) and
+ * DM_LPP with odd p.  DM_ERR_INVALID_ARG for the others. */
 dm_status dm_plan_export(dm_plan* plan, void* sorted_values, int32_t* perm);
 
 /* The plain method: out = A Z with every entry f(x_i, x_j) computed on the
@@ -243,7 +255,8 @@ int64_t dm_launch_count(const dm_ctx* ctx);
  * "l1_aggregate", "l1_query", "l1_finalize", "l2_prepare", "l2_reduce",
  * "l2_apply", "bruteforce", "grad_pack", "grad_l1_tiles", "grad_l1_scan",
  * "grad_l1_eval", "grad_l1_transpose", "grad_l2_reduce", "grad_l2_apply",
- * "tv_scale", "lpp_features", "lpp_reduce", "lpp_apply", "l2_embed_project") is
+ * "tv_scale", "lpp_features", "lpp_reduce", "lpp_apply", "lpp_odd_tiles",
+ * "lpp_odd_scan", "lpp_odd_eval", "l2_embed_project") is
  * bracketed by two CUDA events
  * recorded on the context's stream.  Enabling (or disabling) clears what was
  * collected.  Off by default; costs two event records per group. */

@@ -215,7 +215,9 @@ def dm_prepare(ctx: Context, metric, X) -> Plan:
 
 
 def dm_prepare_lpp(ctx: Context, X, p: int) -> Plan:
-    """dm_prepare_lpp: ||x - y||_p^p plan (even p) on a CUDA tensor X (n x d)."""
+    """dm_prepare_lpp: ||x - y||_p^p plan on a CUDA tensor X (n x d): even p
+    2..16 through moments of the centred coordinates, odd p 3..15 through
+    the sorted coordinates."""
     if X.ndim == 1:
         X = X.reshape(-1, 1)
     code = dtype_code(X.dtype)

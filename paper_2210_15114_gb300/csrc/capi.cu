@@ -2,6 +2,7 @@
 // the launch sequences of each call.  Host code only; kernels live in the
 // other translation units.
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -61,7 +62,7 @@ struct dm_plan {
     const void* X = nullptr;
     int64_t ldx = 0;
     void* mu = nullptr;
-    int p = 0;                    // DM_LPP: the even power
+    int p = 0;                    // DM_LPP: the power (even: moments plan, odd: sorted plan)
     int64_t d_in = 0;             // DM_L2_EMBED: dimension of the input points (d is m)
 };
 
@@ -451,7 +452,11 @@ int64_t l2_chunk(const dm_plan* p, int64_t k) {
     return std::min<int64_t>(k, reduce_max_k(p->dtype, p->d));
 }
 
+// ||x - y||_p^p with odd p runs on the sorted coordinates of an l1 plan.
+bool lpp_odd(const dm_plan* p) { return p->metric == DM_LPP && (p->p & 1); }
+
 size_t matmat_scratch(const dm_plan* p, int64_t k) {
+    if (lpp_odd(p)) return oddp_scratch_bytes(p->n, p->d, k, p->p);
     if (sorted_metric(p->metric)) return l1_query_scratch_bytes(p->dtype, p->n, p->d, k, p->ctx->num_sms);
     size_t feat = 0;
     int64_t D = p->d;
@@ -510,6 +515,31 @@ dm_status lpp_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t l
     return DM_OK;
 }
 
+// ||x - y||_p^p for odd p (Theorem "odd_p"): out is zeroed, then the tile
+// sums of the p + 1 weights per column, the scan over tiles and the
+// evaluation, which adds every coordinate's share into out.
+dm_status lpp_odd_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out,
+                      int64_t ldo) {
+    dm_ctx* ctx = e.ctx;
+    const size_t es = out_size(p->dtype);
+    DM_TRY_CUDA(ldo == k ? cudaMemsetAsync(out, 0, (size_t)p->n * k * es, e.stream)
+                         : cudaMemset2DAsync(out, (size_t)ldo * es, 0, (size_t)k * es, (size_t)p->n, e.stream));
+    OddArgs a{};
+    a.dtype = p->dtype;
+    a.n = p->n; a.d = p->d;
+    a.xs = p->xs; a.perm = p->perm;
+    a.Z = Z; a.ldz = ldz; a.k = k;
+    a.p = p->p;
+    a.out = out; a.ldo = ldo;
+    a.scratch = e.scratch;
+    static const char* const names[3] = {"lpp_odd_tiles", "lpp_odd_scan", "lpp_odd_eval"};
+    for (int stage = 0; stage < 3; ++stage) {
+        ProfScope ps(e, names[stage]);
+        DM_TRY_CUDA(oddp_launch(a, stage, e.stream, &ctx->launches));
+    }
+    return DM_OK;
+}
+
 dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out,
                      int64_t ldo) {
     dm_ctx* ctx = e.ctx;
@@ -517,6 +547,7 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
     const int64_t n = p->n, d = p->d;
     if (e.scratch_bytes < matmat_scratch(p, k)) return DM_ERR_INTERNAL;
 
+    if (lpp_odd(p)) return lpp_odd_run(e, p, Z, k, ldz, out, ldo);
     if (p->metric == DM_LPP) return lpp_run(e, p, Z, k, ldz, out, ldo);
     if (sorted_metric(p->metric)) {
         // R^T Z, 1^T Z and the group-major copy of Z, then the sorted part
@@ -593,8 +624,12 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
 
 dm_status matmat_impl(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out, int64_t ldo) {
     if (p->metric == DM_L2SQ && l2_chunk(p, k) < 1) return DM_ERR_UNSUPPORTED;
-    if (p->metric == DM_LPP && reduce_max_k(p->dtype, p->d * p->p) < 1) return DM_ERR_UNSUPPORTED;
-    if (p->metric == DM_LPP && lpp_apply_smem(p->dtype, p->d, p->p, std::min<int64_t>(k, reduce_max_k(p->dtype, p->d * p->p))) > 200 * 1024)
+    const bool even = p->metric == DM_LPP && !lpp_odd(p);
+    if (even && reduce_max_k(p->dtype, p->d * p->p) < 1) return DM_ERR_UNSUPPORTED;
+    if (lpp_odd(p) && (p->d * (p->p + 1) * k > INT_MAX ||
+                       p->d * ((p->n + 1023) / 1024) > INT_MAX))
+        return DM_ERR_UNSUPPORTED;
+    if (even && lpp_apply_smem(p->dtype, p->d, p->p, std::min<int64_t>(k, reduce_max_k(p->dtype, p->d * p->p))) > 200 * 1024)
         return DM_ERR_UNSUPPORTED;
     DM_TRY(ensure_arena(p->ctx, matmat_scratch(p, k)));
     return matmat_run(ctx_exec(p->ctx), p, Z, k, ldz, out, ldo);
@@ -1009,15 +1044,19 @@ dm_status dm_prepare_lpp(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, 
                          int pw, dm_plan** plan) {
     if (!plan) return DM_ERR_INVALID_ARG;
     *plan = nullptr;
-    if (!ctx || !X || !valid_dtype(dtype) || pw < 2 || pw > 16 || (pw & 1)) return DM_ERR_INVALID_ARG;
+    const bool odd = (pw & 1) != 0;
+    if (!ctx || !X || !valid_dtype(dtype) || pw < 2 || pw > (odd ? 15 : 16)) return DM_ERR_INVALID_ARG;
     if (n < 1 || n > kMaxN || d < 1 || ldx < d) return DM_ERR_INVALID_ARG;
-    if ((double)n * (double)d * pw >= 2147483648.0) return DM_ERR_UNSUPPORTED;
-    if (reduce_max_k(dtype, d * pw) < 1 || lpp_apply_smem(dtype, d, pw, 1) > 200 * 1024) return DM_ERR_UNSUPPORTED;
+    if (odd && (double)n * (double)d >= 2147483648.0) return DM_ERR_UNSUPPORTED;
+    if (!odd && (double)n * (double)d * pw >= 2147483648.0) return DM_ERR_UNSUPPORTED;
+    if (!odd && (reduce_max_k(dtype, d * pw) < 1 || lpp_apply_smem(dtype, d, pw, 1) > 200 * 1024))
+        return DM_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
     dm_plan* p = new (std::nothrow) dm_plan();
     if (!p) return DM_ERR_OOM;
     p->ctx = ctx; p->metric = DM_LPP; p->dtype = dtype; p->n = n; p->d = d; p->p = pw;
-    const dm_status s = prepare_l2(ctx, p, X, ldx);     // records X, column means mu
+    // even p: X and its column means; odd p: the sorted coordinates (Algorithm 1)
+    const dm_status s = odd ? prepare_l1(ctx, p, X, ldx) : prepare_l2(ctx, p, X, ldx);
     if (s != DM_OK) {
         cudaStreamSynchronize(ctx->stream);
         cudaGetLastError();
@@ -1182,7 +1221,7 @@ dm_status dm_sync(dm_ctx* ctx) {
 }
 
 dm_status dm_plan_export(dm_plan* p, void* sorted_values, int32_t* perm) {
-    if (!p || !sorted_metric(p->metric) || !sorted_values || !perm) return DM_ERR_INVALID_ARG;
+    if (!p || !(sorted_metric(p->metric) || lpp_odd(p)) || !sorted_values || !perm) return DM_ERR_INVALID_ARG;
     DeviceGuard g(p->ctx->device);
     const size_t nd = (size_t)p->n * (size_t)p->d;
     DM_TRY_CUDA(cudaMemcpyAsync(sorted_values, p->xs, nd * dtype_size(p->dtype),

@@ -189,6 +189,21 @@ cudaError_t grad_pack_launch(const GradArgs& a, cudaStream_t s, int64_t* launche
 cudaError_t grad_l1_launch(const GradArgs& a, int stage, cudaStream_t s, int64_t* launches);
 cudaError_t grad_l2_apply_launch(const GradArgs& a, cudaStream_t s, int64_t* launches);
 
+// ||x - y||_p^p for odd p through the sorted order (grad.cu): stage 0 tile
+// sums of the p + 1 weights y (-x~)^s, 1 scan over tiles, 2 evaluation,
+// added into out (which the caller zeroes first).
+struct OddArgs {
+    dm_dtype dtype;
+    int64_t n, d;
+    const void* xs; const int32_t* perm;  // the l1 plan's sorted coordinates
+    const void* Z; int64_t ldz; int64_t k;
+    int p;                                // odd, 3..15
+    void* out; int64_t ldo;
+    void* scratch;                        // oddp_scratch_bytes()
+};
+size_t oddp_scratch_bytes(int64_t n, int64_t d, int64_t k, int p);
+cudaError_t oddp_launch(const OddArgs& a, int stage, cudaStream_t s, int64_t* launches);
+
 // Variants (variants.cu).
 cudaError_t scale_launch(dm_dtype t, void* out, int64_t n, int64_t k, int64_t ldo, double s,
                          int num_sms, cudaStream_t st, int64_t* launches);

@@ -341,6 +341,188 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
     }
 }
 
+// ||x - y||_p^p for odd p (Theorem "odd_p"), on the same tiling: with
+// x~ = x - median (translation invariance), for the point at sorted position r
+// in the tie group a..b,
+//     sum_j y_j |x~ - x~_j|^p = sum_s C(p, s) x~^(p-s) S_s,
+//     S_s = E_s(a) + I_s(b) - T_s over the weights y (-x~)^s, s = 0..p
+// (E, I, T as for the gradient; ties contribute nothing).  The p + 1 weights
+// of each query column are scanned two at a time; each coordinate's share is
+// added into out with an atomic add.
+template <dm_dtype DT>
+struct OddParams {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Wide = typename Types<DT>::Wide;
+    using Out = typename Types<DT>::Out;
+    const V* xs; const int32_t* perm; int64_t n; int d;
+    const V* Z; int64_t ldz; int k; int pw;   // pw: the odd power
+    int64_t T;
+    int4* flags;
+    Wide* summ;                 // d x T x Q x 3, Q = k (pw + 1)
+    const Acc* cst;             // d x T x Q x 4
+    Out* out; int64_t ldo;
+    Acc coef[16];               // C(pw, s), s = 0..pw
+};
+
+__device__ __forceinline__ void out_add(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void out_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void out_add(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+template <dm_dtype DT, bool EVAL, bool VEC>
+__global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Wide = typename Types<DT>::Wide;
+    __shared__ Acc Ia[EVAL ? kGTile : 1], Ib[EVAL ? kGTile : 1];
+    __shared__ Acc ws[128];
+    __shared__ int wsi[32];
+    __shared__ int red[4];
+
+    const int c = (int)(blockIdx.x / p.T);
+    const int64_t t = blockIdx.x - (int64_t)c * p.T;
+    const int64_t ts = t * kGTile;
+    const int valid = (int)min64(kGTile, p.n - ts);
+    const int base = threadIdx.x * kGI;
+    const V* xc = p.xs + (int64_t)c * p.n + ts;
+    const int32_t* pc = p.perm + (int64_t)c * p.n + ts;
+    const Acc med = to_a(p.xs[(int64_t)c * p.n + p.n / 2], Acc());
+
+    V x[kGI];
+    int32_t pi[kGI];
+    load_items<V, VEC>(xc, valid, base, x);
+    load_items<int32_t, VEC>(pc, valid, base, pi);
+    const V prevv = (ts + base > 0 && base < valid) ? xc[base - 1] : x[0];
+    const V nextv = (ts + base + kGI < p.n) ? xc[base + kGI] : x[kGI - 1];
+
+    bool hd[kGI], en[kGI];
+#pragma unroll
+    for (int j = 0; j < kGI; ++j) {
+        const bool in = base + j < valid;
+        const int64_t r = ts + base + j;
+        const V left = j > 0 ? x[j - 1] : prevv;
+        const V right = j + 1 < kGI ? x[j + 1] : nextv;
+        hd[j] = in && (r == 0 || x[j] != left);
+        en[j] = in && (r == p.n - 1 || x[j] != right);
+    }
+    int lh = -1, fe = kNone;
+#pragma unroll
+    for (int j = 0; j < kGI; ++j) if (hd[j]) lh = base + j;
+#pragma unroll
+    for (int j = kGI - 1; j >= 0; --j) if (en[j]) fe = base + j;
+    int a[kGI], b[kGI];
+    int last_head, first_end;
+    {
+        int run = block_excl_max(lh, wsi, &last_head);
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) { if (hd[j]) run = base + j; a[j] = run; }
+        run = block_excl_suffix_min(fe, wsi, &first_end);
+#pragma unroll
+        for (int j = kGI - 1; j >= 0; --j) { if (en[j]) run = base + j; b[j] = run; }
+    }
+    if (!EVAL) {
+        int fh = kNone, le = -1;
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) {
+            if (hd[j]) fh = min(fh, base + j);
+            if (en[j]) le = max(le, base + j);
+        }
+        if (threadIdx.x == 0) { red[0] = kNone; red[1] = -1; }
+        __syncthreads();
+        if (fh != kNone) atomicMin(&red[0], fh);
+        if (le >= 0) atomicMax(&red[1], le);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            p.flags[(int64_t)c * p.T + t] = make_int4(red[0], last_head, first_end, red[1]);
+    }
+
+    const int P1 = p.pw + 1;
+    const int Q = p.k * P1;
+    Acc xt[kGI];
+#pragma unroll
+    for (int j = 0; j < kGI; ++j) xt[j] = base + j < valid ? to_a(x[j], Acc()) - med : Acc(0);
+
+    for (int q = 0; q < p.k; ++q) {
+        Acc y[kGI];
+#pragma unroll
+        for (int j = 0; j < kGI; ++j)
+            y[j] = base + j < valid ? to_a(p.Z[(int64_t)pi[j] * p.ldz + q], Acc()) : Acc(0);
+        Acc g[kGI];
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) g[j] = Acc(0);
+        // weights y (-x~)^s for s = s0, s0 + 1, pair by pair
+        Acc pwa[kGI];                          // (-x~)^s0
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) pwa[j] = Acc(1);
+        for (int s0 = 0; s0 < P1; s0 += 2) {
+            Acc va[kGI], vb[kGI], ia[kGI], ib[kGI];
+#pragma unroll
+            for (int j = 0; j < kGI; ++j) {
+                va[j] = y[j] * pwa[j];
+                vb[j] = -va[j] * xt[j];
+            }
+            Acc sa = 0, sb = 0;
+#pragma unroll
+            for (int j = 0; j < kGI; ++j) { sa += va[j]; sb += vb[j]; ia[j] = sa; ib[j] = sb; }
+            Acc oa = sa, ob = sb, ta, tb;
+            block_excl_sum2(oa, ob, ws, ta, tb);
+#pragma unroll
+            for (int j = 0; j < kGI; ++j) { ia[j] += oa; ib[j] += ob; }
+            const int64_t slot = ((int64_t)c * p.T + t) * Q + (int64_t)q * P1 + s0;
+            if (!EVAL) {
+                Wide* sm = p.summ + slot * 3;
+                if (threadIdx.x == 0) {
+                    if (last_head < 0) { sm[1] = 0; sm[4] = 0; }
+                    if (first_end == kNone) { sm[2] = 0; sm[5] = 0; }
+                }
+                Acc v0 = 0, v1 = 0, h0 = 0, h1 = 0, f0 = 0, f1 = 0;
+                bool hv = false, hh = false, hf = false;
+#pragma unroll
+                for (int j = 0; j < kGI; ++j) {
+                    if (base + j == valid - 1) { v0 = ia[j]; v1 = ib[j]; hv = true; }
+                    if (base + j == last_head) { h0 = ia[j] - va[j]; h1 = ib[j] - vb[j]; hh = true; }
+                    if (base + j == first_end) { f0 = ia[j]; f1 = ib[j]; hf = true; }
+                }
+                if (hv) { sm[0] = (Wide)v0; sm[3] = (Wide)v1; }
+                if (hh) { sm[1] = (Wide)h0; sm[4] = (Wide)h1; }
+                if (hf) { sm[2] = (Wide)f0; sm[5] = (Wide)f1; }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kGI; ++j) { Ia[base + j] = ia[j]; Ib[base + j] = ib[j]; }
+                __syncthreads();
+                const Acc* ka = p.cst + slot * 4;
+                const Acc* kb = ka + 4;
+                const Acc ca = p.coef[s0], cb = p.coef[s0 + 1];
+#pragma unroll
+                for (int j = 0; j < kGI; ++j) {
+                    if (base + j >= valid) continue;
+                    const bool ain = a[j] >= 0, bin = b[j] != kNone;
+                    Acc S0 = ain ? (bin ? ka[3] : ka[2]) : (bin ? ka[1] : ka[0]);
+                    Acc S1 = ain ? (bin ? kb[3] : kb[2]) : (bin ? kb[1] : kb[0]);
+                    if (ain && a[j] > 0) { S0 += Ia[a[j] - 1]; S1 += Ib[a[j] - 1]; }
+                    if (bin) { S0 += Ia[b[j]]; S1 += Ib[b[j]]; }
+                    // C(p, s) x~^(p - s) S_s for s = s0 and s0 + 1
+                    Acc e1 = 1;
+                    for (int u = 0; u < p.pw - s0 - 1; ++u) e1 *= xt[j];
+                    const Acc e0 = e1 * xt[j];
+                    g[j] += ca * e0 * S0 + cb * e1 * S1;
+                }
+                __syncthreads();
+            }
+            // next pair: (-x~)^(s0 + 2)
+#pragma unroll
+            for (int j = 0; j < kGI; ++j) pwa[j] *= xt[j] * xt[j];
+        }
+        if (EVAL) {
+#pragma unroll
+            for (int j = 0; j < kGI; ++j)
+                if (base + j < valid) out_add(p.out + (int64_t)pi[j] * p.ldo + q, (typename Types<DT>::Out)g[j]);
+        }
+    }
+}
+
 // One block per (coordinate, column, z or w): forward scan of the tile sums
 // (tile prefixes, E at the head of the group entering each tile), then a
 // backward scan (I at the end of the group leaving each tile).
@@ -607,7 +789,85 @@ cudaError_t grad_l2_apply_t(const GradArgs& a, cudaStream_t s, int64_t* launches
     return cudaGetLastError();
 }
 
+struct OddLayout {
+    int64_t T, Q;
+    size_t flags, summ, pre, cst, total;
+};
+
+OddLayout oddp_layout(int64_t n, int64_t d, int64_t k, int pw) {
+    OddLayout L;
+    L.T = (n + kGTile - 1) / kGTile;
+    L.Q = k * (pw + 1);
+    const size_t dt = (size_t)(d * L.T);
+    L.flags = 0;
+    L.summ = al256(16 * dt);
+    L.pre = al256(L.summ + 8 * 3 * (size_t)L.Q * dt);
+    L.cst = al256(L.pre + 8 * 3 * (size_t)L.Q * dt);
+    L.total = al256(L.cst + 8 * 4 * (size_t)L.Q * dt);
+    return L;
+}
+
+template <dm_dtype DT>
+cudaError_t oddp_stage_t(const OddArgs& a, int stage, cudaStream_t s, int64_t* launches) {
+    using V = typename Types<DT>::V;
+    using Acc = typename Types<DT>::Acc;
+    using Wide = typename Types<DT>::Wide;
+    using Out = typename Types<DT>::Out;
+    const OddLayout L = oddp_layout(a.n, a.d, a.k, a.p);
+    unsigned char* sc = static_cast<unsigned char*>(a.scratch);
+    OddParams<DT> p;
+    p.xs = static_cast<const V*>(a.xs);
+    p.perm = a.perm;
+    p.n = a.n;
+    p.d = (int)a.d;
+    p.Z = static_cast<const V*>(a.Z);
+    p.ldz = a.ldz;
+    p.k = (int)a.k;
+    p.pw = a.p;
+    p.T = L.T;
+    p.flags = reinterpret_cast<int4*>(sc + L.flags);
+    p.summ = reinterpret_cast<Wide*>(sc + L.summ);
+    p.cst = reinterpret_cast<const Acc*>(sc + L.cst);
+    p.out = static_cast<Out*>(a.out);
+    p.ldo = a.ldo;
+    long long cb = 1;
+    for (int t = 0; t < 16; ++t) {
+        p.coef[t] = t <= a.p ? (Acc)cb : Acc(0);
+        if (t < a.p) cb = cb * (a.p - t) / (t + 1);
+    }
+    const int64_t blocks = a.d * L.T;
+    if (blocks > INT_MAX || L.Q * a.d > INT_MAX) return cudaErrorInvalidConfiguration;
+    const bool vec = (a.n % (16 / (int64_t)sizeof(V))) == 0 && (a.n % 4) == 0 &&
+                     reinterpret_cast<uintptr_t>(a.xs) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(a.perm) % 16 == 0;
+    if (stage == 0) {
+        if (vec) oddp_tile_kernel<DT, false, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        else oddp_tile_kernel<DT, false, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+    } else if (stage == 1) {
+        grad_scan_kernel<Wide, Acc><<<(unsigned)(a.d * L.Q), kGT, 0, s>>>(
+            p.flags, p.summ, reinterpret_cast<Wide*>(sc + L.pre), reinterpret_cast<Acc*>(sc + L.cst),
+            a.n, L.T, (int)L.Q);
+    } else {
+        if (vec) oddp_tile_kernel<DT, true, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        else oddp_tile_kernel<DT, true, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+    }
+    *launches += 1;
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t oddp_scratch_bytes(int64_t n, int64_t d, int64_t k, int p) {
+    return oddp_layout(n, d, k, p).total;
+}
+
+cudaError_t oddp_launch(const OddArgs& a, int stage, cudaStream_t s, int64_t* launches) {
+    switch (a.dtype) {
+        case DM_F32: return oddp_stage_t<DM_F32>(a, stage, s, launches);
+        case DM_F64: return oddp_stage_t<DM_F64>(a, stage, s, launches);
+        default: return oddp_stage_t<DM_I32>(a, stage, s, launches);
+    }
+}
 
 size_t grad_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k) {
     return grad_layout(t, n, d, k).total;

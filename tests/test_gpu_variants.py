@@ -1,7 +1,8 @@
 """The variants of Appendix A on the GPU against the CPU oracle:
 total variation (half the l1 product, and half its gradient), ||x - y||_p^p
-for even p (the binomial expansion on centred coordinates), and the
-approximate l2 product through the Gaussian l2 -> l1 embedding.
+for even p (the binomial expansion on centred coordinates) and odd p (p + 1
+prefix sums in sorted order, Theorem "odd_p"), and the approximate l2
+product through the Gaussian l2 -> l1 embedding.
 
 FP32 within 1e-5 and FP64 within 1e-12 of the oracle on the same inputs
 (for the embedding: the oracle's FP64 map of the same FP32 points and G),
@@ -69,13 +70,13 @@ def test_tv_rejects_integers(dm, ctx):
 
 
 # --------------------------------------------------------------- ||.||_p^p
-@pytest.mark.parametrize("p", [2, 4, 6])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int32])
 @pytest.mark.parametrize("n", [1, 257, 4000])
 def test_lpp_matches_definition(dm, ctx, p, dtype, n):
     rng = np.random.default_rng(p * 100 + n)
     if dtype == np.int32:
-        hi = {2: 1 << 15, 4: 1000, 6: 100}[p]
+        hi = {2: 1 << 15, 3: 3000, 4: 1000, 5: 200, 6: 100, 7: 20}[p]
         X = rng.integers(-hi, hi, size=(n, 5)).astype(dtype)
         Z = rng.integers(-100, 101, size=(n, 3)).astype(dtype)
     else:
@@ -96,9 +97,51 @@ def test_lpp_p2_equals_l2sq_plan(dm, ctx):
     assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("p", [3, 5])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64, np.int32])
+def test_lpp_odd_ties_across_tiles(dm, ctx, p, dtype):
+    # four distinct values per coordinate: tie groups of about 1500 points
+    # that span several 1024-position tiles; ties contribute |0|^p = 0
+    rng = np.random.default_rng(31 + p)
+    n = 6003
+    X = rng.integers(-2, 2, size=(n, 4)).astype(dtype)
+    X[:, 3] = 7                                   # one coordinate all tied
+    Z = (rng.integers(-50, 51, size=(n, 5)) if dtype == np.int32
+         else rng.normal(size=(n, 5))).astype(dtype)
+    plan = dm.dm_prepare_lpp(ctx, dev(X), p)
+    out = dm.dm_matmat(plan, dev(Z))
+    dm.dm_sync(ctx)
+    check(out.cpu().numpy(), oracle.lpp_rows(X, Z, p), dtype)
+
+
+def test_lpp_odd_strided_output(dm, ctx):
+    # out is a column slice of a wider block (ldo > k): the columns outside
+    # the slice are left as they were
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(2500, 6)).astype(np.float64)
+    Z = rng.normal(size=(2500, 3))
+    big = torch.full((2500, 8), 3.5, dtype=torch.float64, device="cuda")
+    plan = dm.dm_prepare_lpp(ctx, dev(X), 3)
+    dm.dm_matmat(plan, dev(Z), out=big[:, 2:5])
+    dm.dm_sync(ctx)
+    got = big.cpu().numpy()
+    check(got[:, 2:5], oracle.lpp_rows(X, Z, 3), np.float64)
+    assert np.all(got[:, :2] == 3.5) and np.all(got[:, 5:] == 3.5)
+
+
+def test_lpp_odd_plan_is_the_l1_sort(dm, ctx):
+    # an odd-p plan holds the same sorted coordinates as the l1 plan
+    X = np.random.default_rng(8).integers(-50, 50, size=(3000, 3)).astype(np.int32)
+    a = dm.dm_prepare_lpp(ctx, dev(X), 3)
+    b = dm.dm_prepare(ctx, "l1", dev(X))
+    va, pa = dm.dm_plan_export(a)
+    vb, pb = dm.dm_plan_export(b)
+    assert torch.equal(va, vb) and torch.equal(pa, pb)
+
+
 def test_lpp_invalid_powers(dm, ctx):
     X = dev(np.zeros((10, 2), dtype=np.float32))
-    for p in (0, 1, 3, 18):
+    for p in (0, 1, 17, 18):
         with pytest.raises(dm.DMError):
             dm.dm_prepare_lpp(ctx, X, p)
 
@@ -136,9 +179,11 @@ def test_variants_full_size_sampled(dm, ctx):
     X, Z = inputs.workload_mixture_f32()
     rows = inputs.sample_rows(len(X), 8)
     Xd, Zd = dev(X), dev(Z)
-    # ||.||_4^4 on the mixture
+    # ||.||_4^4 and ||.||_3^3 on the mixture
     out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, Xd, 4), Zd)
     check(out.cpu().numpy()[rows], oracle.lpp_rows(X, Z, 4, rows), np.float32)
+    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, Xd, 3), Zd)
+    check(out.cpu().numpy()[rows], oracle.lpp_rows(X, Z, 3, rows), np.float32)
     # approximate l2 with m = 256
     G = inputs.embedding_matrix(256, X.shape[1])
     out = dm.dm_matmat(dm.dm_prepare_l2_embed(ctx, Xd, dev(G)), Zd)
