@@ -514,6 +514,8 @@ def measure_variants(dm, ctx, stream, dev, X, Z, Xd, Zd, reps=5):
     cases = {
         "tv": (lambda: dm.dm_prepare(ctx, "tv", Pd), lambda: oracle.tv_rows(P, Z, rows)),
         "lpp_p4": (lambda: dm.dm_prepare_lpp(ctx, Xd, 4), lambda: oracle.lpp_rows(X, Z, 4, rows)),
+        "lpp_p3": (lambda: dm.dm_prepare_lpp(ctx, Xd, 3), lambda: oracle.lpp_rows(X, Z, 3, rows)),
+        "lpp_p5": (lambda: dm.dm_prepare_lpp(ctx, Xd, 5), lambda: oracle.lpp_rows(X, Z, 5, rows)),
         "l2_embed_m256": (lambda: dm.dm_prepare_l2_embed(ctx, Xd, Gd),
                           lambda: oracle.l1_rows(oracle.l2_embed(X, G), Z, rows)),
     }

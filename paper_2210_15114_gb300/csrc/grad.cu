@@ -170,7 +170,7 @@ struct GradParams {
     using Acc = typename Types<DT>::Acc;
     int64_t T;                  // tiles per coordinate
     int4* flags;                // d x T: first head, last head, first end, last end
-    Wide* summ;                 // d x T x 2k x 3: sum, prefix at last head, at first end
+    Acc* summ;                  // d x T x 2k x 3: sum, prefix at last head, at first end
     const Acc* cst;             // d x T x 2k x 4: E + I - T for (head, end) outside/inside
     Out* Gt;                    // d x n
 };
@@ -292,9 +292,10 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
             // The tile sum is the inclusive prefix at the tile's last position
             // (not the block total, which sums in another order): a group
             // that runs to the end of the tile then cancels exactly.
-            // Values are picked in the accumulation type and converted once,
-            // by the thread that owns them.
-            Wide* s = p.summ + slot * 3;
+            // Stored in the accumulation type (the values are formed in it):
+            // the scan over tiles widens them as it reads, so this kernel
+            // issues no conversions on the narrow FP64 pipe.
+            Acc* s = p.summ + slot * 3;
             if (threadIdx.x == 0) {
                 if (last_head < 0) { s[1] = 0; s[4] = 0; }
                 if (first_end == kNone) { s[2] = 0; s[5] = 0; }
@@ -307,9 +308,9 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
                 if (base + j == last_head) { hz = iz[j] - z[j]; hw = iw[j] - w[j]; has_h = true; }
                 if (base + j == first_end) { fz = iz[j]; fw = iw[j]; has_f = true; }
             }
-            if (has_v) { s[0] = (Wide)vz; s[3] = (Wide)vw; }
-            if (has_h) { s[1] = (Wide)hz; s[4] = (Wide)hw; }
-            if (has_f) { s[2] = (Wide)fz; s[5] = (Wide)fw; }
+            if (has_v) { s[0] = vz; s[3] = vw; }
+            if (has_h) { s[1] = hz; s[4] = hw; }
+            if (has_f) { s[2] = fz; s[5] = fw; }
         } else {
 #pragma unroll
             for (int j = 0; j < kGI; ++j) { Iz[base + j] = iz[j]; Iw[base + j] = iw[j]; }
@@ -346,9 +347,11 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
 // in the tie group a..b,
 //     sum_j y_j |x~ - x~_j|^p = sum_s C(p, s) x~^(p-s) S_s,
 //     S_s = E_s(a) + I_s(b) - T_s over the weights y (-x~)^s, s = 0..p
-// (E, I, T as for the gradient; ties contribute nothing).  The p + 1 weights
-// of each query column are scanned two at a time; each coordinate's share is
-// added into out with an atomic add.
+// (E, I, T as for the gradient; ties contribute nothing).  Query columns are
+// taken CQ at a time (16 bytes of accumulator: one vector load of each
+// point's row of Z), the weights two powers at a time: one block scan of
+// 2 CQ values per pair.  Each coordinate's share of the CQ columns is added
+// into out with one reduction per point.
 template <dm_dtype DT>
 struct OddParams {
     using V = typename Types<DT>::V;
@@ -359,11 +362,48 @@ struct OddParams {
     const V* Z; int64_t ldz; int k; int pw;   // pw: the odd power
     int64_t T;
     int4* flags;
-    Wide* summ;                 // d x T x Q x 3, Q = k (pw + 1)
+    Acc* summ;                  // d x T x Q x 3, Q = k (pw + 1)
     const Acc* cst;             // d x T x Q x 4
     Out* out; int64_t ldo;
+    bool zvec, ovec;            // vector loads of Z rows / reductions into out
     Acc coef[16];               // C(pw, s), s = 0..pw
 };
+
+template <dm_dtype DT>
+struct OddCq { static constexpr int value = 16 / (int)sizeof(typename Types<DT>::Acc); };
+
+// Exclusive prefix sums over the block (thread order) of N values per
+// thread.  ws: N * kGW entries.
+template <class A, int N>
+__device__ __forceinline__ void block_excl_sumN(A (&v)[N], A* ws) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    A iv[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) iv[u] = v[u];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const A t = __shfl_up_sync(0xffffffffu, iv[u], o);
+            if (lane >= o) iv[u] += t;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int u = 0; u < N; ++u) ws[warp * N + u] = iv[u];
+    }
+    __syncthreads();
+    A before[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) before[u] = A(0);
+    for (int w = 0; w < warp; ++w) {
+#pragma unroll
+        for (int u = 0; u < N; ++u) before[u] += ws[w * N + u];
+    }
+#pragma unroll
+    for (int u = 0; u < N; ++u) v[u] = before[u] + iv[u] - v[u];
+    __syncthreads();
+}
 
 __device__ __forceinline__ void out_add(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void out_add(double* p, double v) { atomicAdd(p, v); }
@@ -371,13 +411,55 @@ __device__ __forceinline__ void out_add(long long* p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 
+// CQ consecutive elements of one row of Z (zeros past column k).
+template <class V, class A, int CQ>
+__device__ __forceinline__ void load_zrow(const V* __restrict__ z, int kq, bool vec, A (&y)[CQ]) {
+    if (vec && kq == CQ) {
+        V r[CQ];
+        if constexpr (sizeof(V) * CQ == 16) {
+            const uint4 raw = __ldg(reinterpret_cast<const uint4*>(z));
+            memcpy(r, &raw, 16);
+        } else {
+            static_assert(sizeof(V) * CQ == 8, "row chunk of 8 or 16 bytes");
+            const uint2 raw = __ldg(reinterpret_cast<const uint2*>(z));
+            memcpy(r, &raw, 8);
+        }
+#pragma unroll
+        for (int u = 0; u < CQ; ++u) y[u] = to_a(r[u], A());
+    } else {
+#pragma unroll
+        for (int u = 0; u < CQ; ++u) y[u] = u < kq ? to_a(z[u], A()) : A(0);
+    }
+}
+
+template <class Out, int CQ>
+__device__ __forceinline__ void add_orow(Out* o, int kq, bool vec, const Out (&g)[CQ]) {
+    if constexpr (CQ == 4 && sizeof(Out) == 4) {
+        if (vec && kq == CQ) {
+            asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                         :: "l"(o), "f"(g[0]), "f"(g[1]), "f"(g[2]), "f"(g[3]) : "memory");
+            return;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < CQ; ++u)
+        if (u < kq) out_add(o + u, g[u]);
+}
+
 template <dm_dtype DT, bool EVAL, bool VEC>
 __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
-    __shared__ Acc Ia[EVAL ? kGTile : 1], Ib[EVAL ? kGTile : 1];
-    __shared__ Acc ws[128];
+    using Out = typename Types<DT>::Out;
+    constexpr int CQ = OddCq<DT>::value;
+    // in-tile inclusive prefixes, one padding element per 32 positions (the
+    // threads' positions are 4 apart: without it a warp's reads fall in 8 banks)
+    constexpr int kPadTile = kGTile + kGTile / 32;
+    __shared__ Acc Ia[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
+    __shared__ Acc Ib[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
+    __shared__ Acc kc[EVAL ? CQ * 8 : 1];     // the pair's scan constants per column
+    __shared__ Acc ws[2 * CQ * kGW];
     __shared__ int wsi[32];
     __shared__ int red[4];
 
@@ -444,70 +526,101 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
 #pragma unroll
     for (int j = 0; j < kGI; ++j) xt[j] = base + j < valid ? to_a(x[j], Acc()) - med : Acc(0);
 
-    for (int q = 0; q < p.k; ++q) {
-        Acc y[kGI];
+    for (int q0 = 0; q0 < p.k; q0 += CQ) {
+        const int kq = min(CQ, p.k - q0);
+        Acc y[kGI][CQ];
+#pragma unroll
+        for (int j = 0; j < kGI; ++j) {
+            if (base + j < valid) {
+                load_zrow<V, Acc, CQ>(p.Z + (int64_t)pi[j] * p.ldz + q0, kq, p.zvec, y[j]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < CQ; ++u) y[j][u] = Acc(0);
+            }
+        }
+        Acc g[kGI][CQ];
 #pragma unroll
         for (int j = 0; j < kGI; ++j)
-            y[j] = base + j < valid ? to_a(p.Z[(int64_t)pi[j] * p.ldz + q], Acc()) : Acc(0);
-        Acc g[kGI];
 #pragma unroll
-        for (int j = 0; j < kGI; ++j) g[j] = Acc(0);
-        // weights y (-x~)^s for s = s0, s0 + 1, pair by pair
+            for (int u = 0; u < CQ; ++u) g[j][u] = Acc(0);
         Acc pwa[kGI];                          // (-x~)^s0
 #pragma unroll
         for (int j = 0; j < kGI; ++j) pwa[j] = Acc(1);
         for (int s0 = 0; s0 < P1; s0 += 2) {
-            Acc va[kGI], vb[kGI], ia[kGI], ib[kGI];
+            // inclusive in-thread prefixes of y (-x~)^s0 and y (-x~)^(s0+1)
+            Acc ia[kGI][CQ], ib[kGI][CQ];
+            Acc off[2 * CQ];
 #pragma unroll
-            for (int j = 0; j < kGI; ++j) {
-                va[j] = y[j] * pwa[j];
-                vb[j] = -va[j] * xt[j];
-            }
-            Acc sa = 0, sb = 0;
-#pragma unroll
-            for (int j = 0; j < kGI; ++j) { sa += va[j]; sb += vb[j]; ia[j] = sa; ib[j] = sb; }
-            Acc oa = sa, ob = sb, ta, tb;
-            block_excl_sum2(oa, ob, ws, ta, tb);
-#pragma unroll
-            for (int j = 0; j < kGI; ++j) { ia[j] += oa; ib[j] += ob; }
-            const int64_t slot = ((int64_t)c * p.T + t) * Q + (int64_t)q * P1 + s0;
-            if (!EVAL) {
-                Wide* sm = p.summ + slot * 3;
-                if (threadIdx.x == 0) {
-                    if (last_head < 0) { sm[1] = 0; sm[4] = 0; }
-                    if (first_end == kNone) { sm[2] = 0; sm[5] = 0; }
-                }
-                Acc v0 = 0, v1 = 0, h0 = 0, h1 = 0, f0 = 0, f1 = 0;
-                bool hv = false, hh = false, hf = false;
+            for (int u = 0; u < CQ; ++u) {
+                Acc sa = 0, sb = 0;
 #pragma unroll
                 for (int j = 0; j < kGI; ++j) {
-                    if (base + j == valid - 1) { v0 = ia[j]; v1 = ib[j]; hv = true; }
-                    if (base + j == last_head) { h0 = ia[j] - va[j]; h1 = ib[j] - vb[j]; hh = true; }
-                    if (base + j == first_end) { f0 = ia[j]; f1 = ib[j]; hf = true; }
+                    const Acc va = y[j][u] * pwa[j];
+                    sa += va;
+                    sb -= va * xt[j];
+                    ia[j][u] = sa;
+                    ib[j][u] = sb;
                 }
-                if (hv) { sm[0] = (Wide)v0; sm[3] = (Wide)v1; }
-                if (hh) { sm[1] = (Wide)h0; sm[4] = (Wide)h1; }
-                if (hf) { sm[2] = (Wide)f0; sm[5] = (Wide)f1; }
-            } else {
+                off[u] = sa;
+                off[CQ + u] = sb;
+            }
+            block_excl_sumN<Acc, 2 * CQ>(off, ws);
 #pragma unroll
-                for (int j = 0; j < kGI; ++j) { Ia[base + j] = ia[j]; Ib[base + j] = ib[j]; }
+            for (int j = 0; j < kGI; ++j)
+#pragma unroll
+                for (int u = 0; u < CQ; ++u) { ia[j][u] += off[u]; ib[j][u] += off[CQ + u]; }
+            if (!EVAL) {
+#pragma unroll
+                for (int u = 0; u < CQ; ++u) {
+                    if (u >= kq) continue;
+                    const int64_t slot = ((int64_t)c * p.T + t) * Q + (int64_t)(q0 + u) * P1 + s0;
+                    Acc* sm = p.summ + slot * 3;
+                    if (threadIdx.x == 0) {
+                        if (last_head < 0) { sm[1] = 0; sm[4] = 0; }
+                        if (first_end == kNone) { sm[2] = 0; sm[5] = 0; }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kGI; ++j) {
+                        const Acc va = y[j][u] * pwa[j];
+                        if (base + j == valid - 1) { sm[0] = ia[j][u]; sm[3] = ib[j][u]; }
+                        if (base + j == last_head) {
+                            sm[1] = ia[j][u] - va;
+                            sm[4] = ib[j][u] + va * xt[j];
+                        }
+                        if (base + j == first_end) { sm[2] = ia[j][u]; sm[5] = ib[j][u]; }
+                    }
+                }
+            } else {
+                const int pb = base + (base >> 5);   // a thread's 4 positions share one 32-group
+#pragma unroll
+                for (int u = 0; u < CQ; ++u)
+#pragma unroll
+                    for (int j = 0; j < kGI; ++j) { Ia[u][pb + j] = ia[j][u]; Ib[u][pb + j] = ib[j][u]; }
+                if (threadIdx.x < CQ * 8) {
+                    const int u = threadIdx.x >> 3;
+                    kc[threadIdx.x] = u < kq ? p.cst[(((int64_t)c * p.T + t) * Q + (int64_t)(q0 + u) * P1 + s0) * 4 +
+                                                     (threadIdx.x & 7)]
+                                             : Acc(0);
+                }
                 __syncthreads();
-                const Acc* ka = p.cst + slot * 4;
-                const Acc* kb = ka + 4;
                 const Acc ca = p.coef[s0], cb = p.coef[s0 + 1];
 #pragma unroll
                 for (int j = 0; j < kGI; ++j) {
                     if (base + j >= valid) continue;
                     const bool ain = a[j] >= 0, bin = b[j] != kNone;
-                    Acc S0 = ain ? (bin ? ka[3] : ka[2]) : (bin ? ka[1] : ka[0]);
-                    Acc S1 = ain ? (bin ? kb[3] : kb[2]) : (bin ? kb[1] : kb[0]);
-                    if (ain && a[j] > 0) { S0 += Ia[a[j] - 1]; S1 += Ib[a[j] - 1]; }
-                    if (bin) { S0 += Ia[b[j]]; S1 += Ib[b[j]]; }
-                    // C(p, s) x~^(p - s) S_s for s = s0 and s0 + 1
+                    const int sel = (ain ? 2 : 0) + (bin ? 1 : 0);
+                    // C(p, s) x~^(p - s) for s = s0 and s0 + 1
                     Acc e1 = 1;
                     for (int u = 0; u < p.pw - s0 - 1; ++u) e1 *= xt[j];
-                    const Acc e0 = e1 * xt[j];
-                    g[j] += ca * e0 * S0 + cb * e1 * S1;
+                    const Acc w0 = ca * e1 * xt[j], w1 = cb * e1;
+                    const int ah = a[j] - 1 + ((a[j] - 1) >> 5), bh = b[j] + (b[j] >> 5);
+#pragma unroll
+                    for (int u = 0; u < CQ; ++u) {
+                        Acc S0 = kc[u * 8 + sel], S1 = kc[u * 8 + 4 + sel];
+                        if (ain && a[j] > 0) { S0 += Ia[u][ah]; S1 += Ib[u][ah]; }
+                        if (bin) { S0 += Ia[u][bh]; S1 += Ib[u][bh]; }
+                        g[j][u] += w0 * S0 + w1 * S1;
+                    }
                 }
                 __syncthreads();
             }
@@ -517,8 +630,13 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
         }
         if (EVAL) {
 #pragma unroll
-            for (int j = 0; j < kGI; ++j)
-                if (base + j < valid) out_add(p.out + (int64_t)pi[j] * p.ldo + q, (typename Types<DT>::Out)g[j]);
+            for (int j = 0; j < kGI; ++j) {
+                if (base + j >= valid) continue;
+                Out o[CQ];
+#pragma unroll
+                for (int u = 0; u < CQ; ++u) o[u] = (Out)g[j][u];
+                add_orow<Out, CQ>(p.out + (int64_t)pi[j] * p.ldo + q0, kq, p.ovec, o);
+            }
         }
     }
 }
@@ -528,7 +646,7 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
 // backward scan (I at the end of the group leaving each tile).
 template <class W, class A>
 __global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__ flags,
-                                                        const W* __restrict__ summ, W* pre,
+                                                        const A* __restrict__ summ, W* pre,
                                                         A* __restrict__ cst, int64_t n, int64_t T,
                                                         int K2) {
     __shared__ W vals[kGT];
@@ -543,11 +661,11 @@ __global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__
         const bool in = t < T;
         const int64_t slot = ((int64_t)c * T + t) * K2 + qy;
         const int4 f = in ? flags[(int64_t)c * T + t] : make_int4(kNone, -1, kNone, -1);
-        const W sum = in ? summ[slot * 3] : W(0);
+        const W sum = in ? (W)summ[slot * 3] : W(0);
         W chunk;
         const W tp = carry_tp + block_excl_sum1(sum, ws, chunk);
         const bool has_head = in && f.y >= 0;
-        vals[tid] = tp + (in ? summ[slot * 3 + 1] : W(0));
+        vals[tid] = tp + (in ? (W)summ[slot * 3 + 1] : W(0));
         int last;
         const int idx = block_excl_max(has_head ? tid : -1, wsi, &last);
         const W el = (in && f.x == 0) ? tp : (idx >= 0 ? vals[idx] : carry_e);
@@ -565,12 +683,12 @@ __global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__
         const int4 f = in ? flags[(int64_t)c * T + t] : make_int4(kNone, -1, kNone, -1);
         const W tp = in ? pre[slot * 3] : W(0);
         const bool has_end = in && f.z != kNone;
-        vals[tid] = tp + (in ? summ[slot * 3 + 2] : W(0));
+        vals[tid] = tp + (in ? (W)summ[slot * 3 + 2] : W(0));
         int first;
         const int idx = block_excl_suffix_min(has_end ? tid : kNone, wsi, &first);
         const int valid = in ? (int)min64(kGTile, n - t * kGTile) : 0;
         const bool end_at_last = in && f.w == valid - 1;
-        const W ir = end_at_last ? tp + summ[slot * 3] : (idx != kNone ? vals[idx] : carry_i);
+        const W ir = end_at_last ? tp + (W)summ[slot * 3] : (idx != kNone ? vals[idx] : carry_i);
         if (in) {
             const W el = pre[slot * 3 + 1];
             A* k4 = cst + slot * 4;
@@ -727,7 +845,7 @@ GradParams<DT> make_params(const GradArgs& a) {
     p.k = (int)a.k;
     p.T = L.T;
     p.flags = reinterpret_cast<int4*>(sc + L.flags);
-    p.summ = reinterpret_cast<Wide*>(sc + L.summ);
+    p.summ = reinterpret_cast<Acc*>(sc + L.summ);
     p.cst = reinterpret_cast<const Acc*>(sc + L.cst);
     p.Gt = reinterpret_cast<Out*>(sc + L.gt);
     return p;
@@ -826,10 +944,14 @@ cudaError_t oddp_stage_t(const OddArgs& a, int stage, cudaStream_t s, int64_t* l
     p.pw = a.p;
     p.T = L.T;
     p.flags = reinterpret_cast<int4*>(sc + L.flags);
-    p.summ = reinterpret_cast<Wide*>(sc + L.summ);
+    p.summ = reinterpret_cast<Acc*>(sc + L.summ);
     p.cst = reinterpret_cast<const Acc*>(sc + L.cst);
     p.out = static_cast<Out*>(a.out);
     p.ldo = a.ldo;
+    constexpr int CQ = OddCq<DT>::value;
+    const size_t zrow = sizeof(V) * CQ;   // bytes of one vector load of a row chunk
+    p.zvec = a.ldz % CQ == 0 && reinterpret_cast<uintptr_t>(a.Z) % zrow == 0;
+    p.ovec = a.ldo % CQ == 0 && reinterpret_cast<uintptr_t>(a.out) % (sizeof(Out) * CQ) == 0;
     long long cb = 1;
     for (int t = 0; t < 16; ++t) {
         p.coef[t] = t <= a.p ? (Acc)cb : Acc(0);
