@@ -52,41 +52,6 @@ __device__ __forceinline__ double to_a(double v, double) { return v; }
 __device__ __forceinline__ long long to_a(int32_t v, long long) { return (long long)v; }
 
 // ---------------------------------------------------------------- scans
-// Exclusive prefix sums over the block (thread order) of two values per
-// thread; tz / tw receive the block totals.  ws: 4 * 32 entries.
-template <class A>
-__device__ __forceinline__ void block_excl_sum2(A& z, A& w, A* ws, A& tz, A& tw) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    A iz = z, iw = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const A a = __shfl_up_sync(0xffffffffu, iz, o);
-        const A b = __shfl_up_sync(0xffffffffu, iw, o);
-        if (lane >= o) { iz += a; iw += b; }
-    }
-    if (lane == 31) { ws[warp] = iz; ws[32 + warp] = iw; }
-    __syncthreads();
-    if (warp == 0) {
-        A vz = lane < kGW ? ws[lane] : A(0), vw = lane < kGW ? ws[32 + lane] : A(0);
-#pragma unroll
-        for (int o = 1; o < kGW; o <<= 1) {
-            const A a = __shfl_up_sync(0xffffffffu, vz, o);
-            const A b = __shfl_up_sync(0xffffffffu, vw, o);
-            if (lane >= o) { vz += a; vw += b; }
-        }
-        ws[64 + lane] = vz;
-        ws[96 + lane] = vw;
-    }
-    __syncthreads();
-    const A bz = warp > 0 ? ws[64 + warp - 1] : A(0);
-    const A bw = warp > 0 ? ws[96 + warp - 1] : A(0);
-    tz = ws[64 + kGW - 1];
-    tw = ws[96 + kGW - 1];
-    z = bz + iz - z;
-    w = bw + iw - w;
-    __syncthreads();
-}
-
 // Exclusive prefix sum of one value per thread; t receives the block total.
 template <class A>
 __device__ __forceinline__ A block_excl_sum1(A v, A* ws, A& t) {
@@ -173,7 +138,13 @@ struct GradParams {
     Acc* summ;                  // d x T x 2k x 3: sum, prefix at last head, at first end
     const Acc* cst;             // d x T x 2k x 4: E + I - T for (head, end) outside/inside
     Out* Gt;                    // d x n
+    bool pvec;                  // 16-byte loads of P's row chunks
 };
+
+// In-tile inclusive prefixes in shared memory: one padding element per 32
+// positions (a thread's positions are 4 apart; without it a warp's reads of
+// them fall in 8 banks).
+constexpr int kPadTile = kGTile + kGTile / 32;
 
 
 template <class V, bool VEC>
@@ -191,14 +162,71 @@ __device__ __forceinline__ void load_items(const V* __restrict__ src, int valid,
     }
 }
 
+// Exclusive prefix sums over the block (thread order) of N values per
+// thread.  ws: N * kGW entries.
+template <class A, int N>
+__device__ __forceinline__ void block_excl_sumN(A (&v)[N], A* ws) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    A iv[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) iv[u] = v[u];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const A t = __shfl_up_sync(0xffffffffu, iv[u], o);
+            if (lane >= o) iv[u] += t;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int u = 0; u < N; ++u) ws[warp * N + u] = iv[u];
+    }
+    __syncthreads();
+    A before[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) before[u] = A(0);
+    for (int w = 0; w < warp; ++w) {
+#pragma unroll
+        for (int u = 0; u < N; ++u) before[u] += ws[w * N + u];
+    }
+#pragma unroll
+    for (int u = 0; u < N; ++u) v[u] = before[u] + iv[u] - v[u];
+    __syncthreads();
+}
+
+// CQ consecutive elements of one row (zeros past the kq valid ones).
+template <class V, class A, int CQ>
+__device__ __forceinline__ void load_zrow(const V* __restrict__ z, int kq, bool vec, A (&y)[CQ]) {
+    if (vec && kq == CQ) {
+        V r[CQ];
+        if constexpr (sizeof(V) * CQ == 16) {
+            const uint4 raw = __ldg(reinterpret_cast<const uint4*>(z));
+            memcpy(r, &raw, 16);
+        } else {
+            static_assert(sizeof(V) * CQ == 8, "row chunk of 8 or 16 bytes");
+            const uint2 raw = __ldg(reinterpret_cast<const uint2*>(z));
+            memcpy(r, &raw, 8);
+        }
+#pragma unroll
+        for (int u = 0; u < CQ; ++u) y[u] = to_a(r[u], A());
+    } else {
+#pragma unroll
+        for (int u = 0; u < CQ; ++u) y[u] = u < kq ? to_a(z[u], A()) : A(0);
+    }
+}
+
 template <dm_dtype DT, bool EVAL, bool VEC>
 __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
-    __shared__ Acc Iz[EVAL ? kGTile : 1], Iw[EVAL ? kGTile : 1];
-    __shared__ Acc ws[128];
+    constexpr int NV = 16 / (int)sizeof(V);   // (z, w) values per 16-byte row chunk
+    constexpr int GQ = NV / 2;                 // query columns per chunk
+    __shared__ Acc Ip[EVAL ? NV : 1][EVAL ? kPadTile : 1];
+    __shared__ Acc kc[EVAL ? NV * 4 : 1];      // the chunk's scan constants
+    __shared__ Acc ws[NV * kGW];
     __shared__ int wsi[32];
     __shared__ int red[4];
 
@@ -265,72 +293,83 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
 #pragma unroll
     for (int j = 0; j < kGI; ++j) g[j] = Acc(0);
 
-    for (int q = 0; q < p.k; ++q) {
-        Acc z[kGI], w[kGI], iz[kGI], iw[kGI];
+    for (int q0 = 0; q0 < p.k; q0 += GQ) {
+        const int kq = min(GQ, p.k - q0);
+        // (z, w) of columns q0 .. q0 + GQ - 1, their in-thread inclusive
+        // prefixes, then the block's exclusive offsets
+        Acc y[kGI][NV], ip[kGI][NV], off[NV];
 #pragma unroll
         for (int j = 0; j < kGI; ++j) {
             if (base + j < valid) {
-                const V* pr = p.P + (int64_t)pi[j] * K2 + 2 * q;
-                z[j] = to_a(pr[0], Acc());
-                w[j] = to_a(pr[1], Acc());
+                load_zrow<V, Acc, NV>(p.P + (int64_t)pi[j] * K2 + 2 * q0, 2 * kq, p.pvec, y[j]);
             } else {
-                z[j] = Acc(0);
-                w[j] = Acc(0);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) y[j][v] = Acc(0);
             }
         }
-        Acc sz = 0, sw = 0;
 #pragma unroll
-        for (int j = 0; j < kGI; ++j) { sz += z[j]; sw += w[j]; iz[j] = sz; iw[j] = sw; }
-        Acc oz = sz, ow = sw, tz, tw;
-        block_excl_sum2(oz, ow, ws, tz, tw);
+        for (int v = 0; v < NV; ++v) {
+            Acc run = 0;
 #pragma unroll
-        for (int j = 0; j < kGI; ++j) { iz[j] += oz; iw[j] += ow; }
+            for (int j = 0; j < kGI; ++j) { run += y[j][v]; ip[j][v] = run; }
+            off[v] = run;
+        }
+        block_excl_sumN<Acc, NV>(off, ws);
+#pragma unroll
+        for (int j = 0; j < kGI; ++j)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ip[j][v] += off[v];
 
-        const int64_t slot = ((int64_t)c * p.T + t) * K2 + 2 * q;
+        const int64_t slot0 = ((int64_t)c * p.T + t) * K2 + 2 * q0;
         if (!EVAL) {
-            // sums, exclusive prefix at the last head, inclusive at the first end
-            // The tile sum is the inclusive prefix at the tile's last position
-            // (not the block total, which sums in another order): a group
-            // that runs to the end of the tile then cancels exactly.
-            // Stored in the accumulation type (the values are formed in it):
-            // the scan over tiles widens them as it reads, so this kernel
-            // issues no conversions on the narrow FP64 pipe.
-            Acc* s = p.summ + slot * 3;
-            if (threadIdx.x == 0) {
-                if (last_head < 0) { s[1] = 0; s[4] = 0; }
-                if (first_end == kNone) { s[2] = 0; s[5] = 0; }
-            }
-            Acc vz = 0, vw = 0, hz = 0, hw = 0, fz = 0, fw = 0;
-            bool has_v = false, has_h = false, has_f = false;
+            // per (column, z or w): the sum, the exclusive prefix at the last
+            // head, the inclusive prefix at the first end.  The tile sum is
+            // the inclusive prefix at the tile's last position (not the block
+            // total, which sums in another order): a group that runs to the
+            // end of the tile then cancels exactly.  Stored in the
+            // accumulation type (the values are formed in it): the scan over
+            // tiles widens them as it reads, so this kernel issues no
+            // conversions on the narrow FP64 pipe.
 #pragma unroll
-            for (int j = 0; j < kGI; ++j) {
-                if (base + j == valid - 1) { vz = iz[j]; vw = iw[j]; has_v = true; }
-                if (base + j == last_head) { hz = iz[j] - z[j]; hw = iw[j] - w[j]; has_h = true; }
-                if (base + j == first_end) { fz = iz[j]; fw = iw[j]; has_f = true; }
+            for (int v = 0; v < NV; ++v) {
+                if (v >= 2 * kq) continue;
+                Acc* sm = p.summ + (slot0 + v) * 3;
+                if (threadIdx.x == 0) {
+                    if (last_head < 0) sm[1] = 0;
+                    if (first_end == kNone) sm[2] = 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kGI; ++j) {
+                    if (base + j == valid - 1) sm[0] = ip[j][v];
+                    if (base + j == last_head) sm[1] = ip[j][v] - y[j][v];
+                    if (base + j == first_end) sm[2] = ip[j][v];
+                }
             }
-            if (has_v) { s[0] = vz; s[3] = vw; }
-            if (has_h) { s[1] = hz; s[4] = hw; }
-            if (has_f) { s[2] = fz; s[5] = fw; }
         } else {
+            const int pb = base + (base >> 5);   // a thread's 4 positions share one 32-group
 #pragma unroll
-            for (int j = 0; j < kGI; ++j) { Iz[base + j] = iz[j]; Iw[base + j] = iw[j]; }
-            __syncthreads();
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int j = 0; j < kGI; ++j) Ip[v][pb + j] = ip[j][v];
             // E(a) + I(b) - T with the parts that lie outside the tile taken
             // from the scan: (head outside, end outside), (outside, inside),
             // (inside, outside), (inside, inside)
-            const Acc* kz = p.cst + slot * 4;
-            const Acc* kw = kz + 4;
-            const Acc z00 = kz[0], z01 = kz[1], z10 = kz[2], z11 = kz[3];
-            const Acc w00 = kw[0], w01 = kw[1], w10 = kw[2], w11 = kw[3];
+            if (threadIdx.x < NV * 4)
+                kc[threadIdx.x] = (threadIdx.x >> 2) < 2 * kq ? p.cst[slot0 * 4 + threadIdx.x] : Acc(0);
+            __syncthreads();
 #pragma unroll
             for (int j = 0; j < kGI; ++j) {
                 if (base + j >= valid) continue;
                 const bool ain = a[j] >= 0, bin = b[j] != kNone;
-                Acc Sz = ain ? (bin ? z11 : z10) : (bin ? z01 : z00);
-                Acc Sw = ain ? (bin ? w11 : w10) : (bin ? w01 : w00);
-                if (ain && a[j] > 0) { Sz += Iz[a[j] - 1]; Sw += Iw[a[j] - 1]; }
-                if (bin) { Sz += Iz[b[j]]; Sw += Iw[b[j]]; }
-                g[j] += w[j] * Sz + z[j] * Sw;
+                const int sel = (ain ? 2 : 0) + (bin ? 1 : 0);
+                const int ah = a[j] - 1 + ((a[j] - 1) >> 5), bh = b[j] + (b[j] >> 5);
+#pragma unroll
+                for (int u = 0; u < GQ; ++u) {
+                    Acc Sz = kc[8 * u + sel], Sw = kc[8 * u + 4 + sel];
+                    if (ain && a[j] > 0) { Sz += Ip[2 * u][ah]; Sw += Ip[2 * u + 1][ah]; }
+                    if (bin) { Sz += Ip[2 * u][bh]; Sw += Ip[2 * u + 1][bh]; }
+                    g[j] += y[j][2 * u + 1] * Sz + y[j][2 * u] * Sw;
+                }
             }
             __syncthreads();
         }
@@ -372,64 +411,10 @@ struct OddParams {
 template <dm_dtype DT>
 struct OddCq { static constexpr int value = 16 / (int)sizeof(typename Types<DT>::Acc); };
 
-// Exclusive prefix sums over the block (thread order) of N values per
-// thread.  ws: N * kGW entries.
-template <class A, int N>
-__device__ __forceinline__ void block_excl_sumN(A (&v)[N], A* ws) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    A iv[N];
-#pragma unroll
-    for (int u = 0; u < N; ++u) iv[u] = v[u];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-        for (int u = 0; u < N; ++u) {
-            const A t = __shfl_up_sync(0xffffffffu, iv[u], o);
-            if (lane >= o) iv[u] += t;
-        }
-    }
-    if (lane == 31) {
-#pragma unroll
-        for (int u = 0; u < N; ++u) ws[warp * N + u] = iv[u];
-    }
-    __syncthreads();
-    A before[N];
-#pragma unroll
-    for (int u = 0; u < N; ++u) before[u] = A(0);
-    for (int w = 0; w < warp; ++w) {
-#pragma unroll
-        for (int u = 0; u < N; ++u) before[u] += ws[w * N + u];
-    }
-#pragma unroll
-    for (int u = 0; u < N; ++u) v[u] = before[u] + iv[u] - v[u];
-    __syncthreads();
-}
-
 __device__ __forceinline__ void out_add(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void out_add(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void out_add(long long* p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-}
-
-// CQ consecutive elements of one row of Z (zeros past column k).
-template <class V, class A, int CQ>
-__device__ __forceinline__ void load_zrow(const V* __restrict__ z, int kq, bool vec, A (&y)[CQ]) {
-    if (vec && kq == CQ) {
-        V r[CQ];
-        if constexpr (sizeof(V) * CQ == 16) {
-            const uint4 raw = __ldg(reinterpret_cast<const uint4*>(z));
-            memcpy(r, &raw, 16);
-        } else {
-            static_assert(sizeof(V) * CQ == 8, "row chunk of 8 or 16 bytes");
-            const uint2 raw = __ldg(reinterpret_cast<const uint2*>(z));
-            memcpy(r, &raw, 8);
-        }
-#pragma unroll
-        for (int u = 0; u < CQ; ++u) y[u] = to_a(r[u], A());
-    } else {
-#pragma unroll
-        for (int u = 0; u < CQ; ++u) y[u] = u < kq ? to_a(z[u], A()) : A(0);
-    }
 }
 
 template <class Out, int CQ>
@@ -453,9 +438,6 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
     constexpr int CQ = OddCq<DT>::value;
-    // in-tile inclusive prefixes, one padding element per 32 positions (the
-    // threads' positions are 4 apart: without it a warp's reads fall in 8 banks)
-    constexpr int kPadTile = kGTile + kGTile / 32;
     __shared__ Acc Ia[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
     __shared__ Acc Ib[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
     __shared__ Acc kc[EVAL ? CQ * 8 : 1];     // the pair's scan constants per column
@@ -848,6 +830,7 @@ GradParams<DT> make_params(const GradArgs& a) {
     p.summ = reinterpret_cast<Acc*>(sc + L.summ);
     p.cst = reinterpret_cast<const Acc*>(sc + L.cst);
     p.Gt = reinterpret_cast<Out*>(sc + L.gt);
+    p.pvec = (2 * a.k * (int64_t)sizeof(V)) % 16 == 0;   // P is 256-byte aligned in the scratch
     return p;
 }
 
