@@ -216,13 +216,14 @@ __device__ __forceinline__ void load_zrow(const V* __restrict__ z, int kq, bool 
     }
 }
 
-template <dm_dtype DT, bool EVAL, bool VEC>
+// NV: (z, w) values per row chunk -- 16 bytes of them, or one (z, w) pair
+// when k = 1.
+template <dm_dtype DT, bool EVAL, bool VEC, int NV>
 __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
-    constexpr int NV = 16 / (int)sizeof(V);   // (z, w) values per 16-byte row chunk
     constexpr int GQ = NV / 2;                 // query columns per chunk
     __shared__ Acc Ip[EVAL ? NV : 1][EVAL ? kPadTile : 1];
     __shared__ Acc kc[EVAL ? NV * 4 : 1];      // the chunk's scan constants
@@ -845,20 +846,35 @@ cudaError_t grad_l1_stage_t(const GradArgs& a, int stage, cudaStream_t s, int64_
     unsigned char* sc = static_cast<unsigned char*>(a.scratch);
     const int64_t blocks = a.d * L.T;
     if (blocks > INT_MAX) return cudaErrorInvalidConfiguration;
+    // row chunks of 16 bytes, or of one (z, w) pair for a single column (its
+    // rows of 2 sizeof(V) bytes are aligned to that size)
+    constexpr int kNV = 16 / (int)sizeof(V);
+    const bool narrow = a.k == 1;
+    if (narrow) p.pvec = true;
     // 16-byte loads of the sorted column need every column start aligned
     const bool vec = (a.n % (16 / (int64_t)sizeof(V))) == 0 && (a.n % 4) == 0 &&
                      reinterpret_cast<uintptr_t>(a.xs) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(a.perm) % 16 == 0;
     if (stage == 0) {
-        if (vec) grad_tile_kernel<DT, false, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
-        else grad_tile_kernel<DT, false, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        if (narrow) {
+            if (vec) grad_tile_kernel<DT, false, true, 2><<<(unsigned)blocks, kGT, 0, s>>>(p);
+            else grad_tile_kernel<DT, false, false, 2><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        } else {
+            if (vec) grad_tile_kernel<DT, false, true, kNV><<<(unsigned)blocks, kGT, 0, s>>>(p);
+            else grad_tile_kernel<DT, false, false, kNV><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        }
     } else if (stage == 1) {
         grad_scan_kernel<Wide, Acc><<<(unsigned)(a.d * 2 * a.k), kGT, 0, s>>>(
             p.flags, p.summ, reinterpret_cast<Wide*>(sc + L.pre), reinterpret_cast<Acc*>(sc + L.cst),
             a.n, L.T, (int)(2 * a.k));
     } else if (stage == 2) {
-        if (vec) grad_tile_kernel<DT, true, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
-        else grad_tile_kernel<DT, true, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        if (narrow) {
+            if (vec) grad_tile_kernel<DT, true, true, 2><<<(unsigned)blocks, kGT, 0, s>>>(p);
+            else grad_tile_kernel<DT, true, false, 2><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        } else {
+            if (vec) grad_tile_kernel<DT, true, true, kNV><<<(unsigned)blocks, kGT, 0, s>>>(p);
+            else grad_tile_kernel<DT, true, false, kNV><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        }
     } else {
         const int64_t bx = (a.n + 31) / 32;
         if (bx > INT_MAX) return cudaErrorInvalidConfiguration;

@@ -17,8 +17,13 @@ normalized directions must be projected out again; one pass each leaves
 the basis far from orthonormal in FP32).  Orthonormalization is
 Cholesky QR applied twice (Gram matrix W^T W, its Cholesky factor R in
 FP64, W R^-1): two skinny matrix products instead of a Householder QR of a
-tall block, with Householder QR as the fallback when the block is
-numerically rank deficient.  The Rayleigh-Ritz matrix M = Q^T (A Q) reuses the
+tall block.  A numerically rank-deficient block (A of rank below the Krylov
+dimension: squared l2 has rank d + 2) keeps its well-resolved directions --
+W V_r diag(lambda_r)^-1/2 from the FP64 eigendecomposition of its Gram
+matrix -- and is filled up to k columns with seeded Gaussian columns, which
+are projected off the basis and orthonormalized the same way: the basis
+stays orthonormal, and the filled directions carry Ritz values at rounding
+level.  The Rayleigh-Ritz matrix M = Q^T (A Q) reuses the
 products A Q_i.  Its eigenpairs (theta, V) of largest |theta| give the
 singular values |theta| and A ~ U diag(theta) U^T with U = Q V.
 """
@@ -27,6 +32,13 @@ from __future__ import annotations
 import torch
 
 from . import binding
+
+# Gram eigenvalues below this fraction of the largest are rounding noise of an
+# FP32 block; Cholesky factors with a diagonal spread beyond 1e3 (eigenvalue
+# ratios near 1e-6) mark the block as rank deficient.
+_RANK_TOL = 1e-5
+_SPREAD = 1e3
+_FILL_SEED = 0x5EED
 
 
 def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
@@ -42,14 +54,14 @@ def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
     dev, dt = Pi.device, Pi.dtype
     Q = torch.empty((n, q * k), dtype=dt, device=dev)
     AQ = torch.empty((n, q * k), dtype=dt, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(_FILL_SEED)
     W = binding.dm_matmat(plan, Pi.contiguous())
     for i in range(q):
         prev = Q[:, : i * k]
         for _ in range(2):
-            if i:
-                for _ in range(2):
-                    W = W - prev @ (prev.T @ W)
-            W = _orthonormalize(W)
+            W = _project_out(W, prev)
+            W = _orthonormalize(W, prev, gen)
         Q[:, i * k:(i + 1) * k] = W
         binding.dm_matmat(plan, Q[:, i * k:(i + 1) * k], out=AQ[:, i * k:(i + 1) * k])
         W = AQ[:, i * k:(i + 1) * k].clone()
@@ -61,21 +73,51 @@ def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
     return theta[order], U
 
 
-def _orthonormalize(W: torch.Tensor) -> torch.Tensor:
-    """Orthonormal basis of the columns of a tall block W (n x k): Cholesky
-    QR twice, or Householder QR when W is (numerically) rank deficient -- a
-    Gram matrix that is not positive definite, or a Cholesky diagonal spread
-    beyond 1e3, past which a Gram matrix formed in the block's precision no
-    longer resolves the smallest direction."""
+def _project_out(W: torch.Tensor, prev: torch.Tensor) -> torch.Tensor:
+    """W minus its projections on the orthonormal columns of prev, removed
+    twice (block classical Gram-Schmidt with one reorthogonalization)."""
+    if prev.shape[1] == 0:
+        return W
+    for _ in range(2):
+        W = W - prev @ (prev.T @ W)
+    return W
+
+
+def _cholqr2(W: torch.Tensor):
+    """Cholesky QR applied twice, or None when W is numerically rank
+    deficient (a Gram matrix that is not positive definite, or a Cholesky
+    diagonal spread beyond _SPREAD, past which a Gram matrix formed in the
+    block's precision no longer resolves the smallest direction)."""
     Q = W
     for _ in range(2):
         G = (Q.T @ Q).double()
         R, info = torch.linalg.cholesky_ex(G, upper=True)
         dg = torch.diagonal(R).abs()
-        if int(info.item()) != 0 or float(dg.min()) < 1e-3 * float(dg.max()):
-            return torch.linalg.qr(W).Q
+        if int(info.item()) != 0 or float(dg.min()) * _SPREAD < float(dg.max()):
+            return None
         Rinv = torch.linalg.solve_triangular(R, torch.eye(R.shape[0], dtype=R.dtype, device=R.device),
                                              upper=True)
         Q = Q @ Rinv.to(Q.dtype)
     return Q
 
+
+def _orthonormalize(W: torch.Tensor, prev: torch.Tensor, gen: torch.Generator) -> torch.Tensor:
+    """Orthonormal basis of a tall block W (n x k) whose columns are already
+    orthogonal to prev: Cholesky QR twice; for a rank-deficient W, its
+    resolved directions plus seeded Gaussian fill (projected off prev),
+    Householder QR only if that block is still deficient."""
+    Q = _cholqr2(W)
+    if Q is not None:
+        return Q
+    # k x k eigenproblem on the host (a small dense solve; the block stays on the device)
+    lam, V = torch.linalg.eigh((W.T @ W).double().cpu())    # ascending
+    top = float(lam[-1]) if lam.numel() else 0.0
+    keep = lam > max(_RANK_TOL * top, 0.0)
+    r = int(keep.sum().item())
+    good = W @ (V[:, keep] / lam[keep].sqrt()).to(device=W.device, dtype=W.dtype)
+    # unit-norm Gaussian columns, on the scale of the resolved ones
+    fill = torch.randn((W.shape[0], W.shape[1] - r), generator=gen, device=W.device, dtype=W.dtype)
+    fill /= W.shape[0] ** 0.5
+    Wf = _project_out(torch.cat([good, fill], dim=1), prev)
+    Q = _cholqr2(Wf)
+    return Q if Q is not None else torch.linalg.qr(Wf).Q
