@@ -147,6 +147,28 @@ struct GradParams {
 constexpr int kPadTile = kGTile + kGTile / 32;
 
 
+// Which of this thread's items sits at tile position pos (-1: none).
+__device__ __forceinline__ int own_item(int pos, int base) {
+    const int j = pos - base;
+    return (j >= 0 && j < kGI) ? j : -1;
+}
+
+// x[j][v] for a run-time j (register selects, no local memory).
+template <class A, int N>
+__device__ __forceinline__ A pick(const A (&x)[kGI][N], int j, int v) {
+    A r = x[0][v];
+#pragma unroll
+    for (int i = 1; i < kGI; ++i) if (j == i) r = x[i][v];
+    return r;
+}
+template <class A>
+__device__ __forceinline__ A pick1(const A (&x)[kGI], int j) {
+    A r = x[0];
+#pragma unroll
+    for (int i = 1; i < kGI; ++i) if (j == i) r = x[i];
+    return r;
+}
+
 template <class V, bool VEC>
 __device__ __forceinline__ void load_items(const V* __restrict__ src, int valid, int base, V* v) {
     if (VEC && base + kGI <= valid) {
@@ -163,7 +185,7 @@ __device__ __forceinline__ void load_items(const V* __restrict__ src, int valid,
 }
 
 // Exclusive prefix sums over the block (thread order) of N values per
-// thread.  ws: N * kGW entries.
+// thread.  ws: N * kGW entries, 16-byte aligned.
 template <class A, int N>
 __device__ __forceinline__ void block_excl_sumN(A (&v)[N], A* ws) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -187,8 +209,19 @@ __device__ __forceinline__ void block_excl_sumN(A (&v)[N], A* ws) {
 #pragma unroll
     for (int u = 0; u < N; ++u) before[u] = A(0);
     for (int w = 0; w < warp; ++w) {
+        if constexpr ((N * sizeof(A)) % 16 == 0) {
+            A t[N];
 #pragma unroll
-        for (int u = 0; u < N; ++u) before[u] += ws[w * N + u];
+            for (int h = 0; h < (int)(N * sizeof(A) / 16); ++h) {
+                const uint4 raw = reinterpret_cast<const uint4*>(ws + w * N)[h];
+                memcpy(reinterpret_cast<unsigned char*>(t) + 16 * h, &raw, 16);
+            }
+#pragma unroll
+            for (int u = 0; u < N; ++u) before[u] += t[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < N; ++u) before[u] += ws[w * N + u];
+        }
     }
 #pragma unroll
     for (int u = 0; u < N; ++u) v[u] = before[u] + iv[u] - v[u];
@@ -227,7 +260,7 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
     constexpr int GQ = NV / 2;                 // query columns per chunk
     __shared__ Acc Ip[EVAL ? NV : 1][EVAL ? kPadTile : 1];
     __shared__ Acc kc[EVAL ? NV * 4 : 1];      // the chunk's scan constants
-    __shared__ Acc ws[NV * kGW];
+    __shared__ __align__(16) Acc ws[NV * kGW];
     __shared__ int wsi[32];
     __shared__ int red[4];
 
@@ -293,6 +326,10 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
     Acc g[kGI];
 #pragma unroll
     for (int j = 0; j < kGI; ++j) g[j] = Acc(0);
+    // the items holding the tile's last position, last head and first end
+    // (three threads of the block store the tile sums)
+    const int jv = own_item(valid - 1, base), jh = own_item(last_head, base), jf = own_item(first_end, base);
+    const bool owner = threadIdx.x == 0 || jv >= 0 || jh >= 0 || jf >= 0;
 
     for (int q0 = 0; q0 < p.k; q0 += GQ) {
         const int kq = min(GQ, p.k - q0);
@@ -331,19 +368,18 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
             // accumulation type (the values are formed in it): the scan over
             // tiles widens them as it reads, so this kernel issues no
             // conversions on the narrow FP64 pipe.
+            if (owner) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                if (v >= 2 * kq) continue;
-                Acc* sm = p.summ + (slot0 + v) * 3;
-                if (threadIdx.x == 0) {
-                    if (last_head < 0) sm[1] = 0;
-                    if (first_end == kNone) sm[2] = 0;
-                }
-#pragma unroll
-                for (int j = 0; j < kGI; ++j) {
-                    if (base + j == valid - 1) sm[0] = ip[j][v];
-                    if (base + j == last_head) sm[1] = ip[j][v] - y[j][v];
-                    if (base + j == first_end) sm[2] = ip[j][v];
+                for (int v = 0; v < NV; ++v) {
+                    if (v >= 2 * kq) continue;
+                    Acc* sm = p.summ + (slot0 + v) * 3;
+                    if (threadIdx.x == 0) {
+                        if (last_head < 0) sm[1] = 0;
+                        if (first_end == kNone) sm[2] = 0;
+                    }
+                    if (jv >= 0) sm[0] = pick(ip, jv, v);
+                    if (jh >= 0) sm[1] = pick(ip, jh, v) - pick(y, jh, v);
+                    if (jf >= 0) sm[2] = pick(ip, jf, v);
                 }
             }
         } else {
@@ -442,7 +478,7 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
     __shared__ Acc Ia[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
     __shared__ Acc Ib[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
     __shared__ Acc kc[EVAL ? CQ * 8 : 1];     // the pair's scan constants per column
-    __shared__ Acc ws[2 * CQ * kGW];
+    __shared__ __align__(16) Acc ws[2 * CQ * kGW];
     __shared__ int wsi[32];
     __shared__ int red[4];
 
@@ -508,6 +544,8 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
     Acc xt[kGI];
 #pragma unroll
     for (int j = 0; j < kGI; ++j) xt[j] = base + j < valid ? to_a(x[j], Acc()) - med : Acc(0);
+    const int jv = own_item(valid - 1, base), jh = own_item(last_head, base), jf = own_item(first_end, base);
+    const bool owner = threadIdx.x == 0 || jv >= 0 || jh >= 0 || jf >= 0;
 
     for (int q0 = 0; q0 < p.k; q0 += CQ) {
         const int kq = min(CQ, p.k - q0);
@@ -553,24 +591,23 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
 #pragma unroll
                 for (int u = 0; u < CQ; ++u) { ia[j][u] += off[u]; ib[j][u] += off[CQ + u]; }
             if (!EVAL) {
+                if (owner) {
 #pragma unroll
-                for (int u = 0; u < CQ; ++u) {
-                    if (u >= kq) continue;
-                    const int64_t slot = ((int64_t)c * p.T + t) * Q + (int64_t)(q0 + u) * P1 + s0;
-                    Acc* sm = p.summ + slot * 3;
-                    if (threadIdx.x == 0) {
-                        if (last_head < 0) { sm[1] = 0; sm[4] = 0; }
-                        if (first_end == kNone) { sm[2] = 0; sm[5] = 0; }
-                    }
-#pragma unroll
-                    for (int j = 0; j < kGI; ++j) {
-                        const Acc va = y[j][u] * pwa[j];
-                        if (base + j == valid - 1) { sm[0] = ia[j][u]; sm[3] = ib[j][u]; }
-                        if (base + j == last_head) {
-                            sm[1] = ia[j][u] - va;
-                            sm[4] = ib[j][u] + va * xt[j];
+                    for (int u = 0; u < CQ; ++u) {
+                        if (u >= kq) continue;
+                        const int64_t slot = ((int64_t)c * p.T + t) * Q + (int64_t)(q0 + u) * P1 + s0;
+                        Acc* sm = p.summ + slot * 3;
+                        if (threadIdx.x == 0) {
+                            if (last_head < 0) { sm[1] = 0; sm[4] = 0; }
+                            if (first_end == kNone) { sm[2] = 0; sm[5] = 0; }
                         }
-                        if (base + j == first_end) { sm[2] = ia[j][u]; sm[5] = ib[j][u]; }
+                        if (jv >= 0) { sm[0] = pick(ia, jv, u); sm[3] = pick(ib, jv, u); }
+                        if (jh >= 0) {
+                            const Acc va = pick(y, jh, u) * pick1(pwa, jh);
+                            sm[1] = pick(ia, jh, u) - va;
+                            sm[4] = pick(ib, jh, u) + va * pick1(xt, jh);
+                        }
+                        if (jf >= 0) { sm[2] = pick(ia, jf, u); sm[5] = pick(ib, jf, u); }
                     }
                 }
             } else {
