@@ -397,18 +397,27 @@ __global__ void __launch_bounds__(kGT) grad_tile_kernel(GradParams<DT> p) {
 #pragma unroll
             for (int j = 0; j < kGI; ++j) {
                 if (base + j >= valid) continue;
+                // a point alone in its tie group: both prefixes are this
+                // thread's own (the exclusive one is the previous item's)
+                const bool single = a[j] == base + j && b[j] == base + j;
                 const bool ain = a[j] >= 0, bin = b[j] != kNone;
                 const int sel = (ain ? 2 : 0) + (bin ? 1 : 0);
                 const int ah = a[j] - 1 + ((a[j] - 1) >> 5), bh = b[j] + (b[j] >> 5);
 #pragma unroll
                 for (int u = 0; u < GQ; ++u) {
                     Acc Sz = kc[8 * u + sel], Sw = kc[8 * u + 4 + sel];
-                    if (ain && a[j] > 0) { Sz += Ip[2 * u][ah]; Sw += Ip[2 * u + 1][ah]; }
-                    if (bin) { Sz += Ip[2 * u][bh]; Sw += Ip[2 * u + 1][bh]; }
+                    if (single) {
+                        Sz += (j > 0 ? ip[j - 1][2 * u] : off[2 * u]) + ip[j][2 * u];
+                        Sw += (j > 0 ? ip[j - 1][2 * u + 1] : off[2 * u + 1]) + ip[j][2 * u + 1];
+                    } else {
+                        if (ain && a[j] > 0) { Sz += Ip[2 * u][ah]; Sw += Ip[2 * u + 1][ah]; }
+                        if (bin) { Sz += Ip[2 * u][bh]; Sw += Ip[2 * u + 1][bh]; }
+                    }
                     g[j] += y[j][2 * u + 1] * Sz + y[j][2 * u] * Sw;
                 }
             }
-            __syncthreads();
+            // (Ip and kc are next written after the next chunk's block scan,
+            // whose barriers order those writes after these reads)
         }
     }
     if (EVAL) {
@@ -642,7 +651,8 @@ __global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
                         g[j][u] += w0 * S0 + w1 * S1;
                     }
                 }
-                __syncthreads();
+                // (Ia, Ib and kc are next written after the next pair's block
+                // scan, whose barriers order those writes after these reads)
             }
             // next pair: (-x~)^(s0 + 2)
 #pragma unroll
