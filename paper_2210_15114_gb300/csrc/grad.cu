@@ -477,13 +477,15 @@ __device__ __forceinline__ void add_orow(Out* o, int kq, bool vec, const Out (&g
         if (u < kq) out_add(o + u, g[u]);
 }
 
-template <dm_dtype DT, bool EVAL, bool VEC>
-__global__ void __launch_bounds__(kGT) oddp_tile_kernel(OddParams<DT> p) {
+// CQ: query columns per chunk.  The FP32 tile-sum pass fits 3 blocks per SM
+// in registers; the evaluation pass (more state per column) runs 2.
+template <dm_dtype DT, bool EVAL, bool VEC, int CQ>
+__global__ void __launch_bounds__(kGT, (!EVAL && sizeof(typename Types<DT>::Acc) == 4) ? 3 : 2)
+oddp_tile_kernel(OddParams<DT> p) {
     using V = typename Types<DT>::V;
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
-    constexpr int CQ = OddCq<DT>::value;
     __shared__ Acc Ia[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
     __shared__ Acc Ib[EVAL ? CQ : 1][EVAL ? kPadTile : 1];
     __shared__ Acc kc[EVAL ? CQ * 8 : 1];     // the pair's scan constants per column
@@ -994,10 +996,13 @@ cudaError_t oddp_stage_t(const OddArgs& a, int stage, cudaStream_t s, int64_t* l
     p.cst = reinterpret_cast<const Acc*>(sc + L.cst);
     p.out = static_cast<Out*>(a.out);
     p.ldo = a.ldo;
+    // 16 bytes of accumulator per chunk in both passes (2 FP32 columns per
+    // chunk in the evaluation pass measured slower: twice the block scans)
     constexpr int CQ = OddCq<DT>::value;
-    const size_t zrow = sizeof(V) * CQ;   // bytes of one vector load of a row chunk
-    p.zvec = a.ldz % CQ == 0 && reinterpret_cast<uintptr_t>(a.Z) % zrow == 0;
-    p.ovec = a.ldo % CQ == 0 && reinterpret_cast<uintptr_t>(a.out) % (sizeof(Out) * CQ) == 0;
+    const int cq = CQ;
+    const size_t zrow = sizeof(V) * cq;   // bytes of one vector load of a row chunk
+    p.zvec = a.ldz % cq == 0 && reinterpret_cast<uintptr_t>(a.Z) % zrow == 0;
+    p.ovec = a.ldo % cq == 0 && reinterpret_cast<uintptr_t>(a.out) % (sizeof(Out) * cq) == 0;
     long long cb = 1;
     for (int t = 0; t < 16; ++t) {
         p.coef[t] = t <= a.p ? (Acc)cb : Acc(0);
@@ -1009,15 +1014,15 @@ cudaError_t oddp_stage_t(const OddArgs& a, int stage, cudaStream_t s, int64_t* l
                      reinterpret_cast<uintptr_t>(a.xs) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(a.perm) % 16 == 0;
     if (stage == 0) {
-        if (vec) oddp_tile_kernel<DT, false, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
-        else oddp_tile_kernel<DT, false, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        if (vec) oddp_tile_kernel<DT, false, true, CQ><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        else oddp_tile_kernel<DT, false, false, CQ><<<(unsigned)blocks, kGT, 0, s>>>(p);
     } else if (stage == 1) {
         grad_scan_kernel<Wide, Acc><<<(unsigned)(a.d * L.Q), kGT, 0, s>>>(
             p.flags, p.summ, reinterpret_cast<Wide*>(sc + L.pre), reinterpret_cast<Acc*>(sc + L.cst),
             a.n, L.T, (int)L.Q);
     } else {
-        if (vec) oddp_tile_kernel<DT, true, true><<<(unsigned)blocks, kGT, 0, s>>>(p);
-        else oddp_tile_kernel<DT, true, false><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        if (vec) oddp_tile_kernel<DT, true, true, CQ><<<(unsigned)blocks, kGT, 0, s>>>(p);
+        else oddp_tile_kernel<DT, true, false, CQ><<<(unsigned)blocks, kGT, 0, s>>>(p);
     }
     *launches += 1;
     return cudaGetLastError();
