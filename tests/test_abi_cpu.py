@@ -82,6 +82,11 @@ def test_argument_checks_without_device(lib):
     assert lib.dm_l2sq_matmat_noalloc(0, dummy, 0, 2, 2, dummy, 1, 1, dummy, 1, None) == 1
     assert lib.dm_l2sq_matmat_noalloc(0, dummy, 10, 33, 33, dummy, 1, 1, dummy, 1, None) == 2
     assert lib.dm_l2sq_matmat_noalloc(0, dummy, 10, 2, 2, dummy, 33, 33, dummy, 33, None) == 2
+    # ||.||_p^p plans: p = 2..16 even, 3..15 odd; the power is checked before
+    # the context is used (a dummy context pointer is never dereferenced)
+    for pw in (-3, 0, 1, 17, 18, 19):
+        assert lib.dm_prepare_lpp(dummy, 0, dummy, 10, 2, 2, pw, ctypes.byref(h)) == 1, pw
+        assert not h.value
 
 
 def test_create_without_gpu_fails_cleanly(lib):
