@@ -255,12 +255,18 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
     // warp*32*ITEMS + j*32 + l, so ranking items in (j, lane) order is the
     // original order.  Positions past n get digit 255 and land after every
     // real key of the tile; their global positions are >= n and are dropped.
+    // Tile-relative indices in 32 bits (n < 2^30): base pointers of the column
+    // and of the tile are formed once.
+    const uint32_t n32 = (uint32_t)n;
+    const uint32_t rem = (uint32_t)(n - tile0);           // positions left in the column
+    const uint32_t lbase = (uint32_t)(warp * 32 * ITEMS + lane);
+    const Key* kin = keys_in + seg + tile0;
     Key key[ITEMS];
     uint32_t rank[ITEMS];
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const int64_t gi = tile0 + warp * 32 * ITEMS + j * 32 + lane;
-        key[j] = gi < n ? keys_in[seg + gi] : ~(Key)0;
+        const uint32_t li = lbase + 32u * j;
+        key[j] = li < rem ? kin[li] : ~(Key)0;
     }
     // Stable ranks within the warp: item j of every lane is ranked after all
     // items j' < j of the warp and after lower lanes' item j.  All matches are
@@ -342,28 +348,31 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
         rank[j] += tile_start[dg] + wcount[warp][dg];
         sk[rank[j]] = key[j];
     }
+    const int32_t* vin = first ? nullptr : vals_in + seg + tile0;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const int64_t gi = tile0 + warp * 32 * ITEMS + j * 32 + lane;
-        sv[rank[j]] = gi < n ? (first ? (int32_t)gi : vals_in[seg + gi]) : -1;
+        const uint32_t li = lbase + 32u * j;
+        sv[rank[j]] = li < rem ? (first ? (int32_t)(tile0 + li) : vin[li]) : -1;
     }
     __syncthreads();
 
+    Key* kout = last ? nullptr : keys_out + seg;
+    int32_t* vout = last ? perm_out + seg : vals_out + seg;
+    V* sout = last ? sorted_out + seg : nullptr;
 #pragma unroll 4
     for (int pos = tid; pos < TILE; pos += kThreads) {
         const Key k = sk[pos];
         const uint32_t dg = (uint32_t)(k >> shift) & 0xffu;
         const uint32_t gp = gbase[dg] + (uint32_t)pos;
-        if ((int64_t)gp < n) {
+        if (gp < n32) {
             if (last) {
                 V v;
                 from_key(k, &v);
-                sorted_out[seg + gp] = v;
-                perm_out[seg + gp] = sv[pos];
+                sout[gp] = v;
             } else {
-                keys_out[seg + gp] = k;
-                vals_out[seg + gp] = sv[pos];
+                kout[gp] = k;
             }
+            vout[gp] = sv[pos];
         }
     }
 }
