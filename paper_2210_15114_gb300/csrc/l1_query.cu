@@ -57,8 +57,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
 template <dm_dtype DT, int KC>
 struct QCfg {
     using V = typename Types<DT>::V;
@@ -72,7 +70,6 @@ struct QCfg {
     static constexpr int SEGS = kThreads / NQ;
     static constexpr int SEG_LEN = sizeof(Acc) == 8 ? 4 : 8;
     static constexpr int TILE_E = SEGS * SEG_LEN;              // sorted positions per tile
-    static constexpr int ROWB = KC * (int)sizeof(V);           // bytes of one Zg row
     static constexpr int NV = 2 * KC;                          // scanned quantities
     static_assert(KC % QW == 0, "tile shape");
 };
@@ -107,22 +104,6 @@ struct QParams {
 };
 
 // ---------------------------------------------------------------- helpers
-__device__ __forceinline__ void cp_async16(void* s, const void* g, int src) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(sa), "l"(g), "r"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* s, const void* g, int src) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(sa), "l"(g), "r"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* s, const void* g, int src) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(sa), "l"(g), "r"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 __device__ __forceinline__ float diff(float a, float b) { return a - b; }
 __device__ __forceinline__ double diff(double a, double b) { return a - b; }
 __device__ __forceinline__ long long diff(int32_t a, int32_t b) { return (long long)a - (long long)b; }
