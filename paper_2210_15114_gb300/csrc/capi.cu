@@ -1262,16 +1262,18 @@ dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const vo
         DM_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
         DM_TRY_CUDA(cudaEventCreateWithFlags(&ctx->aux_done, cudaEventDisableTiming));
     }
-    // Z travels on the second stream while X is copied and preprocessed; the
-    // product waits for it.  (The second stream first waits for earlier work
-    // on the context's stream, which may still read the previous Z.)
+    // X crosses the host link first, alone and at the link's full rate, so
+    // preprocessing starts as early as possible; Z follows on the second
+    // stream while X is preprocessed, and the product waits for it.  (The
+    // second stream waits for the X copy, and with it for earlier work on the
+    // context's stream, which may still read the previous Z.)
+    DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hx, d * es, Xh, ldx * es, d * es, n, cudaMemcpyHostToDevice,
+                                  ctx->stream));
     DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->stream));
     DM_TRY_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->aux_done, 0));
     DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hz, k * es, Zh, ldz * es, k * es, n, cudaMemcpyHostToDevice,
                                   ctx->aux));
     DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->aux));
-    DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hx, d * es, Xh, ldx * es, d * es, n, cudaMemcpyHostToDevice,
-                                  ctx->stream));
     dm_plan* p = nullptr;
     DM_TRY(dm_prepare(ctx, metric, dtype, ctx->hx, n, d, d, &p));
     DM_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->aux_done, 0));
