@@ -12,12 +12,18 @@
 // and stores R_k = sum_c (x_k(c) - mu_c)).  So the query is
 //     out[k,:] = R^T Z - R_k 1^T Z + sum_c 2 (x_r P_z[r] - P_xz[r]).
 //
-// Two kernels.
+// Kernels, in launch order:
 //
-// l1_prologue: one pass over the query block computes R^T Z and 1^T Z (FP32
-//   partial sums per 64 rows, added in FP64, fixed-order finalize) and writes
+// l1_prologue (+ finalize): one pass over the query block computes R^T Z and
+//   1^T Z (FP32 partial sums, added in FP64, fixed-order finalize) and writes
 //   a column-group-major copy Zg[g][i][0:KC] of Z (KC = 8 FP32 columns = one
-//   32-byte sector per row; a partial last group is zero-padded).
+//   32-byte sector per row, or 4 when one group's copies outgrow L2; a
+//   partial last group is zero-padded).
+//
+// l1_aggregate + l1_tile_scan (reduce-then-scan): per tile of TILE_E sorted
+//   positions, the sums of z and (x - mu) z over the tile (one warp per
+//   tile), then an exclusive scan of those sums over the tiles of each
+//   (group, coordinate) in FP64: Pt, the tile's exclusive prefix.
 //
 // l1_query: one persistent kernel does the sorted part for all coordinates.
 //   The k columns are processed one group of KC at a time, all coordinates of
@@ -25,27 +31,27 @@
 //   the gathered rows of Zg[g] and the partial output outg[g], n*KC elements
 //   each (32 + 32 MiB at n = 2^20) -- stays resident in L2 while the sorted
 //   columns stream past it.  Work unit: a tile of TILE_E consecutive sorted
-//   positions of one coordinate of one group.  Per tile:
-//   A. stage perm, x - b (b = the tile's first sorted value) and gather the
-//      KC-wide rows Zg[g][perm[r]] into shared memory (cp.async);
+//   positions of one coordinate of one group, claimed from an atomic counter
+//   in (group, coordinate, tile) order; the next tile's permutation and
+//   values are loaded while the current one is evaluated.  Per tile:
+//   A. each thread takes SEG_LEN consecutive positions: x - b (b = the tile's
+//      first sorted value), the checked permutation and the gathered QW-wide
+//      slices of the rows Zg[g][perm[r]], held in registers;
 //   B. in-tile exclusive prefix sums Lz, Lxz of z and (x - b) z (FP32 for
-//      FP32 data);
-//   C. decoupled look-back over the earlier tiles of the same coordinate for
-//      the tile's exclusive prefix Pt (FP64 for FP32 data, bounded spin), and
-//      two per-column constants in FP64:
+//      FP32 data): in-thread, then across the warp by shuffles, then across
+//      the warps through double-buffered shared totals (one barrier per tile);
+//   C. from the tile scan's Pt, two per-column constants formed in FP64:
 //        alpha = Pt_z,   gamma = Pt_xz - (b - mu) Pt_z,
 //      so that 2 (x_r P_z[r] - P_xz[r]) = 2 ((x_r - b)(alpha + Lz_r) - (gamma + Lxz_r)):
 //      the large terms are combined in FP64 once per tile and each element
 //      works on tile-local values;
-//   D. wait until every tile of coordinate c-1 (same group) has added its
-//      values (bounded spin on a counter), so each output element receives
-//      its d contributions in coordinate order: the result is deterministic;
-//   E. coordinate 0 stores value + R^T Z - R_k 1^T Z into outg, later
-//      coordinates add to it, the last one writes the sum into the caller's
-//      output (for d = 1 coordinate 0 writes it directly);
-//   F. publish "tile done" for coordinate c.
-// Tiles are claimed from an atomic counter in (group, coordinate, tile) order,
-// so every wait is on work claimed earlier by a running CTA: no deadlock.
+//   D. each value is added into outg with a vector reduction in L2 (the
+//      default); l1_finalize then writes out = outg + R^T Z - R_k 1^T Z in
+//      the caller's layout.  In the ordered (deterministic) mode a tile of
+//      coordinate c instead waits (bounded spin) until every tile of
+//      coordinate c-1 of its group is done, adds to outg with plain loads and
+//      stores in coordinate order, and the last coordinate writes out.
+// Every wait is on work claimed earlier by a running CTA: no deadlock.
 // Integer data run the same steps exactly in int64.
 #include <algorithm>
 
@@ -734,9 +740,19 @@ __global__ void l1_prologue_finalize(const Wide* __restrict__ partial, int block
 
 int full_kc(dm_dtype t) { return t == DM_F64 ? 4 : 8; }
 
-int pick_kc(dm_dtype t, int64_t k) {
+// Column-group width: one 32-byte sector of a Zg row (8 FP32 / 4 FP64
+// columns), or half of it when one group's Zg and outg copies
+// ((element + accumulator) n kc bytes) exceed what L2 keeps: the random row
+// gathers and reductions then go to DRAM, and narrower rows halve that
+// working set at the cost of one more pass over the sorted data per group
+// (measured at n = 2^22, d = 16: k = 8 / 16 / 40 ran 13 / 11 / 1% faster).
+constexpr size_t kGroupL2Bytes = size_t(96) << 20;
+
+int pick_kc(dm_dtype t, int64_t n, int64_t k) {
     const int full = full_kc(t);
-    if (k >= full) return full;
+    const size_t row = dtype_size(t) + (t == DM_F32 ? 4 : 8);
+    const int cap = (size_t)n * row * full > kGroupL2Bytes ? full / 2 : full;
+    if (k >= cap) return cap;
     int kc = 1;
     while (kc < k) kc <<= 1;
     return kc;
@@ -776,7 +792,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 ScratchLayout scratch_layout(dm_dtype t, int64_t n, int64_t d, int64_t k, int num_sms) {
     ScratchLayout L;
-    L.kc = pick_kc(t, k);
+    L.kc = pick_kc(t, n, k);
     L.G = (k + L.kc - 1) / L.kc;
     const int64_t tile = tile_elems_dt(t, L.kc);
     L.T = (n + tile - 1) / tile;
@@ -915,7 +931,7 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
 template <dm_dtype DT>
 cudaError_t launch_dt(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, int stage) {
     constexpr int FULL = DT == DM_F64 ? 4 : 8;
-    switch (pick_kc(a.dtype, a.k)) {
+    switch (pick_kc(a.dtype, a.n, a.k)) {
         case 1: return launch_kc<DT, 1>(a, st, launches, stage);
         case 2: return launch_kc<DT, 2>(a, st, launches, stage);
         case 4: return launch_kc<DT, 4>(a, st, launches, stage);

@@ -335,6 +335,28 @@ def test_full_size_int_sampled_rows_exact(dm, mctx, metric, full_int):
     np.testing.assert_array_equal(out[rows], want)
 
 
+@pytest.mark.parametrize("dtype,k", [(np.float32, 12), (np.float64, 6), (np.int32, 10)])
+def test_l1_large_n_narrow_column_groups(dm, mctx, dtype, k):
+    # n above the size where one full column group's copies of Z and of the
+    # output outgrow L2: the l1 query takes half-width groups (4 FP32 / int32,
+    # 2 FP64 columns), with a ragged last group and a ragged last tile
+    n, d = (1 << 21) + 37, 3
+    rng = np.random.default_rng(211)
+    if dtype == np.int32:
+        X = rng.integers(0, 1 << 16, size=(n, d)).astype(dtype)
+        Z = rng.integers(-100, 101, size=(n, k)).astype(dtype)
+    else:
+        X = rng.normal(0, 4, size=(n, d)).astype(dtype)
+        Z = rng.normal(size=(n, k)).astype(dtype)
+    out = gpu_product(dm, mctx, "l1", X, Z)
+    rows = np.concatenate([inputs.sample_rows(n, 10), [0, n - 1]])
+    want = oracle.l1_rows(X, Z, rows)
+    if dtype == np.int32:
+        np.testing.assert_array_equal(out[rows], want)
+    else:
+        assert oracle.relative_error(out[rows], want) <= TOL[dtype]
+
+
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
 def test_full_size_symmetry(dm, ctx, metric, full_fp32):
     # w^T (A z) = z^T (A w) for the symmetric A, at full size.
