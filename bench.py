@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true", help="skip the variant measurements")
     ap.add_argument("--grad-n", type=int, default=1 << 21)
     ap.add_argument("--grad-d", type=int, default=64)
+    ap.add_argument("--engine", choices=["auto", "cuda", "tensor"], default="auto",
+                    help="units of the squared-l2 contraction (dm_set_engine)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warmup + steps only (for profiler captures); print nothing else")
     return ap.parse_args()
@@ -74,7 +76,8 @@ def workload_config(a, flush):
     return {"workload": f"gaussian-mixture-16 n={a.n} d={a.d} k={a.k} fp32",
             "n": a.n, "d": a.d, "k": a.k, "clusters": 16, "dtype": "fp32",
             "products": ["l1", "l2sq"], "prepare_in_step": True, "l2_flush": flush,
-            "l1_accumulation": "L2 reductions (dm_set_deterministic off)"}
+            "l1_accumulation": "L2 reductions (dm_set_deterministic off)",
+            "l2_engine": getattr(a, "engine", "auto")}
 
 
 def dist_env():
@@ -600,6 +603,7 @@ def main():
     flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)   # 512 MiB > L2
     stream = torch.cuda.current_stream(dev)
     ctx = dm.dm_create(local, stream.cuda_stream)
+    dm.dm_set_engine(ctx, a.engine)
 
     def step():
         p1 = dm.dm_prepare(ctx, "l1", Xd)

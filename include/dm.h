@@ -88,6 +88,19 @@ dm_status dm_set_stream(dm_ctx* ctx, void* cuda_stream);
  * data are deterministic in both settings (integer sums are exact). */
 dm_status dm_set_deterministic(dm_ctx* ctx, int on);
 
+/* Units that run the squared-l2 contraction [X - mu, 1, s]^T Z (Appendix A,
+ * the reduce step of DM_L2SQ products, of their gradients and of even-p
+ * DM_LPP products).  DM_ENGINE_TENSOR_CORES: FP32 data with d + 2 <= 128 and
+ * column blocks the kernel's shared memory holds run on the tensor cores
+ * (tcgen05, TF32 operands split as hi + lo, three products per term, FP32
+ * accumulation drained every 64 points, FP64 across runs); other shapes and
+ * types keep the CUDA-core kernel.  DM_ENGINE_CUDA_CORES: always the
+ * CUDA-core kernel.  DM_ENGINE_AUTO (the default): the tensor cores only for
+ * the shapes where they measured faster.  Results agree with the FP64 oracle
+ * within the FP32 tolerance either way; the bits differ between engines. */
+typedef enum { DM_ENGINE_AUTO = 0, DM_ENGINE_CUDA_CORES = 1, DM_ENGINE_TENSOR_CORES = 2 } dm_engine;
+dm_status dm_set_engine(dm_ctx* ctx, dm_engine engine);
+
 /* Preprocess a point set (Algorithm 1, Section 2, for DM_L1; Appendix A for
  * DM_L2SQ).
  *   DM_L1:   every coordinate column of X is sorted ascending with a stable

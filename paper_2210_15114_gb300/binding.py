@@ -64,6 +64,7 @@ def load() -> ctypes.CDLL:
             "dm_destroy": ([P], None),
             "dm_set_stream": ([P, P], I32),
             "dm_set_deterministic": ([P, I32], I32),
+            "dm_set_engine": ([P, I32], I32),
             "dm_prepare": ([P, I32, I32, P, I64, I64, I64, ctypes.POINTER(P)], I32),
             "dm_plan_destroy": ([P], None),
             "dm_matvec_l1": ([P, P, P], I32),
@@ -196,6 +197,17 @@ def dm_set_stream(ctx: Context, stream) -> None:
 
 def dm_set_deterministic(ctx: Context, on: bool = True) -> None:
     _check(load().dm_set_deterministic(ctx.handle, 1 if on else 0), "dm_set_deterministic")
+
+
+ENGINES = {"auto": 0, "cuda": 1, "tensor": 2}
+
+
+def dm_set_engine(ctx: Context, engine: str = "auto") -> None:
+    """dm_set_engine: units of the squared-l2 contraction ("auto", "cuda" for
+    the CUDA cores, "tensor" for the tensor cores where the shape allows)."""
+    if engine not in ENGINES:
+        raise DMError(DM_ERR_INVALID_ARG, f"engine must be one of {sorted(ENGINES)}")
+    _check(load().dm_set_engine(ctx.handle, ENGINES[engine]), "dm_set_engine")
 
 
 def dm_prepare(ctx: Context, metric, X) -> Plan:

@@ -26,6 +26,7 @@ struct dm_ctx {
     size_t host_hist_words = 0;
     int64_t launches = 0;
     int deterministic = 0;           // dm_set_deterministic
+    int engine = DM_ENGINE_AUTO;     // dm_set_engine
     // Device buffers of dm_matmat_host (grown on demand), and the stream and
     // event its copy of Z uses to overlap the preprocessing.
     void* hx = nullptr; size_t hx_bytes = 0;
@@ -468,8 +469,10 @@ size_t matmat_scratch(const dm_plan* p, int64_t k) {
         k = std::max<int64_t>(1, l2_chunk(p, k));
     }
     ReduceArgs r{};
+    r.dtype = p->dtype;
     r.n = p->n; r.d = D; r.k = k;
     r.num_sms = p->ctx->num_sms;
+    r.engine = p->ctx->engine;
     const size_t o_res = up16((size_t)reduce_blocks(r) * (D + 2) * k * 8);
     return feat + up16(o_res + (size_t)(D + 2) * k * 8);
 }
@@ -500,6 +503,8 @@ dm_status lpp_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t l
         r.Z = static_cast<const unsigned char*>(Z) + (size_t)j0 * dtype_size(t);
         r.k = kk; r.ldz = ldz;
         r.num_sms = ctx->num_sms;
+        r.err = ctx->err;
+        r.engine = ctx->engine;
         const size_t o_res = up16((size_t)reduce_blocks(r) * (D + 2) * kk * 8);
         r.partial = base;
         r.res = base + o_res;
@@ -597,6 +602,8 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
         r.Z = static_cast<const unsigned char*>(Z) + (size_t)j0 * dtype_size(t);
         r.k = kk; r.ldz = ldz;
         r.num_sms = ctx->num_sms;
+        r.err = ctx->err;
+        r.engine = ctx->engine;
         const int blocks = reduce_blocks(r);
         const size_t o_res = up16((size_t)blocks * (d + 2) * kk * 8);
         unsigned char* base = e.scratch;
@@ -686,6 +693,8 @@ dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64
     r.n = n; r.d = d;
     r.k = 2 * k; r.ldz = 2 * k;
     r.num_sms = ctx->num_sms;
+    r.err = ctx->err;
+    r.engine = ctx->engine;
     const int blocks = reduce_blocks(r);
     const size_t o_res = up16(gbytes + (size_t)blocks * (d + 2) * 2 * k * 8);
     DM_TRY(ensure_arena(ctx, up16(o_res + (size_t)(d + 2) * 2 * k * 8)));
@@ -970,6 +979,13 @@ void dm_destroy(dm_ctx* ctx) {
 dm_status dm_set_deterministic(dm_ctx* ctx, int on) {
     if (!ctx) return DM_ERR_INVALID_ARG;
     ctx->deterministic = on ? 1 : 0;
+    return DM_OK;
+}
+
+dm_status dm_set_engine(dm_ctx* ctx, dm_engine engine) {
+    if (!ctx || (engine != DM_ENGINE_AUTO && engine != DM_ENGINE_CUDA_CORES && engine != DM_ENGINE_TENSOR_CORES))
+        return DM_ERR_INVALID_ARG;
+    ctx->engine = engine;
     return DM_OK;
 }
 

@@ -99,6 +99,8 @@ struct ReduceArgs {
     void* res;                           // (d+2) x k Wide
     int num_sms;
     int max_blocks;                      // 0: no cap beyond the default
+    uint32_t* err;                       // device error word (may be null)
+    int engine;                          // dm_engine: the contraction's units
 };
 bool reduce_supported(int64_t d, int64_t k);   // any element type (FP64 worst case)
 int64_t reduce_max_k(dm_dtype t, int64_t d);   // columns per launch for this type

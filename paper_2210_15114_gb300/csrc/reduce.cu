@@ -29,6 +29,7 @@ namespace dm {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 128;  // rows staged in shared memory per step
 constexpr int RC = 4;        // output rows (of X-hat) per thread
 constexpr int RJ = 4;        // output columns (of Z) per thread
@@ -327,6 +328,318 @@ __global__ void reduce_finalize_kernel(const Wide* __restrict__ partial, int blo
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) res[w] = acc;
+}
+
+// --------------------------------------------------- reduce on tensor cores
+// FP32 data: the same contraction [X - mu, 1, s]^T Z on the 5th-generation
+// tensor cores (tcgen05.mma, kind::tf32), accumulated in tensor memory.
+//
+// Operands live in shared memory in the canonical K-major layout without
+// swizzle; the contraction index K runs over the points:
+//   A: M = 128 rows, the d + 2 rows of [X - mu, 1, s]^T (zero padded),
+//   B: N = k rounded up to 16 rows, the columns of Z (zero padded),
+//   K = 64 points per chunk, 8 per instruction.
+// Element (r, p) of a tile sits at byte (r / 8) * SBO + (p / 4) * LBO +
+// (r % 8) * 16 + (p % 4) * 4: core matrices of 8 rows x 16 bytes, adjacent
+// along K (LBO = 128 bytes), 8-row groups SBO = 16 * 128 bytes apart.
+//
+// Precision (split precision on TF32 tensor cores): every operand is split
+// into two TF32 parts, v = hi + lo with hi = tf32(v) and lo = tf32(v - hi)
+// (about 21 significant bits together), and each product is formed as
+// hi*hi + hi*lo + lo*hi (three MMAs; lo*lo lies below FP32 resolution).
+// The tensor core's FP32 accumulation drifts with the number of additions
+// (measured: relative error 5e-6 after 1024 points, 1.2e-6 after 256,
+// 3.5e-7 after 64), so an accumulator in TMEM holds one chunk of 64 points
+// only: each chunk's D is read into FP32 registers (round-to-nearest adds),
+// and those go into the CTA's FP64 partial of its segment every kTcRun
+// points (the length of the CUDA-core kernel's FP32 runs); a finalize adds
+// the partials in a fixed order.
+//
+// Pipeline (one CTA per SM): two operand sets and two accumulators.  Chunk
+// c's raw rows arrive by cp.async during chunk c - 1; all threads form s and
+// the split operands of chunk c in set c % 2 once the MMAs of chunk c - 2
+// (which read that set and wrote accumulator c % 2) have completed -- a
+// bounded mbarrier wait (DM_ERR_TIMEOUT on expiry), after which warps 0-3
+// read that accumulator (the TMEM lanes each warp may access); one thread
+// then issues chunk c's 24 MMAs and commits them to the set's mbarrier, and
+// the tensor core runs them while chunk c + 1 is prepared.
+constexpr int kTcM = 128;                        // MMA M: rows of [X - mu, 1, s]^T
+constexpr int kTcK = 64;                         // points per chunk
+constexpr int kTcRun = 1024;                     // points per FP32 register run
+constexpr uint32_t kTcLbo = 128;                 // bytes between core matrices along K
+constexpr uint32_t kTcSbo = (kTcK / 4) * 128;    // bytes between 8-row groups
+static_assert(kTcK * 4 == kThreads, "four threads per point form s");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row group) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((kTcLbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((kTcSbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+// Bounded wait for the mbarrier phase of parity `parity` (test_wait does not
+// block, so the bound is the iteration count times the sleep).
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Four values of row r, points 4 g4 .. 4 g4 + 3, as their hi and lo parts.
+__device__ __forceinline__ void tc_put4(unsigned char* hi, unsigned char* lo, int r, int g4,
+                                        const float (&v)[4]) {
+    float h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { h[i] = tf32_rna(v[i]); l[i] = tf32_rna(v[i] - h[i]); }
+    const size_t off = (size_t)(r >> 3) * kTcSbo + (size_t)g4 * kTcLbo + (size_t)(r & 7) * 16;
+    *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+}
+
+size_t tc_smem_bytes(int d, int k) {
+    const int N = (k + 15) / 16 * 16;
+    return 2 * (2 * (size_t)kTcM * kTcK * 4 + 2 * (size_t)N * kTcK * 4) +
+           4 * (2 * (size_t)kTcK * d + 2 * (size_t)kTcK * k + kTcK + d) + 48;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ldx,
+                 const float* __restrict__ mu, int64_t mu_stride, int with_s,
+                 const float* __restrict__ Z, int k, int64_t ldz, double* __restrict__ partial,
+                 int64_t nseg, int64_t seg_rows, int N, uint32_t tmem_cols, int xv16, int zv16,
+                 uint32_t* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D2 = d + 2;
+    // Two operand sets (chunk c fills set c % 2 while the tensor core works
+    // on chunk c - 1) and two accumulators in TMEM (columns [b N, b N + N)).
+    const size_t a_bytes = (size_t)kTcM * kTcK * 4, b_bytes = (size_t)N * kTcK * 4;
+    const size_t set_bytes = 2 * a_bytes + 2 * b_bytes;
+    float* xraw = reinterpret_cast<float*>(smem_raw + 2 * set_bytes);   // [2][kTcK][d]
+    float* zraw = xraw + 2 * kTcK * d;                                    // [2][kTcK][k]
+    float* s_buf = zraw + 2 * kTcK * k;                                   // [kTcK]
+    float* mu_s = s_buf + kTcK;                                           // [d]
+    const uintptr_t tail = (reinterpret_cast<uintptr_t>(mu_s + d) + 7) & ~uintptr_t(7);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);                   // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+    for (size_t i = tid; i < 2 * set_bytes / 16; i += kThreads)
+        reinterpret_cast<uint4*>(smem_raw)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int c = tid; c < d; c += kThreads) mu_s[c] = mu ? mu[c * mu_stride] : 0.f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // instruction descriptor: D FP32, A and B TF32, both K-major, N, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+                           ((uint32_t)(kTcM >> 4) << 24);
+    // descriptors of the first K step of each tile of set 0; set 1 and a K
+    // step (256 bytes) add to the address field (16-byte units; every shared
+    // address stays below 2^18, so the field does not carry)
+    const uint32_t base0 = smem_u32(smem_raw);
+    const uint64_t dah = tc_desc(base0), dal = tc_desc(base0 + (uint32_t)a_bytes);
+    const uint64_t dbh = tc_desc(base0 + 2 * (uint32_t)a_bytes);
+    const uint64_t dbl = tc_desc(base0 + 2 * (uint32_t)a_bytes + (uint32_t)b_bytes);
+    const uint64_t set_step = (uint64_t)(set_bytes >> 4);
+    uint32_t parity = 0u, pending = 0u;   // bit b: operand set / accumulator b
+    bool failed = false;
+    uint32_t gch = 0;        // chunks this CTA has filled (selects the operand set)
+
+    // Warps 0-3: row m = 32 warp + lane of D, up to 64 columns, summed over
+    // the chunks of a run in FP32 registers.
+    float facc[4][16];
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) facc[cb][q] = 0.f;
+    // Wait for the MMAs that read operand set b and wrote accumulator b, then
+    // add that accumulator into facc.  Uniform across the CTA; false on expiry.
+    auto retire = [&](int b) -> bool {
+        const bool was = (pending >> b) & 1u;
+        bool ok = true;
+        if (was) { ok = tc_wait(smem_u32(mbar + b), (parity >> b) & 1u); parity ^= 1u << b; }
+        if (__syncthreads_or(!ok)) return false;
+        if (was) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (warp < 4) {
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    if (cb * 16 < N) {
+                        float v[16];
+                        tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * N + cb * 16), v);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) facc[cb][q] += v[q];
+                    }
+                }
+            }
+            pending &= ~(1u << b);
+        }
+        return true;
+    };
+
+    for (int64_t seg = blockIdx.x; seg < nseg && !failed; seg += gridDim.x) {
+        const int64_t s0 = seg * seg_rows, s1 = min64(n, s0 + seg_rows);
+        double* part = partial + seg * (int64_t)D2 * k;
+        bool first_run = true;
+        for (int64_t r0 = s0; r0 < s1 && !failed; r0 += kTcRun) {
+            const int64_t r1 = min64(s1, r0 + kTcRun);
+            const int nch = (int)((r1 - r0 + kTcK - 1) / kTcK);
+            stage_rows(xraw, X, ldx, d, r0, kTcK, (int)min64(kTcK, r1 - r0), xv16 != 0);
+            stage_rows(zraw, Z, ldz, k, r0, kTcK, (int)min64(kTcK, r1 - r0), zv16 != 0);
+            cp_commit();
+            for (int ch = 0; ch < nch; ++ch, ++gch) {
+                const int64_t base = r0 + (int64_t)ch * kTcK;
+                const int nr = (int)min64(kTcK, r1 - base);
+                const int rb = ch & 1;           // raw staging buffer
+                const int ob = (int)(gch & 1u);  // operand set and accumulator
+                if (ch + 1 < nch) {
+                    const int64_t nb = base + kTcK;
+                    const int nn = (int)min64(kTcK, r1 - nb);
+                    stage_rows(xraw + (rb ^ 1) * kTcK * d, X, ldx, d, nb, kTcK, nn, xv16 != 0);
+                    stage_rows(zraw + (rb ^ 1) * kTcK * k, Z, ldz, k, nb, kTcK, nn, zv16 != 0);
+                    cp_commit();
+                    cp_wait<1>();
+                } else {
+                    cp_wait<0>();
+                }
+                __syncthreads();
+                const float* xb = xraw + rb * kTcK * d;
+                const float* zb = zraw + rb * kTcK * k;
+                {   // s_p = ||x_p - mu||^2, four threads per point
+                    const int p = tid >> 2, part4 = tid & 3;
+                    float acc = 0.f;
+                    for (int c = part4; c < d; c += 4) {
+                        const float v = xb[p * d + c] - mu_s[c];
+                        acc = fmaf(v, v, acc);
+                    }
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                    if (part4 == 0) s_buf[p] = (with_s && p < nr) ? acc : 0.f;
+                }
+                // operand set ob was read by the MMAs of chunk gch - 2
+                if (!retire(ob)) { failed = true; break; }
+                unsigned char* a_hi = smem_raw + ob * set_bytes;
+                unsigned char* a_lo = a_hi + a_bytes;
+                unsigned char* b_hi = a_lo + a_bytes;
+                unsigned char* b_lo = b_hi + b_bytes;
+                // warp w takes the 4-point groups g4 = w, w + 8; its lanes the
+                // rows (adjacent rows: conflict-free 16-byte stores)
+                for (int g4 = warp; g4 < kTcK / 4; g4 += kWarps) {
+                    for (int r = lane; r < D2; r += 32) {
+                        float v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int p = 4 * g4 + i;
+                            v[i] = p >= nr ? 0.f : r < d ? xb[p * d + r] - mu_s[r] : r == d ? 1.f : s_buf[p];
+                        }
+                        tc_put4(a_hi, a_lo, r, g4, v);
+                    }
+                    for (int r = lane; r < k; r += 32) {
+                        float v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) v[i] = zb[(4 * g4 + i) * k + r];   // zero past nr
+                        tc_put4(b_hi, b_lo, r, g4, v);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dt = tmem + (uint32_t)(ob * N);
+                    const uint64_t so = ob ? set_step : 0u;
+#pragma unroll
+                    for (int st = 0; st < kTcK / 8; ++st) {
+                        const uint64_t o = so + ((uint64_t)(st * 2 * kTcLbo) >> 4);
+                        tc_mma(dt, dah + o, dbh + o, idesc, st > 0 ? 1u : 0u);
+                        tc_mma(dt, dah + o, dbl + o, idesc, 1u);
+                        tc_mma(dt, dal + o, dbh + o, idesc, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(mbar + ob)) : "memory");
+                }
+                pending |= 1u << ob;
+            }
+            if (failed) break;
+            // end of the run: both accumulators into facc, facc into the
+            // segment's FP64 partial
+            if (!retire(0) || !retire(1)) { failed = true; break; }
+            if (warp < 4) {
+                const int m = warp * 32 + lane;
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int j = cb * 16 + q;
+                        if (m < D2 && j < k) {
+                            double* dst = part + (int64_t)m * k + j;
+                            *dst = first_run ? (double)facc[cb][q] : *dst + (double)facc[cb][q];
+                        }
+                        facc[cb][q] = 0.f;
+                    }
+                }
+            }
+            first_run = false;
+            // the reads of the accumulators precede the next MMAs into them
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    if (failed && err) set_error(err, kErrTimeout);
+    cp_wait<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
+    }
 }
 
 // ----------------------------------------------------------------- l2prep
@@ -724,7 +1037,59 @@ bool reduce_supported(int64_t d, int64_t k) {
     return smem <= 220 * 1024;
 }
 
+// The tensor-core path: FP32, d + 2 <= 128 rows of A, k <= 64 columns, the
+// two operand sets in shared memory; taken when the context asks for it, or
+// automatically where it measured faster than the CUDA-core kernel.
+bool tc_shape_ok(const ReduceArgs& a) {
+    return a.dtype == DM_F32 && a.d >= 1 && a.d + 2 <= kTcM && a.k >= 1 && a.k <= 64 &&
+           tc_smem_bytes((int)a.d, (int)a.k) <= 220 * 1024;
+}
+
+bool tc_auto(const ReduceArgs&) { return false; }
+
+bool tc_ok(const ReduceArgs& a) {
+    if (!tc_shape_ok(a) || a.engine == DM_ENGINE_CUDA_CORES) return false;
+    return a.engine == DM_ENGINE_TENSOR_CORES || tc_auto(a);
+}
+
+// Points per segment (one FP64 partial each): kTcRun, or longer when the
+// number of partials is capped.
+int64_t tc_seg_rows(const ReduceArgs& a) {
+    const int64_t cap = a.max_blocks > 0 ? a.max_blocks : (int64_t)1 << 20;
+    const int64_t want = (a.n + cap - 1) / cap;
+    return std::max<int64_t>(kTcRun, (want + kTcK - 1) / kTcK * kTcK);
+}
+
+cudaError_t reduce_tc_launch(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
+    const int N = (int)((a.k + 15) / 16 * 16);
+    uint32_t cols = 32;
+    while (cols < 2u * (uint32_t)N) cols <<= 1;    // two accumulators
+    const size_t smem = tc_smem_bytes((int)a.d, (int)a.k);
+    cudaError_t e = cudaFuncSetAttribute(reduce_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reduce_tc_kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t seg_rows = tc_seg_rows(a);
+    const int64_t nseg = (a.n + seg_rows - 1) / seg_rows;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)std::max(occ, 1) * sm_count(a.num_sms)));
+    reduce_tc_kernel<<<blocks, kThreads, smem, st>>>(
+        static_cast<const float*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const float*>(a.mu), a.mu_stride,
+        a.with_s ? 1 : 0, static_cast<const float*>(a.Z), (int)a.k, a.ldz, static_cast<double*>(a.partial),
+        nseg, seg_rows, N, cols, rows16(a.X, a.ldx, a.d, 4) ? 1 : 0, rows16(a.Z, a.ldz, a.k, 4) ? 1 : 0, a.err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int total = (int)((a.d + 2) * a.k);
+    const int warps_per_block = 8;
+    reduce_finalize_kernel<double><<<(total + warps_per_block - 1) / warps_per_block, 32 * warps_per_block,
+                                     0, st>>>(static_cast<const double*>(a.partial), (int)nseg, total,
+                                              static_cast<double*>(a.res));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *launches += 2;
+    return cudaSuccess;
+}
+
 int reduce_blocks(const ReduceArgs& a) {
+    if (tc_ok(a)) return (int)((a.n + tc_seg_rows(a) - 1) / tc_seg_rows(a));
     const int sms = sm_count(a.num_sms);
     int64_t cap = 3 * (int64_t)sms;
     if (a.max_blocks > 0) cap = std::min<int64_t>(cap, a.max_blocks);
@@ -741,6 +1106,7 @@ int l2prep_blocks(const L2PrepArgs& a) {
 }
 
 cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s, int64_t* launches) {
+    if (tc_ok(a)) return reduce_tc_launch(a, s, launches);
     switch (a.dtype) {
         case DM_F32: return reduce_launch_dt<DM_F32>(a, s, launches);
         case DM_F64: return reduce_launch_dt<DM_F64>(a, s, launches);

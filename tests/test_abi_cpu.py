@@ -33,7 +33,8 @@ def test_header_declares_the_boundary():
                      "dm_matvec_l2sq", "dm_matmat", "dm_sync", "dm_status_string",
                      "dm_bruteforce", "dm_matmat_host", "dm_plan_export", "dm_grad",
                      "dm_batch_create", "dm_batch_run", "dm_batch_lanes", "dm_batch_destroy",
-                     "dm_prepare_lpp", "dm_prepare_l2_embed", "dm_l2sq_matmat_noalloc"):
+                     "dm_prepare_lpp", "dm_prepare_l2_embed", "dm_l2sq_matmat_noalloc",
+                     "dm_set_deterministic", "dm_set_engine"):
         assert required in names
 
 
@@ -66,6 +67,7 @@ def test_argument_checks_without_device(lib):
     assert lib.dm_prepare(None, 0, 0, None, 1, 1, 1, ctypes.byref(h)) == 1
     assert lib.dm_matmat(None, None, 1, 1, None, 1) == 1
     assert lib.dm_sync(None) == 1
+    assert lib.dm_set_engine(None, 0) == 1
     assert lib.dm_matvec_l1(None, None, None) == 1
     assert lib.dm_bruteforce(None, 0, 0, None, 1, 1, 1, None, 1, 1, None, 1) == 1
     assert lib.dm_grad(None, None, 1, None, 1, 1, None, 1) == 1

@@ -381,3 +381,52 @@ def test_l2sq_wide_blocks_in_column_chunks(dm, ctx, dtype, d, k):
         X = rng.normal(0, 4, size=(3000, d)).astype(dtype)
         Z = rng.normal(size=(3000, k)).astype(dtype)
     check(gpu_product(dm, ctx, "l2sq", X, Z), reference("l2sq", X, Z), dtype)
+
+
+# ------------------------------------------------ squared-l2 engine switch
+@pytest.fixture(scope="module")
+def ctx_tensor(dm):
+    c = dm.dm_create(0)
+    dm.dm_set_engine(c, "tensor")
+    return c
+
+
+@pytest.mark.parametrize("n,d,k", [(1, 1, 1), (63, 3, 5), (1000, 8, 16), (3001, 32, 17),
+                                   (2048, 126, 16), (70001, 16, 40), (5000, 30, 64)])
+def test_l2sq_tensor_engine(dm, ctx_tensor, n, d, k):
+    # tcgen05 contraction (TF32 hi + lo split) where the shape allows it --
+    # ragged n (partial chunks), k not a multiple of 16, d + 2 = 128 -- and the
+    # CUDA-core kernel for k = 64 (two operand sets no longer fit)
+    rng = np.random.default_rng(n + d + k)
+    X = rng.normal(0, 3, size=(n, d)).astype(np.float32)
+    Z = rng.normal(size=(n, k)).astype(np.float32)
+    out = gpu_product(dm, ctx_tensor, "l2sq", X, Z)
+    rows = np.unique(np.concatenate([inputs.sample_rows(n, 16), [0, n - 1]]))
+    assert oracle.relative_error(out[rows], oracle.l2sq_rows(X, Z, rows)) <= 1e-5
+
+
+def test_l2sq_tensor_engine_full_size(dm, ctx_tensor, full_fp32):
+    X, Z = full_fp32
+    out = gpu_product(dm, ctx_tensor, "l2sq", X, Z)
+    rows = inputs.sample_rows(len(X), 24)
+    assert oracle.relative_error(out[rows], oracle.l2sq_rows(X, Z, rows)) <= 1e-5
+
+
+def test_tensor_engine_gradient_and_even_p(dm, ctx_tensor):
+    rng = np.random.default_rng(17)
+    X = rng.normal(size=(4000, 6)).astype(np.float32)
+    W = rng.normal(size=(4000, 3)).astype(np.float32)
+    Z = rng.normal(size=(4000, 3)).astype(np.float32)
+    plan = dm.dm_prepare(ctx_tensor, "l2sq", dev(X))
+    G = dm.dm_grad(plan, dev(W), dev(Z)).cpu().numpy()
+    assert oracle.relative_error(G, oracle.l2sq_grad_rows(X, W, Z)) <= 1e-5
+    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx_tensor, dev(X), 4), dev(Z)).cpu().numpy()
+    assert oracle.relative_error(out, oracle.lpp_rows(X, Z, 4)) <= 1e-5
+    dm.dm_sync(ctx_tensor)
+
+
+def test_engine_rejects_unknown(dm, ctx):
+    with pytest.raises(dm.DMError):
+        dm.dm_set_engine(ctx, "fpga")
+    lib = dm.load()
+    assert lib.dm_set_engine(ctx.handle, 7) == 1
