@@ -12,13 +12,17 @@
 //            chunks, then added in the Wide type), the CTA writes one
 //            partial and a finalize kernel adds the partials in a fixed order.
 //            With s omitted the same kernel gives u and W alone.
+// reduce_tc -- the same contraction for FP32 on the tensor cores (tcgen05,
+//            TF32 hi + lo split), selected with dm_set_engine; see below.
 // l2prep  -- column means mu (the frame shift), FP64 sums, fixed order.
 // l2apply -- out_i = s_i u + v - 2 (x_i - mu) . W  (the p = 2 query, Appendix
 //            A), s_i recomputed from the staged row with the same code as in
 //            the reduce.
-// These kernels are HBM-bound at the shapes of interest (d, k <= 64): the
-// contraction does 2(d+2)k flops per (4d + 4k) bytes read, below the FP32
-// ALU ridge, so they run on the CUDA cores.
+// The contraction does 2(d+2)k flops per (4d + 4k) bytes read (5.6 flop/byte
+// at d = 32, k = 16).  Neither reduce reaches the HBM roof: both are bound by
+// the instructions that stage, centre and (on the tensor cores) split the
+// rows, and the CUDA-core kernel measured faster at every shape, so it is the
+// default.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
