@@ -735,25 +735,32 @@ __global__ void __launch_bounds__(kGT) grad_scan_kernel(const int4* __restrict__
 }
 
 // G (n x d, leading dimension ldg) = Gt^T (Gt: d x n), through 32 x 32 tiles
-// in shared memory: coalesced reads of Gt rows and writes of G rows.
+// in shared memory: coalesced reads of Gt rows and writes of G rows.  Each
+// block moves two tiles along n, so every thread has 8 loads in flight.
 template <class Out>
 __global__ void __launch_bounds__(256) grad_transpose_kernel(const Out* __restrict__ Gt, int64_t n, int d,
                                                              Out* __restrict__ G, int64_t ldg) {
-    __shared__ Out tile[32][33];
-    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    __shared__ Out tile[2][32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 64;
     const int c0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-    for (int r = ty; r < 32; r += 8) {
-        const int c = c0 + r;
-        const int64_t i = i0 + tx;
-        if (c < d && i < n) tile[r][tx] = Gt[(int64_t)c * n + i];
-    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = ty; r < 32; r += 8) {
+            const int c = c0 + r;
+            const int64_t i = i0 + 32 * h + tx;
+            if (c < d && i < n) tile[h][r][tx] = Gt[(int64_t)c * n + i];
+        }
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t i = i0 + r;
-        const int c = c0 + tx;
-        if (c < d && i < n) G[i * ldg + c] = tile[tx][r];
-    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t i = i0 + 32 * h + r;
+            const int c = c0 + tx;
+            if (c < d && i < n) G[i * ldg + c] = tile[h][tx][r];
+        }
 }
 
 // P[i, 2q] = Z[i, q], P[i, 2q + 1] = W[i, q].
@@ -925,7 +932,7 @@ cudaError_t grad_l1_stage_t(const GradArgs& a, int stage, cudaStream_t s, int64_
             else grad_tile_kernel<DT, true, false, kNV><<<(unsigned)blocks, kGT, 0, s>>>(p);
         }
     } else {
-        const int64_t bx = (a.n + 31) / 32;
+        const int64_t bx = (a.n + 63) / 64;
         if (bx > INT_MAX) return cudaErrorInvalidConfiguration;
         dim3 grid((unsigned)bx, (unsigned)((a.d + 31) / 32));
         grad_transpose_kernel<Out><<<grid, 256, 0, s>>>(p.Gt, a.n, (int)a.d, static_cast<Out*>(a.G), a.ldg);

@@ -61,10 +61,10 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
 
 // Lanes of the warp holding the same 8-bit digit as this lane, from eight
 // ballots (one per digit bit): a lane is a peer when it agrees on every bit.
-// Lanes with valid == false are excluded from every mask (their own result
-// is meaningless).  All 32 lanes must call it.
-__device__ __forceinline__ uint32_t digit_peers(uint32_t digit, bool valid) {
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+// Every lane holds a key (positions past n carry the all-ones padding key),
+// so the match starts from the full warp.  All 32 lanes must call it.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t digit) {
+    uint32_t peers = 0xffffffffu;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         const bool bit = (digit >> b) & 1u;
@@ -277,7 +277,7 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t peers[ITEMS];
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) peers[j] = digit_peers((uint32_t)(key[j] >> shift) & 0xffu, true);
+    for (int j = 0; j < ITEMS; ++j) peers[j] = digit_peers((uint32_t)(key[j] >> shift) & 0xffu);
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t dg = (uint32_t)(key[j] >> shift) & 0xffu;
