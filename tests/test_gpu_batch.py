@@ -89,6 +89,24 @@ def test_batch_matches_oracle(dm, ctx, metric, dtype, lanes):
     dm.dm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_batch_l2sq_tensor_engine(dm, lanes):
+    # the graph captures the tensor-core contraction when the context asks
+    # for it; FP32 sets of uneven size, replayed twice
+    c = dm.dm_create(0)
+    dm.dm_set_engine(c, "tensor")
+    sets = small_sets(np.float32)
+    Xs = [torch.from_numpy(X).cuda() for X, _ in sets]
+    Zs = [torch.from_numpy(Z).cuda() for _, Z in sets]
+    b = dm.dm_batch_create(c, "l2sq", Xs, Zs, lanes=lanes)
+    for _ in range(2):
+        outs = dm.dm_batch_run(b)
+        dm.dm_sync(c)
+        for (X, Z), o in zip(sets, outs):
+            check(o.cpu().numpy(), reference("l2sq", X, Z), np.float32)
+    dm.dm_batch_destroy(b)
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_batch_total_variation(dm, ctx, dtype):
     sets = [(inputs.simplex_points(n, d, seed=s, dtype=dtype), inputs.gaussian_queries(n, k, seed=s, dtype=dtype))
