@@ -123,12 +123,18 @@ def test_odd_p_sorted_form_matches_definition(p):
 
 
 def test_odd_p_grid_closed_form():
-    # sum_{m=1}^{N} m^3 = (N (N + 1) / 2)^2
-    n = 400
-    X = np.arange(n).reshape(n, 1)
-    i = np.arange(n)
-    cube = lambda N: (N * (N + 1) // 2) ** 2
-    want = cube(i) + cube(n - 1 - i)
-    np.testing.assert_array_equal(oracle.lpp_odd_sort(X, np.ones(n, dtype=np.int64), 3), want)
-    np.testing.assert_array_equal(oracle.lpp_rows(X, np.ones(n, dtype=np.int64), 3), want)
+    # x_i = i on a 1D grid, z = 1: sum_j |i - j|^p = S_p(i) + S_p(n-1-i) with
+    # S_p(N) = 1^p + ... + N^p: Nicomachus for p = 3, Faulhaber's polynomials
+    # for p = 5 and 7 (exact integers; the grid sizes keep every sum < 2^63)
+    sums = {
+        3: (400, lambda N: (N * (N + 1) // 2) ** 2),
+        5: (400, lambda N: N * N * (N + 1) ** 2 * (2 * N * N + 2 * N - 1) // 12),
+        7: (150, lambda N: N * N * (N + 1) ** 2 * (3 * N ** 4 + 6 * N ** 3 - N * N - 4 * N + 2) // 24),
+    }
+    for p, (n, S) in sums.items():
+        assert S(4) == sum(t ** p for t in range(1, 5))        # the polynomial itself
+        X = np.arange(n).reshape(n, 1)
+        want = np.array([S(i) + S(n - 1 - i) for i in range(n)], dtype=np.int64)
+        np.testing.assert_array_equal(oracle.lpp_odd_sort(X, np.ones(n, dtype=np.int64), p), want)
+        np.testing.assert_array_equal(oracle.lpp_rows(X, np.ones(n, dtype=np.int64), p), want)
 
