@@ -114,6 +114,20 @@ def test_lpp_odd_ties_across_tiles(dm, ctx, p, dtype):
     check(out.cpu().numpy(), oracle.lpp_rows(X, Z, p), dtype)
 
 
+@pytest.mark.parametrize("p,n", [(3, 3000), (5, 1200), (7, 150)])
+def test_lpp_odd_grid_closed_form(dm, ctx, p, n):
+    # x_i = i, z = 1: sum_j |i - j|^p = S_p(i) + S_p(n - 1 - i), S_p the power
+    # sums (Nicomachus / Faulhaber), exact in int64 from int32 points
+    S = {3: lambda N: (N * (N + 1) // 2) ** 2,
+         5: lambda N: N * N * (N + 1) ** 2 * (2 * N * N + 2 * N - 1) // 12,
+         7: lambda N: N * N * (N + 1) ** 2 * (3 * N ** 4 + 6 * N ** 3 - N * N - 4 * N + 2) // 24}[p]
+    X = np.arange(n, dtype=np.int32)[:, None]
+    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, dev(X), p), dev(np.ones((n, 1), dtype=np.int32)))
+    dm.dm_sync(ctx)
+    want = np.array([[S(i) + S(n - 1 - i)] for i in range(n)], dtype=np.int64)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
 def test_lpp_odd_strided_output(dm, ctx):
     # out is a column slice of a wider block (ldo > k): the columns outside
     # the slice are left as they were
