@@ -123,16 +123,17 @@ def out_numpy_dtype(code: int):
 
 
 def _ld(t) -> int:
-    """Leading dimension (elements) of a row-major 2-D tensor/array view."""
+    """Leading dimension (elements) of a row-major 2-D tensor/array view.  The
+    column stride of a single-column view (x[:, None]) is irrelevant."""
     if t.ndim == 1:
         return 1
     if hasattr(t, "stride") and callable(t.stride):
         st = t.stride()
-        if st[1] != 1:
+        if st[1] != 1 and t.shape[1] != 1:
             raise DMError(DM_ERR_INVALID_ARG, "matrix rows must be contiguous")
         return st[0]
     st = t.strides
-    if st[1] != t.itemsize:
+    if st[1] != t.itemsize and t.shape[1] != 1:
         raise DMError(DM_ERR_INVALID_ARG, "matrix rows must be contiguous")
     return st[0] // t.itemsize
 

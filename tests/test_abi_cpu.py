@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from conftest import ROOT
@@ -106,3 +107,19 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "LIB", str(tmp_path / "absent.so"))
     with pytest.raises(binding.DMError):
         binding.load()
+
+
+def test_leading_dimension_of_views():
+    # row-major views: the column stride of a single-column view is ignored,
+    # any other non-unit column stride is rejected
+    import torch
+    from paper_2210_15114_gb300 import binding
+    a = np.arange(12, dtype=np.int32)[:, None]                 # strides (4, 0)
+    assert binding._ld(a) == 1
+    assert binding._ld(torch.from_numpy(a)) == 1
+    assert binding._ld(torch.zeros(5, 7)[:, :3]) == 7           # a column slice keeps ld
+    assert binding._ld(np.zeros((5, 7), dtype=np.float32)[1:, 2:]) == 7
+    with pytest.raises(binding.DMError):
+        binding._ld(torch.zeros(4, 6)[:, ::2])
+    with pytest.raises(binding.DMError):
+        binding._ld(np.zeros((4, 6))[:, ::2])
