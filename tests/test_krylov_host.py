@@ -2,6 +2,7 @@
 orthonormalization of a block against the earlier basis, for full-rank,
 rank-deficient and zero blocks.  The products A Z are the library's and are
 tested on the GPU; these steps are dense linear algebra on tall blocks."""
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -83,3 +84,39 @@ def test_fill_is_seeded():
     a = krylov._orthonormalize(W, prev, torch.Generator().manual_seed(9))
     b = krylov._orthonormalize(W, prev, torch.Generator().manual_seed(9))
     assert torch.equal(a, b)
+
+
+def _dense(metric, X):
+    D = X[:, None, :] - X[None, :, :]
+    return np.abs(D).sum(-1) if metric == "l1" else (D * D).sum(-1)
+
+
+@pytest.mark.parametrize("metric", ["l1", "l2sq"])
+def test_block_krylov_host_steps_with_a_dense_product(monkeypatch, metric):
+    # the iteration's host steps end to end, the library product replaced by
+    # a dense FP32 product on the CPU: the top Ritz values equal the dense
+    # eigenvalues; squared l2 (rank d + 2 = 6 < the block width 10) takes the
+    # rank-deficient path on every block after the first
+    from paper_2210_15114_gb300 import binding
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(500, 4))
+    A = torch.from_numpy(_dense(metric, X).astype(np.float32))
+
+    def product(plan, Z, out=None):
+        r = A @ Z
+        if out is None:
+            return r
+        out.copy_(r)
+        return out
+
+    monkeypatch.setattr(binding, "dm_matmat", product)
+    Pi = torch.from_numpy(rng.normal(size=(500, 10)).astype(np.float32))
+    theta, U = krylov.block_krylov(None, Pi, q=3, rank=8)
+    ev = np.linalg.eigvalsh(_dense(metric, X))
+    ev = ev[np.argsort(-np.abs(ev))]
+    top = 6 if metric == "l2sq" else 4
+    np.testing.assert_allclose(theta[:top].numpy(), ev[:top], rtol=1e-4)
+    if metric == "l2sq":
+        assert np.all(np.abs(theta[6:].numpy()) <= 1e-4 * abs(float(theta[0])))
+    Ud = U.double()
+    np.testing.assert_allclose((Ud.T @ Ud).numpy(), np.eye(8), atol=1e-4)
