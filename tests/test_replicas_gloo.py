@@ -70,3 +70,27 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     a = argparse.Namespace(n=1 << 20, d=32, k=16, steps=1, warmup=0, gpus=2)
     assert bench.run_reference(a) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    # rank 0 times the oracle and prints one JSON line with the keys the
+    # benchmark contract asks of the reference arm (small n: seconds)
+    sys.path.insert(0, ROOT)
+    import argparse
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    a = argparse.Namespace(n=4096, d=8, k=4, steps=2, warmup=1, gpus=1, engine="auto")
+    bench.run_reference(a)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in rec, key
+    assert rec["impl"] == "reference" and rec["value"] > 0 and rec["steps"] == 2
+    assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["d2h_bytes_per_step"] == 0
+    assert rec["e2e"]["value"] == rec["value"] and rec["cpu_baseline"]["kind"] == "oracle"
+    assert {"value", "unit", "cores", "kind", "sample"} <= set(rec["cpu_baseline"])
