@@ -70,8 +70,13 @@ typedef struct dm_plan dm_plan;   /* opaque: one preprocessed point set         
  * word. */
 dm_status dm_create(dm_ctx** ctx, int device, void* cuda_stream);
 
-/* Synchronize the stream and free the context.  Plans made from it must be
- * destroyed first. */
+/* Synchronize the stream and free the context.  Plans and batches made from
+ * it may be destroyed before or after it, in any order: while any of them is
+ * alive the context's memory is kept, every other call on the context or on
+ * its plans and batches returns DM_ERR_INVALID_ARG, and the memory is
+ * released with the last of them (the stream is not used again, so it may be
+ * gone by then).  Calling dm_destroy twice on one context is an error unless
+ * children kept it alive in between. */
 void dm_destroy(dm_ctx* ctx);
 
 /* Switch the stream later calls are issued on (borrowed, as in dm_create). */
@@ -232,6 +237,23 @@ void dm_batch_destroy(dm_batch* batch);
 /* Wait for the context's stream and return (then clear) the first device-side
  * error latched since the last dm_sync. */
 dm_status dm_sync(dm_ctx* ctx);
+
+/* Rounds a device-side wait of this context's kernels may spin before it
+ * gives up (the radix passes' decoupled look-back over earlier tiles of a
+ * column, Algorithm 1's sort; the ordered mode of the l1 query waiting for
+ * the previous coordinate).  A wait that runs out latches DM_ERR_TIMEOUT for
+ * dm_sync and lets its kernel finish (its results are then wrong); the
+ * context stays usable.  rounds = 0 restores the default (2^20 rounds of a
+ * short sleep, about a second). */
+dm_status dm_set_wait_limit(dm_ctx* ctx, uint32_t rounds);
+
+/* Test hook for the bounded wait (no counterpart in the paper): launches one
+ * CTA of a radix pass over a two-tile FP32 column, started as the second
+ * tile, so the predecessor it looks back to never publishes its counts.  The
+ * CTA gives up after the context's wait limit, latches DM_ERR_TIMEOUT (read
+ * it with dm_sync) and returns; it touches only the context's scratch arena.
+ * Use a small limit (dm_set_wait_limit) to keep the call short. */
+dm_status dm_test_unpublished_wait(dm_ctx* ctx);
 
 /* Static, human-readable name of a status code. */
 const char* dm_status_string(dm_status status);

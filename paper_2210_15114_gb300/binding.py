@@ -86,6 +86,8 @@ def load() -> ctypes.CDLL:
             "dm_profile_enable": ([P, I32], I32),
             "dm_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int), P, P, P], I32),
             "dm_l2sq_matmat_noalloc": ([I32, P, I64, I64, I64, P, I64, I64, P, I64, P], I32),
+            "dm_set_wait_limit": ([P, ctypes.c_uint32], I32),
+            "dm_test_unpublished_wait": ([P], I32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -148,9 +150,10 @@ def _dev_ptr(t) -> int:
 class Context:
     """Owner of a dm_ctx handle (device, stream, scratch arena)."""
 
-    def __init__(self, handle: int, device: int):
+    def __init__(self, handle: int, device: int, stream: int = 0):
         self.handle = handle
         self.device = device
+        self.stream = stream          # the stream work is issued on (cudaStream_t)
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -183,7 +186,7 @@ def dm_create(device: int = 0, stream=None) -> Context:
         stream = torch.cuda.current_stream(device).cuda_stream
     h = ctypes.c_void_p()
     _check(lib.dm_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream)), "dm_create")
-    return Context(h.value, int(device))
+    return Context(h.value, int(device), stream)
 
 
 def dm_destroy(ctx: Context) -> None:
@@ -194,6 +197,7 @@ def dm_destroy(ctx: Context) -> None:
 
 def dm_set_stream(ctx: Context, stream) -> None:
     _check(load().dm_set_stream(ctx.handle, ctypes.c_void_p(stream)), "dm_set_stream")
+    ctx.stream = stream
 
 
 def dm_set_deterministic(ctx: Context, on: bool = True) -> None:
@@ -267,36 +271,65 @@ def dm_plan_destroy(plan: Plan) -> None:
         plan.handle = None
 
 
-def _alloc_out(plan: Plan, Z, out):
+def _as2d(t):
+    """A 1-D tensor as its n x 1 view (the stride of the elements becomes the
+    leading dimension); 2-D tensors unchanged."""
+    if t.ndim == 1:
+        return t.reshape(-1, 1)
+    if t.ndim != 2:
+        raise DMError(DM_ERR_INVALID_ARG, "expected a vector or a matrix")
+    return t
+
+
+def _on_device(device: int, *ts):
+    for t in ts:
+        if not t.is_cuda or t.device.index != device:
+            raise DMError(DM_ERR_INVALID_ARG, f"tensors must be on cuda:{device}")
+
+
+def _query_args(plan: Plan, Z, out):
+    """Checks of a query block Z (n or n x k, the plan's element type, on the
+    plan's device) and of its result `out` (allocated when None: the shape of
+    Z, the plan's result type).  Returns (out, Z as n x k, out as n x k)."""
     import torch
-    k = 1 if Z.ndim == 1 else Z.shape[1]
-    shape = (plan.n,) if Z.ndim == 1 else (plan.n, k)
+    if dtype_code(Z.dtype) != plan.dtype:
+        raise DMError(DM_ERR_INVALID_ARG, "Z element type differs from the plan's")
+    Z2 = _as2d(Z)
+    if Z2.shape[0] != plan.n:
+        raise DMError(DM_ERR_INVALID_ARG, f"Z has {Z2.shape[0]} rows, the plan {plan.n} points")
+    shape = (plan.n,) if Z.ndim == 1 else (plan.n, Z2.shape[1])
     if out is None:
         out = torch.empty(shape, dtype=out_torch_dtype(plan.dtype), device=Z.device)
-    return out, k
+    elif tuple(out.shape) != shape or out.dtype != out_torch_dtype(plan.dtype):
+        raise DMError(DM_ERR_INVALID_ARG, f"out must be {shape} of {out_torch_dtype(plan.dtype)}")
+    _on_device(plan.ctx.device, Z, out)
+    return out, Z2, _as2d(out)
+
+
+def _matvec(name: str, plan: Plan, z, out):
+    if z.ndim != 1:
+        raise DMError(DM_ERR_INVALID_ARG, f"{name} takes one query vector of n elements")
+    out, _, _ = _query_args(plan, z, out)
+    if not out.is_contiguous():
+        raise DMError(DM_ERR_INVALID_ARG, f"{name} writes a contiguous result vector")
+    z = z.contiguous()                # the entry point reads n consecutive elements
+    _check(getattr(load(), name)(plan.handle, ctypes.c_void_p(_dev_ptr(z)),
+                                 ctypes.c_void_p(_dev_ptr(out))), name)
+    return out
 
 
 def dm_matvec_l1(plan: Plan, z, out=None):
-    out, _ = _alloc_out(plan, z, out)
-    _check(load().dm_matvec_l1(plan.handle, ctypes.c_void_p(_dev_ptr(z)),
-                               ctypes.c_void_p(_dev_ptr(out))), "dm_matvec_l1")
-    return out
+    return _matvec("dm_matvec_l1", plan, z, out)
 
 
 def dm_matvec_l2sq(plan: Plan, z, out=None):
-    out, _ = _alloc_out(plan, z, out)
-    _check(load().dm_matvec_l2sq(plan.handle, ctypes.c_void_p(_dev_ptr(z)),
-                                 ctypes.c_void_p(_dev_ptr(out))), "dm_matvec_l2sq")
-    return out
+    return _matvec("dm_matvec_l2sq", plan, z, out)
 
 
 def dm_matmat(plan: Plan, Z, out=None):
-    if dtype_code(Z.dtype) != plan.dtype:
-        raise DMError(DM_ERR_INVALID_ARG, "Z element type differs from the plan's")
-    out, k = _alloc_out(plan, Z, out)
-    _check(load().dm_matmat(plan.handle, ctypes.c_void_p(_dev_ptr(Z)), k, _ld(Z) if Z.ndim == 2 else 1,
-                            ctypes.c_void_p(_dev_ptr(out)), _ld(out) if out.ndim == 2 else 1),
-           "dm_matmat")
+    out, Z2, o2 = _query_args(plan, Z, out)
+    _check(load().dm_matmat(plan.handle, ctypes.c_void_p(_dev_ptr(Z2)), Z2.shape[1], _ld(Z2),
+                            ctypes.c_void_p(_dev_ptr(o2)), _ld(o2)), "dm_matmat")
     return out
 
 
@@ -305,12 +338,16 @@ def dm_grad(plan: Plan, W, Z, out=None):
     import torch
     if dtype_code(W.dtype) != plan.dtype or dtype_code(Z.dtype) != plan.dtype:
         raise DMError(DM_ERR_INVALID_ARG, "W / Z element type differs from the plan's")
-    W2 = W.reshape(-1, 1) if W.ndim == 1 else W
-    Z2 = Z.reshape(-1, 1) if Z.ndim == 1 else Z
+    W2, Z2 = _as2d(W), _as2d(Z)
     if W2.shape != Z2.shape:
         raise DMError(DM_ERR_INVALID_ARG, "W and Z must have the same shape")
+    if W2.shape[0] != plan.n:
+        raise DMError(DM_ERR_INVALID_ARG, f"W and Z have {W2.shape[0]} rows, the plan {plan.n} points")
     if out is None:
         out = torch.empty((plan.n, plan.d), dtype=out_torch_dtype(plan.dtype), device=W.device)
+    elif tuple(out.shape) != (plan.n, plan.d) or out.dtype != out_torch_dtype(plan.dtype):
+        raise DMError(DM_ERR_INVALID_ARG, f"out must be ({plan.n}, {plan.d}) of {out_torch_dtype(plan.dtype)}")
+    _on_device(plan.ctx.device, W2, Z2, out)
     _check(load().dm_grad(plan.handle, ctypes.c_void_p(_dev_ptr(W2)), _ld(W2),
                           ctypes.c_void_p(_dev_ptr(Z2)), _ld(Z2), W2.shape[1],
                           ctypes.c_void_p(_dev_ptr(out)), _ld(out)), "dm_grad")
@@ -385,6 +422,17 @@ def dm_sync(ctx: Context) -> None:
     _check(load().dm_sync(ctx.handle), "dm_sync")
 
 
+def dm_set_wait_limit(ctx: Context, rounds: int = 0) -> None:
+    """dm_set_wait_limit: rounds a device-side wait may spin (0: default)."""
+    _check(load().dm_set_wait_limit(ctx.handle, int(rounds)), "dm_set_wait_limit")
+
+
+def dm_test_unpublished_wait(ctx: Context) -> None:
+    """dm_test_unpublished_wait: one radix-pass CTA whose predecessor never
+    publishes (a test of the bounded wait; dm_sync then reports it)."""
+    _check(load().dm_test_unpublished_wait(ctx.handle), "dm_test_unpublished_wait")
+
+
 def dm_status_string(status: int) -> str:
     return load().dm_status_string(int(status)).decode()
 
@@ -404,16 +452,20 @@ def dm_plan_export(plan: Plan):
 def dm_bruteforce(ctx: Context, metric, X, Z, out=None):
     import torch
     m = METRICS[metric] if isinstance(metric, str) else int(metric)
-    if X.ndim == 1:
-        X = X.reshape(-1, 1)
+    X = _as2d(X)
     code = dtype_code(X.dtype)
     squeeze = Z.ndim == 1
-    Z2 = Z.reshape(-1, 1) if squeeze else Z
+    Z2 = _as2d(Z)
     n, d = X.shape
     k = Z2.shape[1]
+    if dtype_code(Z2.dtype) != code or Z2.shape[0] != n:
+        raise DMError(DM_ERR_INVALID_ARG, "Z must have n rows of the points' element type")
     if out is None:
         out = torch.empty((n, k), dtype=out_torch_dtype(code), device=X.device)
-    o2 = out.reshape(-1, 1) if out.ndim == 1 else out
+    o2 = _as2d(out)
+    if tuple(o2.shape) != (n, k) or out.dtype != out_torch_dtype(code):
+        raise DMError(DM_ERR_INVALID_ARG, f"out must be ({n}, {k}) of {out_torch_dtype(code)}")
+    _on_device(X.device.index if X.is_cuda else -1, X, Z2, o2)
     _check(load().dm_bruteforce(ctx.handle, m, code, ctypes.c_void_p(_dev_ptr(X)), n, d, _ld(X),
                                 ctypes.c_void_p(_dev_ptr(Z2)), k, _ld(Z2),
                                 ctypes.c_void_p(_dev_ptr(o2)), _ld(o2)), "dm_bruteforce")
@@ -468,14 +520,18 @@ def dm_l2sq_matmat_noalloc(X, Z, out, stream=None) -> None:
     `out` without any allocation by the library (its scratch is a fixed
     device array; see include/dm.h for the limits and the sharing rules)."""
     import torch
-    if X.ndim == 1:
-        X = X.reshape(-1, 1)
-    Z2 = Z.reshape(-1, 1) if Z.ndim == 1 else Z
-    o2 = out.reshape(-1, 1) if out.ndim == 1 else out
-    if stream is None:
-        stream = torch.cuda.current_stream(X.device).cuda_stream
+    X = _as2d(X)
+    Z2, o2 = _as2d(Z), _as2d(out)
     n, d = X.shape
     k = Z2.shape[1]
+    code = dtype_code(X.dtype)
+    if dtype_code(Z2.dtype) != code or Z2.shape[0] != n:
+        raise DMError(DM_ERR_INVALID_ARG, "Z must have n rows of the points' element type")
+    if tuple(o2.shape) != (n, k) or out.dtype != out_torch_dtype(code):
+        raise DMError(DM_ERR_INVALID_ARG, f"out must be ({n}, {k}) of {out_torch_dtype(code)}")
+    _on_device(X.device.index if X.is_cuda else -1, X, Z2, o2)
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device).cuda_stream
     _check(load().dm_l2sq_matmat_noalloc(dtype_code(X.dtype), ctypes.c_void_p(_dev_ptr(X)), n, d,
                                          _ld(X), ctypes.c_void_p(_dev_ptr(Z2)), k, _ld(Z2),
                                          ctypes.c_void_p(_dev_ptr(o2)), _ld(o2),

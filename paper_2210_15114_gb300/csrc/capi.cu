@@ -26,6 +26,7 @@ struct dm_ctx {
     size_t host_hist_words = 0;
     int64_t launches = 0;
     int deterministic = 0;           // dm_set_deterministic
+    uint32_t spin_limit = dm::kSpinLimit; // dm_set_wait_limit
     int engine = DM_ENGINE_AUTO;     // dm_set_engine
     // Device buffers of dm_matmat_host (grown on demand), and the stream and
     // event its copy of Z uses to overlap the preprocessing.
@@ -47,6 +48,12 @@ struct dm_ctx {
     struct Block { void* p; size_t bytes; };
     std::vector<Block> pool;
     size_t pool_bytes = 0;
+    // Lifetime: live plans and batches made from this context.  dm_destroy
+    // with children still alive only marks the context destroyed (every later
+    // call through it or its children fails with DM_ERR_INVALID_ARG); the
+    // memory is released when the last child is destroyed.
+    int64_t children = 0;
+    bool destroyed = false;
 };
 
 struct dm_plan {
@@ -269,11 +276,14 @@ dm_status plan_alloc(dm_plan* p, size_t bytes, void** out) {
     return DM_OK;
 }
 
-// Hand a plan's buffers back to the context pool (freed beyond the cap).
+// Hand a plan's buffers back to the context pool (freed beyond the cap, and
+// always once the context is destroyed: cudaFree waits for the device).
 void plan_release(dm_plan* p) {
     dm_ctx* ctx = p->ctx;
     for (auto& ob : p->owned) {
-        if (ctx->pool_bytes + ob.second <= kPoolCap) {
+        if (ctx->destroyed) {
+            cudaFree(ob.first);
+        } else if (ctx->pool_bytes + ob.second <= kPoolCap) {
             ctx->pool.push_back({ob.first, ob.second});
             ctx->pool_bytes += ob.second;
         } else {
@@ -354,6 +364,7 @@ dm_status prepare_l1_run(const Exec& e, dm_plan* p, const void* X, int64_t ldx) 
     a.sorted_out = p->xs;
     a.perm_out = p->perm;
     a.err = ctx->err;
+    a.spin_limit = ctx->spin_limit;
 
     DM_TRY_CUDA(cudaMemsetAsync(base, 0, L.zero_bytes, e.stream));
     {
@@ -569,6 +580,7 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
         q.err = ctx->err;
         q.num_sms = ctx->num_sms;
         q.deterministic = ctx->deterministic;
+        q.spin_limit = ctx->spin_limit;
         {
             ProfScope ps(e, "l1_prologue");
             DM_TRY_CUDA(l1_prologue_launch(q, e.stream, &ctx->launches));
@@ -902,7 +914,7 @@ dm_status batch_autotune(dm_batch* b) {
 
 void batch_free(dm_batch* b) {
     if (b->origin) cudaStreamSynchronize(b->origin);
-    if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
+    if (b->ctx && !b->ctx->destroyed) cudaStreamSynchronize(b->ctx->stream);
     batch_release_graph(b);
     for (auto& st : b->sets) {
         if (st.plan) { free_plan_buffers(st.plan); delete st.plan; }
@@ -911,6 +923,31 @@ void batch_free(dm_batch* b) {
     if (b->done) cudaEventDestroy(b->done);
     if (b->origin) cudaStreamDestroy(b->origin);
     delete b;
+}
+
+// Release everything a context owns.  The caller has synchronized its
+// stream (dm_destroy) or the stream may be gone already (the last child of a
+// destroyed context): only device-wide waits are used here.
+void ctx_free(dm_ctx* ctx) {
+    if (ctx->arena) cudaFree(ctx->arena);
+    for (auto& b : ctx->pool) cudaFree(b.p);
+    if (ctx->hx) cudaFree(ctx->hx);
+    if (ctx->hz) cudaFree(ctx->hz);
+    if (ctx->ho) cudaFree(ctx->ho);
+    if (ctx->aux) { cudaStreamSynchronize(ctx->aux); cudaStreamDestroy(ctx->aux); }
+    if (ctx->aux_done) cudaEventDestroy(ctx->aux_done);
+    if (ctx->err) cudaFree(ctx->err);
+    if (ctx->host_err) cudaFreeHost(ctx->host_err);
+    if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
+    for (auto& p : ctx->pending) { cudaEventDestroy(p.start); cudaEventDestroy(p.stop); }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+// A plan or batch of `ctx` is gone; the context follows it when it was
+// destroyed already and this was its last child.
+void child_released(dm_ctx* ctx) {
+    if (--ctx->children == 0 && ctx->destroyed) ctx_free(ctx);
 }
 
 }  // namespace
@@ -958,39 +995,59 @@ dm_status dm_create(dm_ctx** out, int device, void* stream) {
 }
 
 void dm_destroy(dm_ctx* ctx) {
-    if (!ctx) return;
+    if (!ctx || ctx->destroyed) return;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    if (ctx->arena) cudaFree(ctx->arena);
-    for (auto& b : ctx->pool) cudaFree(b.p);
-    if (ctx->hx) cudaFree(ctx->hx);
-    if (ctx->hz) cudaFree(ctx->hz);
-    if (ctx->ho) cudaFree(ctx->ho);
-    if (ctx->aux) { cudaStreamSynchronize(ctx->aux); cudaStreamDestroy(ctx->aux); }
-    if (ctx->aux_done) cudaEventDestroy(ctx->aux_done);
-    if (ctx->err) cudaFree(ctx->err);
-    if (ctx->host_err) cudaFreeHost(ctx->host_err);
-    if (ctx->host_hist) cudaFreeHost(ctx->host_hist);
-    for (auto& p : ctx->pending) { cudaEventDestroy(p.start); cudaEventDestroy(p.stop); }
-    for (auto e : ctx->event_pool) cudaEventDestroy(e);
-    delete ctx;
+    ctx->destroyed = true;
+    if (ctx->children == 0) ctx_free(ctx);
 }
 
 dm_status dm_set_deterministic(dm_ctx* ctx, int on) {
-    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (!ctx || ctx->destroyed) return DM_ERR_INVALID_ARG;
     ctx->deterministic = on ? 1 : 0;
     return DM_OK;
 }
 
+dm_status dm_set_wait_limit(dm_ctx* ctx, uint32_t rounds) {
+    if (!ctx || ctx->destroyed) return DM_ERR_INVALID_ARG;
+    ctx->spin_limit = rounds ? rounds : dm::kSpinLimit;
+    return DM_OK;
+}
+
+dm_status dm_test_unpublished_wait(dm_ctx* ctx) {
+    if (!ctx || ctx->destroyed) return DM_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    const int64_t n = 2 * (int64_t)sort_tile_f32();
+    const SortLayout L = sort_layout(DM_F32, n, 1);
+    DM_TRY(ensure_arena(ctx, L.total));
+    unsigned char* base = static_cast<unsigned char*>(ctx->arena);
+    SortArgs a{};
+    a.dtype = DM_F32;
+    a.n = n; a.d = 1; a.ldx = 1;
+    a.keys_a = base + L.ka; a.keys_b = base + L.kb;
+    a.vals_a = reinterpret_cast<int32_t*>(base + L.va);
+    a.vals_b = reinterpret_cast<int32_t*>(base + L.vb);
+    a.hist = reinterpret_cast<uint32_t*>(base + L.hist);
+    a.counters = reinterpret_cast<uint32_t*>(base + L.cnt);
+    a.lookback = reinterpret_cast<uint32_t*>(base + L.lb);
+    a.err = ctx->err;
+    a.spin_limit = ctx->spin_limit;
+    // zero keys, histograms and look-back words; the tile counter starts at 1
+    DM_TRY_CUDA(cudaMemsetAsync(base, 0, L.kb, ctx->stream));
+    DM_TRY_CUDA(cudaMemsetAsync(a.counters, 1, 1, ctx->stream));
+    DM_TRY_CUDA(sort_launch_unpublished_wait(a, ctx->stream, &ctx->launches));
+    return DM_OK;
+}
+
 dm_status dm_set_engine(dm_ctx* ctx, dm_engine engine) {
-    if (!ctx || (engine != DM_ENGINE_AUTO && engine != DM_ENGINE_CUDA_CORES && engine != DM_ENGINE_TENSOR_CORES))
+    if (!ctx || ctx->destroyed || (engine != DM_ENGINE_AUTO && engine != DM_ENGINE_CUDA_CORES && engine != DM_ENGINE_TENSOR_CORES))
         return DM_ERR_INVALID_ARG;
     ctx->engine = engine;
     return DM_OK;
 }
 
 dm_status dm_set_stream(dm_ctx* ctx, void* stream) {
-    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (!ctx || ctx->destroyed) return DM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);   // pooled buffers may be in use on the old stream
     ctx->stream = static_cast<cudaStream_t>(stream);
@@ -1000,7 +1057,7 @@ dm_status dm_set_stream(dm_ctx* ctx, void* stream) {
 int64_t dm_launch_count(const dm_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 dm_status dm_profile_enable(dm_ctx* ctx, int enable) {
-    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (!ctx || ctx->destroyed) return DM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     DM_TRY(resolve_profile(ctx));
     ctx->stats.clear();
@@ -1010,7 +1067,7 @@ dm_status dm_profile_enable(dm_ctx* ctx, int enable) {
 
 dm_status dm_profile_read(dm_ctx* ctx, int max, int* count, char* names, int64_t* launches,
                           double* total_ms) {
-    if (!ctx || !count || max < 0 || (max > 0 && (!names || !launches || !total_ms)))
+    if (!ctx || ctx->destroyed || !count || max < 0 || (max > 0 && (!names || !launches || !total_ms)))
         return DM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     DM_TRY(resolve_profile(ctx));
@@ -1031,7 +1088,7 @@ dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* 
                      int64_t d, int64_t ldx, dm_plan** plan) {
     if (!plan) return DM_ERR_INVALID_ARG;
     *plan = nullptr;
-    if (!ctx || !X || !(valid_metric(metric) || metric == DM_TV) || !valid_dtype(dtype))
+    if (!ctx || ctx->destroyed || !X || !(valid_metric(metric) || metric == DM_TV) || !valid_dtype(dtype))
         return DM_ERR_INVALID_ARG;
     if (metric == DM_TV && dtype == DM_I32) return DM_ERR_UNSUPPORTED;   // half-integer results
     if (n < 1 || n > kMaxN || d < 1 || ldx < d) return DM_ERR_INVALID_ARG;
@@ -1052,6 +1109,7 @@ dm_status dm_prepare(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* 
         delete p;
         return s;
     }
+    ++ctx->children;
     *plan = p;
     return DM_OK;
 }
@@ -1067,6 +1125,7 @@ dm_status dm_prepare_lpp(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, 
     if (!odd && (double)n * (double)d * pw >= 2147483648.0) return DM_ERR_UNSUPPORTED;
     if (!odd && (reduce_max_k(dtype, d * pw) < 1 || lpp_apply_smem(dtype, d, pw, 1) > 200 * 1024))
         return DM_ERR_UNSUPPORTED;
+    if (ctx->destroyed) return DM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     dm_plan* p = new (std::nothrow) dm_plan();
     if (!p) return DM_ERR_OOM;
@@ -1080,6 +1139,7 @@ dm_status dm_prepare_lpp(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_t n, 
         delete p;
         return s;
     }
+    ++ctx->children;
     *plan = p;
     return DM_OK;
 }
@@ -1088,7 +1148,8 @@ dm_status dm_prepare_l2_embed(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_
                               int64_t ldx, const void* G, int64_t m, dm_plan** plan) {
     if (!plan) return DM_ERR_INVALID_ARG;
     *plan = nullptr;
-    if (!ctx || !X || !G || (dtype != DM_F32 && dtype != DM_F64) || m < 1) return DM_ERR_INVALID_ARG;
+    if (!ctx || ctx->destroyed || !X || !G || (dtype != DM_F32 && dtype != DM_F64) || m < 1)
+        return DM_ERR_INVALID_ARG;
     if (n < 1 || n > kMaxN || d < 1 || ldx < d) return DM_ERR_INVALID_ARG;
     if ((double)n * (double)m >= 2147483648.0) return DM_ERR_UNSUPPORTED;
     if (project_smem(dtype, d, m) > 200 * 1024) return DM_ERR_UNSUPPORTED;
@@ -1127,26 +1188,29 @@ dm_status dm_prepare_l2_embed(dm_ctx* ctx, dm_dtype dtype, const void* X, int64_
         delete p;
         return s;
     }
+    ++ctx->children;
     *plan = p;
     return DM_OK;
 }
 
 void dm_plan_destroy(dm_plan* p) {
     if (!p) return;
-    DeviceGuard g(p->ctx->device);
+    dm_ctx* ctx = p->ctx;
+    DeviceGuard g(ctx->device);
     free_plan_buffers(p);   // stream-ordered reuse: no wait needed
     delete p;
+    child_released(ctx);
 }
 
 dm_status dm_matmat(dm_plan* p, const void* Z, int64_t k, int64_t ldz, void* out, int64_t ldo) {
-    if (!p || !Z || !out || k < 1 || ldz < k || ldo < k) return DM_ERR_INVALID_ARG;
+    if (!p || p->ctx->destroyed || !Z || !out || k < 1 || ldz < k || ldo < k) return DM_ERR_INVALID_ARG;
     DeviceGuard g(p->ctx->device);
     return matmat_impl(p, Z, k, ldz, out, ldo);
 }
 
 dm_status dm_grad(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64_t ldz, int64_t k,
                   void* G, int64_t ldg) {
-    if (!p || !W || !Z || !G || k < 1 || k > 64 || ldw < k || ldz < k || ldg < p->d)
+    if (!p || p->ctx->destroyed || !W || !Z || !G || k < 1 || k > 64 || ldw < k || ldz < k || ldg < p->d)
         return DM_ERR_INVALID_ARG;
     DeviceGuard g(p->ctx->device);
     return grad_impl(p, W, ldw, Z, ldz, k, G, ldg);
@@ -1159,7 +1223,7 @@ dm_status dm_batch_create(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, int64_t
                           dm_batch** batch) {
     if (!batch) return DM_ERR_INVALID_ARG;
     *batch = nullptr;
-    if (!ctx || !(valid_metric(metric) || metric == DM_TV) || !valid_dtype(dtype) || nsets < 1 || lanes < 0 ||
+    if (!ctx || ctx->destroyed || !(valid_metric(metric) || metric == DM_TV) || !valid_dtype(dtype) || nsets < 1 || lanes < 0 ||
         lanes > 64 ||
         !n || !d || !X || !ldx || !k || !Z || !ldz || !out || !ldo)
         return DM_ERR_INVALID_ARG;
@@ -1200,12 +1264,13 @@ dm_status dm_batch_create(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, int64_t
         batch_free(b);
         return s;
     }
+    ++ctx->children;
     *batch = b;
     return DM_OK;
 }
 
 dm_status dm_batch_run(dm_batch* b) {
-    if (!b || !b->exec) return DM_ERR_INVALID_ARG;
+    if (!b || !b->exec || b->ctx->destroyed) return DM_ERR_INVALID_ARG;
     DeviceGuard g(b->ctx->device);
     return batch_launch(b);
 }
@@ -1214,8 +1279,10 @@ int dm_batch_lanes(const dm_batch* b) { return b ? b->lanes : 0; }
 
 void dm_batch_destroy(dm_batch* b) {
     if (!b) return;
-    DeviceGuard g(b->ctx->device);
+    dm_ctx* ctx = b->ctx;
+    DeviceGuard g(ctx->device);
     batch_free(b);
+    child_released(ctx);
 }
 
 dm_status dm_matvec_l1(dm_plan* p, const void* z, void* out) {
@@ -1229,7 +1296,7 @@ dm_status dm_matvec_l2sq(dm_plan* p, const void* z, void* out) {
 }
 
 dm_status dm_sync(dm_ctx* ctx) {
-    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (!ctx || ctx->destroyed) return DM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return from_cuda(e);
@@ -1237,7 +1304,8 @@ dm_status dm_sync(dm_ctx* ctx) {
 }
 
 dm_status dm_plan_export(dm_plan* p, void* sorted_values, int32_t* perm) {
-    if (!p || !(sorted_metric(p->metric) || lpp_odd(p)) || !sorted_values || !perm) return DM_ERR_INVALID_ARG;
+    if (!p || p->ctx->destroyed || !(sorted_metric(p->metric) || lpp_odd(p)) || !sorted_values || !perm)
+        return DM_ERR_INVALID_ARG;
     DeviceGuard g(p->ctx->device);
     const size_t nd = (size_t)p->n * (size_t)p->d;
     DM_TRY_CUDA(cudaMemcpyAsync(sorted_values, p->xs, nd * dtype_size(p->dtype),
@@ -1249,7 +1317,8 @@ dm_status dm_plan_export(dm_plan* p, void* sorted_values, int32_t* perm) {
 dm_status dm_bruteforce(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* X, int64_t n,
                         int64_t d, int64_t ldx, const void* Z, int64_t k, int64_t ldz, void* out,
                         int64_t ldo) {
-    if (!ctx || !X || !Z || !out || !valid_metric(metric) || !valid_dtype(dtype)) return DM_ERR_INVALID_ARG;
+    if (!ctx || ctx->destroyed || !X || !Z || !out || !valid_metric(metric) || !valid_dtype(dtype))
+        return DM_ERR_INVALID_ARG;
     if (n < 1 || n > kMaxN || d < 1 || ldx < d || k < 1 || ldz < k || ldo < k) return DM_ERR_INVALID_ARG;
     if (d > 64) return DM_ERR_UNSUPPORTED;
     DeviceGuard g(ctx->device);
@@ -1266,7 +1335,8 @@ dm_status dm_bruteforce(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const voi
 dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* Xh, int64_t n,
                          int64_t d, int64_t ldx, const void* Zh, int64_t k, int64_t ldz,
                          void* outh, int64_t ldo) {
-    if (!ctx || !Xh || !Zh || !outh || !valid_metric(metric) || !valid_dtype(dtype)) return DM_ERR_INVALID_ARG;
+    if (!ctx || ctx->destroyed || !Xh || !Zh || !outh || !valid_metric(metric) || !valid_dtype(dtype))
+        return DM_ERR_INVALID_ARG;
     if (n < 1 || n > kMaxN || d < 1 || ldx < d || k < 1 || ldz < k || ldo < k) return DM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     const size_t es = dtype_size(dtype), os = out_size(dtype);

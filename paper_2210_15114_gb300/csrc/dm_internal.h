@@ -14,9 +14,11 @@ namespace dm {
 enum : uint32_t { kErrNone = 0, kErrNonfinite = DM_ERR_NONFINITE, kErrTimeout = DM_ERR_TIMEOUT,
                   kErrInternal = DM_ERR_INTERNAL };
 
-// Iteration cap of every device-side spin wait (with a short __nanosleep per
-// round, about a second in total).  On expiry the waiting kernel latches
-// DM_ERR_TIMEOUT, stops waiting and finishes its tile with what it has.
+// Default iteration cap of every device-side spin wait (with a short
+// __nanosleep per round, about a second in total).  On expiry the waiting
+// kernel latches DM_ERR_TIMEOUT, stops waiting and finishes its tile with
+// what it has.  A context can lower it (dm_set_wait_limit); the radix passes
+// and the ordered l1 query take the context's value as a launch argument.
 constexpr uint32_t kSpinLimit = 1u << 20;
 
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -72,6 +74,7 @@ struct SortArgs {
     uint32_t* counters;                  // passes tile counters
     void* sorted_out; int32_t* perm_out; // plan outputs, d x n
     uint32_t* err;
+    uint32_t spin_limit = kSpinLimit;    // rounds of a look-back wait before DM_ERR_TIMEOUT
 };
 size_t sort_hist_words(dm_dtype t, int64_t d);
 size_t sort_lookback_words(dm_dtype t, int64_t n, int64_t d);
@@ -81,6 +84,13 @@ cudaError_t sort_launch_keygen(const SortArgs& a, cudaStream_t s, int64_t* launc
 // Launch the radix passes listed in pass_list (digit positions, ascending).
 cudaError_t sort_launch_passes(const SortArgs& a, const int* pass_list, int npass,
                                cudaStream_t s, int64_t* launches);
+// Test of the bounded look-back wait: one CTA of the first FP32 radix pass
+// over one column of two tiles, started as the column's second tile (the
+// caller sets *counters to 1 and zeroes the histogram and look-back words),
+// so its predecessor never publishes.  Writes stay inside the first tile of
+// keys_b / vals_b; the wait runs out after a.spin_limit rounds.
+cudaError_t sort_launch_unpublished_wait(const SortArgs& a, cudaStream_t s, int64_t* launches);
+int sort_tile_f32();
 
 // Column sums of the query block and the shifted contraction:
 //   u[j]   = sum_i Z[i,j]
@@ -152,6 +162,7 @@ struct L1QueryArgs {
     uint32_t* err;
     int num_sms;
     int deterministic;                   // 1: ordered accumulation, 0: L2 reductions
+    uint32_t spin_limit = kSpinLimit;    // rounds of the ordered mode's wait
 };
 size_t l1_query_scratch_bytes(dm_dtype t, int64_t n, int64_t d, int64_t k, int num_sms);
 cudaError_t l1_prologue_launch(const L1QueryArgs& a, cudaStream_t s, int64_t* launches);

@@ -107,6 +107,7 @@ struct QParams {
     const Wide* pre;                  // G x d x T x 2KC exclusive tile prefixes
     uint32_t* err;
     int T, G;
+    uint32_t spin_limit;              // rounds of the ordered mode's wait
 };
 
 // ---------------------------------------------------------------- helpers
@@ -223,10 +224,11 @@ __device__ __forceinline__ void red_add(long long* p, const long long (&v)[N]) {
 }
 
 // Bounded wait until *p >= target (acquire).  Returns false on timeout.
-__device__ __forceinline__ bool wait_geq(const uint32_t* p, uint32_t target, uint32_t* err) {
+__device__ __forceinline__ bool wait_geq(const uint32_t* p, uint32_t target, uint32_t* err,
+                                         uint32_t spin_limit) {
     uint32_t spins = 0;
     while (ld_acquire(p) < target) {
-        if (++spins > kSpinLimit) { set_error(err, kErrTimeout); return false; }
+        if (++spins > spin_limit) { set_error(err, kErrTimeout); return false; }
         __nanosleep(128);
     }
     return true;
@@ -356,7 +358,7 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
         }
         // D. (ordered) coordinate order: wait for every tile of coordinate c-1
         if (MODE == kOrdered) {
-            if (c > 0 && tid == 0) wait_geq(p.done + (int64_t)g * d + c - 1, (uint32_t)T, p.err);
+            if (c > 0 && tid == 0) wait_geq(p.done + (int64_t)g * d + c - 1, (uint32_t)T, p.err, p.spin_limit);
         }
         __syncthreads();
         const uint32_t next = s_claim[slot ^ 1];
@@ -914,6 +916,7 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
     p.err = a.err;
     p.T = (int)L.T;
     p.G = (int)L.G;
+    p.spin_limit = a.spin_limit;
 
     auto kern = atomic ? l1_query_kernel<DT, KC, kAtomic> : l1_query_kernel<DT, KC, kOrdered>;
     int occ = 0;

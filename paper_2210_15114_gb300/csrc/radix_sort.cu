@@ -219,7 +219,8 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
                 typename Types<DT>::V* __restrict__ sorted_out,  // last pass only
                 int32_t* __restrict__ perm_out,                   // last pass only
                 const uint32_t* __restrict__ hist, uint32_t* lookback, uint32_t* counter,
-                int64_t n, int D, int pass, int P, int T, int first, int last, uint32_t* err) {
+                int64_t n, int D, int pass, int P, int T, int first, int last, uint32_t* err,
+                uint32_t spin_limit) {
     using Key = typename Types<DT>::Key;
     using V = typename Types<DT>::V;
     constexpr int ITEMS = PassCfg<DT>::ITEMS, TILE = PassCfg<DT>::TILE;
@@ -322,7 +323,7 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
                 if (!done) {
                     uint32_t sq = sv[u];
                     while ((sq & ~kValMask) == 0) {
-                        if (++spins > kSpinLimit) { set_error(err, kErrTimeout); sq = kFlagInc; break; }
+                        if (++spins > spin_limit) { set_error(err, kErrTimeout); sq = kFlagInc; break; }
                         __nanosleep(64);
                         sq = ld_relaxed(&lb[(int64_t)(base - u) * kRadix + tid]);
                     }
@@ -417,7 +418,7 @@ cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, 
         onesweep_kernel<DT><<<(unsigned)(a.d * T), kThreads, 0, s>>>(
             kin, vin, kout, vout, static_cast<V*>(a.sorted_out), a.perm_out, a.hist,
             a.lookback + i * lb_stride, a.counters + i, a.n, (int)a.d, pass_list[i], P, T, first,
-            last, a.err);
+            last, a.err, a.spin_limit);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         ++*launches;
@@ -428,6 +429,23 @@ cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, 
 }
 
 }  // namespace
+
+int sort_tile_f32() { return PassCfg<DM_F32>::TILE; }
+
+cudaError_t sort_launch_unpublished_wait(const SortArgs& a, cudaStream_t s, int64_t* launches) {
+    using Key = Types<DM_F32>::Key;
+    constexpr int TILE = PassCfg<DM_F32>::TILE;
+    if (a.dtype != DM_F32 || a.d != 1 || a.n != 2 * TILE) return cudaErrorInvalidValue;
+    // One CTA; it claims ticket 1 = (column 0, tile 1) and waits for tile 0.
+    // First pass (no payload read), not the last (keys_b / vals_b written).
+    onesweep_kernel<DM_F32><<<1, kThreads, 0, s>>>(
+        static_cast<const Key*>(a.keys_a), nullptr, static_cast<Key*>(a.keys_b), a.vals_b, nullptr,
+        nullptr, a.hist, a.lookback, a.counters, a.n, 1, 0, sort_passes(DM_F32), 2, 1, 0, a.err,
+        a.spin_limit);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) ++*launches;
+    return e;
+}
 
 int sort_passes(dm_dtype t) { return key_bits(t) / 8; }
 

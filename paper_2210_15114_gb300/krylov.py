@@ -70,6 +70,9 @@ def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
     theta, V = torch.linalg.eigh(M)
     order = torch.argsort(theta.abs(), descending=True)[:rank]
     U = Q @ V[:, order].to(dt)
+    # the eigensolver has synchronized already: surface any device-side error
+    # of the products (a bounded wait that ran out) instead of returning
+    binding.dm_sync(plan.ctx)
     return theta[order], U
 
 

@@ -42,6 +42,7 @@ def test_wrapper_routes_gradients(monkeypatch, metric):
     monkeypatch.setattr(binding, "dm_prepare", prepare)
     monkeypatch.setattr(binding, "dm_matmat", matmat)
     monkeypatch.setattr(binding, "dm_grad", grad)
+    monkeypatch.setattr(binding, "dm_sync", lambda ctx: None)
 
     rng = np.random.default_rng(5)
     X0 = torch.from_numpy(rng.normal(size=(40, 3)))

@@ -3,16 +3,19 @@ with the CPU oracle, through the C ABI.
 
 Tolerances (Frobenius relative error of G against the FP64 oracle on the same
 input values): 1e-5 for FP32, 1e-12 for FP64; int32 inputs give exact int64
-gradients, compared bit for bit.  Small cases are compared on every entry;
-the full-size workload (n = 2^21, d = 64, k = 1) on sampled rows computed by
-the oracle's definition, plus two properties that hold at any size:
-translation invariance (every column of G sums to zero) and Euler's relation
-sum X . G = deg * w^T A z (deg 1 for l1, 2 for squared l2).
+gradients, compared bit for bit.  Every case is compared on
+every entry; the full-size workload (n = 2^21, d = 64, k = 1, uniform and
+tie-heavy) against the oracle's sorted-order gradient (l1, the coordinates on
+parallel host processes) or its closed form (squared l2), with sampled rows
+checked once more against the definition, plus two properties that hold at
+any size: translation invariance (every column of G sums to zero) and
+Euler's relation sum X . G = deg * w^T A z (deg 1 for l1, 2 for squared l2).
 """
 import numpy as np
 import pytest
 
 import oracle
+from oracle import parallel
 from paper_2210_15114_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -154,7 +157,7 @@ def full(request):
 
 
 @pytest.mark.parametrize("metric", ["l1", "l2sq"])
-def test_grad_full_size_sampled_rows(dm, ctx, full, metric):
+def test_grad_full_size_whole_block(dm, ctx, full, metric):
     X, W, Z = full
     n = len(X)
     Xd, Wd, Zd = dev(X), dev(W), dev(Z)
@@ -163,9 +166,10 @@ def test_grad_full_size_sampled_rows(dm, ctx, full, metric):
     Az = dm.dm_matmat(plan, Zd)
     dm.dm_sync(ctx)
     Gh = G.cpu().numpy().astype(np.float64)
-    rows = inputs.sample_rows(n, 12)
-    want = GRAD[metric](X, W, Z, rows)
-    check(Gh[rows], want, np.float32)
+    whole = parallel.l1_grad_sort(X, W, Z) if metric == "l1" else oracle.l2sq_grad_closed(X, W, Z)
+    check(Gh, whole, np.float32)
+    rows = inputs.sample_rows(n, 6)
+    check(Gh[rows], GRAD[metric](X, W, Z, rows), np.float32)
     # translation invariance: columns of G sum to zero
     col = np.abs(Gh.sum(axis=0))
     scale = np.sqrt((Gh ** 2).sum(axis=0) * n)

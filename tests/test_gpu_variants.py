@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import parallel
 from paper_2210_15114_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -189,22 +190,29 @@ def test_l2_embed_approximates_l2(dm, ctx):
 
 
 # ---------------------------------------------------------------- full size
-def test_variants_full_size_sampled(dm, ctx):
+def test_variants_full_size_whole_block(dm, ctx):
+    # every variant on the step's workload (n = 2^20, d = 32, k = 16), the
+    # whole block against the oracle's O(n d log n) or O(n d p k) forms, and
+    # sampled rows once more against the definitions
     X, Z = inputs.workload_mixture_f32()
-    rows = inputs.sample_rows(len(X), 8)
+    rows = inputs.sample_rows(len(X), 4)
     Xd, Zd = dev(X), dev(Z)
-    # ||.||_4^4 and ||.||_3^3 on the mixture
-    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, Xd, 4), Zd)
-    check(out.cpu().numpy()[rows], oracle.lpp_rows(X, Z, 4, rows), np.float32)
-    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, Xd, 3), Zd)
-    check(out.cpu().numpy()[rows], oracle.lpp_rows(X, Z, 3, rows), np.float32)
-    # approximate l2 with m = 256
+    # ||.||_4^4 (even-p expansion) and ||.||_3^3 (odd p through sorted order)
+    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, Xd, 4), Zd).cpu().numpy()
+    check(out, oracle.lpp_even_expansion(X, Z, 4), np.float32)
+    check(out[rows], oracle.lpp_rows(X, Z, 4, rows), np.float32)
+    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, Xd, 3), Zd).cpu().numpy()
+    check(out, parallel.lpp_odd_sort(X, Z, 3), np.float32)
+    check(out[rows], oracle.lpp_rows(X, Z, 3, rows), np.float32)
+    # approximate l2 with m = 256: Algorithms 1-2 on the mapped points
     G = inputs.embedding_matrix(256, X.shape[1])
-    out = dm.dm_matmat(dm.dm_prepare_l2_embed(ctx, Xd, dev(G)), Zd)
-    want = oracle.l1_rows(oracle.l2_embed(X, G), Z, rows)
-    check(out.cpu().numpy()[rows], want, np.float32)
+    out = dm.dm_matmat(dm.dm_prepare_l2_embed(ctx, Xd, dev(G)), Zd).cpu().numpy()
+    T = oracle.l2_embed(X, G)
+    check(out, parallel.l1_sort(T, Z), np.float32)
+    check(out[rows], oracle.l1_rows(T, Z, rows), np.float32)
     # total variation on distributions
     P = inputs.simplex_points(len(X), X.shape[1])
-    out = dm.dm_matmat(dm.dm_prepare(ctx, "tv", dev(P)), Zd)
-    check(out.cpu().numpy()[rows], oracle.tv_rows(P, Z, rows), np.float32)
+    out = dm.dm_matmat(dm.dm_prepare(ctx, "tv", dev(P)), Zd).cpu().numpy()
+    check(out, 0.5 * parallel.l1_sort(P, Z), np.float32)
+    check(out[rows], oracle.tv_rows(P, Z, rows), np.float32)
     dm.dm_sync(ctx)

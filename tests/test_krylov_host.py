@@ -2,6 +2,8 @@
 orthonormalization of a block against the earlier basis, for full-rank,
 rank-deficient and zero blocks.  The products A Z are the library's and are
 tested on the GPU; these steps are dense linear algebra on tall blocks."""
+import types
+
 import numpy as np
 import pytest
 
@@ -110,8 +112,11 @@ def test_block_krylov_host_steps_with_a_dense_product(monkeypatch, metric):
         return out
 
     monkeypatch.setattr(binding, "dm_matmat", product)
+    synced = []
+    monkeypatch.setattr(binding, "dm_sync", lambda ctx: synced.append(ctx))
     Pi = torch.from_numpy(rng.normal(size=(500, 10)).astype(np.float32))
-    theta, U = krylov.block_krylov(None, Pi, q=3, rank=8)
+    theta, U = krylov.block_krylov(types.SimpleNamespace(ctx="ctx"), Pi, q=3, rank=8)
+    assert synced == ["ctx"]          # device-side errors are collected once, at the end
     ev = np.linalg.eigvalsh(_dense(metric, X))
     ev = ev[np.argsort(-np.abs(ev))]
     top = 6 if metric == "l2sq" else 4

@@ -2,7 +2,8 @@
 takes all of its scratch from a fixed device array instead of allocating.
 
 Compared with the allocating path (dm_prepare with DM_L2SQ, then dm_matmat)
-on the same device inputs, on two calls in a row (the second reuses the
+on the same device inputs, and with the CPU oracle's p = 2 identity
+(Appendix A) on the whole block, on two calls in a row (the second reuses the
 scratch the first left behind): relative error <= 1e-5 for FP32, <= 1e-12
 for FP64, and identical int64 results for int32 inputs.  The file is named
 to run last so that the entry point is also exercised after every other GPU
@@ -13,6 +14,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2210_15114_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -78,6 +80,7 @@ def test_noalloc_matches_allocating_path(dm, label, make_x, make_z):
     want = dm.dm_matmat(plan, Zd)
     dm.dm_sync(ctx)
     want = want.cpu().numpy()
+    exact = oracle.l2sq_identity(X, Z)
     out_dtype = torch.int64 if X.dtype == np.int32 else Xd.dtype
     for call in range(2):
         out = torch.full((len(X), Z.shape[1]), -7, dtype=out_dtype, device="cuda")
@@ -86,9 +89,12 @@ def test_noalloc_matches_allocating_path(dm, label, make_x, make_z):
         got = out.cpu().numpy()
         if X.dtype == np.int32:
             np.testing.assert_array_equal(got, want, err_msg=f"call {call}")
+            np.testing.assert_array_equal(got, exact, err_msg=f"call {call} vs oracle")
         else:
             err = rel(got, want)
             assert err <= TOL[X.dtype.type], f"call {call}: relative error {err:.3e}"
+            err = rel(got, exact)
+            assert err <= TOL[X.dtype.type], f"call {call}: relative error {err:.3e} vs oracle"
     dm.dm_plan_destroy(plan)
     dm.dm_destroy(ctx)
 
