@@ -72,10 +72,13 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_config(a, flush):
+def workload_config(a):
+    # identical in both arms: the driver compares the two config objects
     return {"workload": f"gaussian-mixture-16 n={a.n} d={a.d} k={a.k} fp32",
             "n": a.n, "d": a.d, "k": a.k, "clusters": 16, "dtype": "fp32",
-            "products": ["l1", "l2sq"], "prepare_in_step": True, "l2_flush": flush,
+            "products": ["l1", "l2sq"], "prepare_in_step": True,
+            "l2_flush": "GPU arm: 512 MiB write between timed steps (outside the step events); "
+                        "CPU arm: none",
             "l1_accumulation": "L2 reductions (dm_set_deterministic off)",
             "l2_engine": getattr(a, "engine", "auto")}
 
@@ -262,38 +265,51 @@ def start_clock_sampler(dev):
 _WORKLOAD_CACHE = {}
 
 
-def cpu_oracle_sample(n, d, d_sample, k):
-    """Time the CPU oracle (sort-based l1 form and p = 2 identity) on the first
-    d_sample coordinates of the workload, in this process.  Returns seconds."""
+def cpu_oracle_sample(n, d, d_sample, k, pool=None, workers=1):
+    """Time the CPU oracle on the workload: the sort-based l1 form of
+    Algorithms 1-2 on the first d_sample coordinates (blocks of coordinates on
+    `workers` processes of `pool`) and the p = 2 identity on all coordinates,
+    in this process.  Returns seconds."""
     import oracle
+    from oracle import parallel
     from paper_2210_15114_gb300 import inputs
     key = (n, d, k)
     if key not in _WORKLOAD_CACHE:
         _WORKLOAD_CACHE.clear()
         _WORKLOAD_CACHE[key] = inputs.workload_mixture_f32(n=n, d=d, k=k)
     X, Z = _WORKLOAD_CACHE[key]
-    Xs = X[:, :d_sample]
     t0 = time.perf_counter()
-    oracle.l1_sort(Xs, Z)
-    oracle.l2sq_identity(Xs, Z)
+    parallel.l1_sort(X[:, :d_sample], Z, workers, pool)
+    oracle.l2sq_identity(X, Z)
     return time.perf_counter() - t0
 
 
-def cpu_baseline(n, d, k, d_sample):
-    """The oracle as it stands, single-threaded, in a spawned subprocess."""
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.cpu_oracle_sample(%d, %d, %d, %d)))" % (ROOT, n, d, d_sample, k))
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                       timeout=600)
+def cpu_baseline(n, d, k):
+    """The oracle as it stands on all host cores, in a spawned subprocess (no
+    CUDA context): the whole workload, every coordinate, at full n."""
+    cores = os.cpu_count() or 1
+    code = ("import sys, json; sys.path.insert(0, %r); import bench\n"
+            "from oracle import parallel\n"
+            "if __name__ == '__main__':\n"
+            "    with parallel.executor(%d) as pool:\n"
+            "        print(json.dumps(bench.cpu_oracle_sample(%d, %d, %d, %d, pool, %d)))\n"
+            % (ROOT, cores, n, d, d, k, cores))
+    with tempfile.NamedTemporaryFile("w", suffix=".py", delete=False) as f:
+        f.write(code)
+        path = f.name
+    try:
+        r = subprocess.run([sys.executable, path], capture_output=True, text=True, timeout=900)
+    finally:
+        os.unlink(path)
     if r.returncode != 0:
         return {"value": None, "error": r.stderr[-300:]}
     secs = float(r.stdout.strip().splitlines()[-1])
-    units = 2 * n * d_sample * k
-    return {"value": units / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+    units = 2 * n * d * k
+    return {"value": units / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
             "seconds": secs,
-            "sample": f"first {d_sample} of the coordinates at full n={n}, k={k}: numpy "
-                      f"sort-based l1 form (Algorithms 1-2) + p=2 identity, FP64, one thread"}
+            "sample": f"the whole workload (all {d} coordinates, n={n}, k={k}): numpy sort-based l1 "
+                      f"form (Algorithms 1-2) with the coordinates on {cores} processes + p=2 "
+                      f"identity (BLAS threads), FP64"}
 
 
 # ------------------------------------------------------------- algorithmic bytes
@@ -553,22 +569,24 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[var] = "1"   # before numpy is imported: the oracle runs on one core
-    d_sample = 1
-    units = 2 * a.n * d_sample * a.k
-    for _ in range(a.warmup):
-        cpu_oracle_sample(a.n, a.d, d_sample, a.k)
-    times = [cpu_oracle_sample(a.n, a.d, d_sample, a.k) for _ in range(a.steps)]
+    from oracle import parallel
+    cores = os.cpu_count() or 1
+    # one coordinate per core per step: a bounded sample of the l1 part, the
+    # whole squared-l2 part
+    d_sample = max(1, min(a.d, cores))
+    units = a.n * d_sample * a.k + a.n * a.d * a.k
+    with parallel.executor(min(cores, d_sample)) as pool:
+        for _ in range(a.warmup):
+            cpu_oracle_sample(a.n, a.d, d_sample, a.k, pool, d_sample)
+        times = [cpu_oracle_sample(a.n, a.d, d_sample, a.k, pool, d_sample) for _ in range(a.steps)]
     ms = 1e3 * statistics.mean(times)
     value = units / (ms / 1e3)
-    cores = 1
-    sample = (f"first {d_sample} of {a.d} coordinates at full n={a.n}, k={a.k} per step: numpy "
-              f"sort-based l1 form + p=2 identity, FP64")
+    sample = (f"per step: the l1 sort-based form (Algorithms 1-2) on {d_sample} of {a.d} coordinates "
+              f"(one process per coordinate) + the p=2 identity on all {a.d}, full n={a.n}, k={a.k}, FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(a, "none (CPU)"),
+            "data": "synthetic", "config": workload_config(a),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -760,12 +778,12 @@ def main():
 
     cpu = None
     if not a.no_cpu and world == 1:
-        cpu = cpu_baseline(a.n, a.d, a.k, 4)
+        cpu = cpu_baseline(a.n, a.d, a.k)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(a, "512 MiB write between timed steps (outside the step events)"),
+            "config": workload_config(a),
             "parallelism": "replicas" if world > 1 else "single GPU",
             "gpu_launches": launches, "launches_per_step": launches / a.steps,
             "wall_s_timed_region": t_wall,

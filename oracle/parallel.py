@@ -93,17 +93,24 @@ def _result_dtype(X, Z):
         else np.float64
 
 
-def _run(jobs, workers):
-    # An executor (not a Pool) so that a worker that dies raises here instead
-    # of being replaced forever.
-    if len(jobs) == 1:
+def executor(workers: int) -> ProcessPoolExecutor:
+    """A spawned worker pool that callers may pass to several calls (an
+    executor, not a Pool: a worker that dies raises instead of being replaced
+    forever)."""
+    return ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
+def _run(jobs, pool=None):
+    if pool is not None:
+        list(pool.map(_work, jobs))
+    elif len(jobs) == 1:
         _work(jobs[0])
-        return
-    with ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
-        list(ex.map(_work, jobs))
+    else:
+        with executor(len(jobs)) as ex:
+            list(ex.map(_work, jobs))
 
 
-def _product(kind, X, Z, extra, workers):
+def _product(kind, X, Z, extra, workers, pool=None):
     X = np.asarray(X)
     Z = np.asarray(Z)
     if X.ndim == 1:
@@ -121,7 +128,7 @@ def _product(kind, X, Z, extra, workers):
     try:
         jobs = [(kind, lo, hi, s, [sx.spec, sz.spec, so.spec], extra)
                 for s, (lo, hi) in enumerate(blocks)]
-        _run(jobs, len(blocks))
+        _run(jobs, pool)
         out = so.array[0].copy()
         for s in range(1, len(blocks)):
             out += so.array[s]
@@ -131,10 +138,11 @@ def _product(kind, X, Z, extra, workers):
     return out[:, 0] if squeeze else out
 
 
-def l1_sort(X, Z, workers: int | None = None) -> np.ndarray:
+def l1_sort(X, Z, workers: int | None = None, pool=None) -> np.ndarray:
     """``oracle.l1_sort`` (Algorithms 1 and 2) with blocks of coordinates on
-    separate processes; the blocks' products are added in block order."""
-    return _product("l1_sort", X, Z, None, workers)
+    separate processes (a fresh pool, or ``pool`` from ``executor()``); the
+    blocks' products are added in block order."""
+    return _product("l1_sort", X, Z, None, workers, pool)
 
 
 def lpp_odd_sort(X, Z, p: int, workers: int | None = None) -> np.ndarray:
@@ -166,7 +174,7 @@ def l1_grad_sort(X, W, Z, workers: int | None = None) -> np.ndarray:
     try:
         jobs = [("l1_grad_sort", lo, hi, 0, [sx.spec, sw.spec, sz.spec, sg.spec], None)
                 for lo, hi in blocks]
-        _run(jobs, len(blocks))
+        _run(jobs)
         G = sg.array.copy()
     finally:
         for sh in (sx, sw, sz, sg):

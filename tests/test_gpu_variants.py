@@ -172,7 +172,7 @@ def test_l2_embed_matches_oracle(dm, ctx, dtype, n, d, m):
     plan = dm.dm_prepare_l2_embed(ctx, dev(X), dev(G))
     out = dm.dm_matmat(plan, dev(Z))
     dm.dm_sync(ctx)
-    tol = 1e-5 if dtype == np.float32 else 1e-11
+    tol = 1e-5 if dtype == np.float32 else 1e-12
     check(out.cpu().numpy(), oracle.l2_approx(X, G, Z), dtype, tol)
 
 
