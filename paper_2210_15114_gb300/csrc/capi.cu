@@ -585,7 +585,7 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
             ProfScope ps(e, "l1_prologue");
             DM_TRY_CUDA(l1_prologue_launch(q, e.stream, &ctx->launches));
         }
-        if (q.deterministic) {   // the ordered mode's separate pass of tile sums
+        {
             ProfScope ps(e, "l1_aggregate");
             DM_TRY_CUDA(l1_aggregate_launch(q, e.stream, &ctx->launches));
         }

@@ -41,21 +41,23 @@
 //      works on tile-local values;
 //   D. the values are summed over the coordinates into a partial output.
 //
-// Default mode (L2 reductions), one kernel: l1_onepass stages each tile's
-//   permutation and gathered rows in shared memory by cp.async one tile
-//   ahead, publishes the tile's sums and takes Pt from a decoupled look-back
-//   over the earlier tiles (claims in (group, tile, coordinate) order), and
-//   adds every value into outg with a vector reduction in L2; l1_finalize
-//   then writes out = outg + R^T Z - R_k 1^T Z in the caller's layout.
-//
-// Ordered mode (dm_set_deterministic), reduce-then-scan:
-//   l1_aggregate + l1_tile_scan form every tile's sums (one warp per tile)
-//   and their exclusive scan over the tiles of each (group, coordinate) in
-//   FP64; l1_query (claims in (group, coordinate, tile) order, the next
-//   tile's permutation loaded while the current one is evaluated) waits
+// Kernels of the sorted part (reduce-then-scan):
+//   l1_aggregate + l1_tile_scan form every tile's sums of z and (x - mu) z
+//   (one warp per tile, 256-bit row loads) and their exclusive scan over the
+//   tiles of each (group, coordinate) in FP64: Pt.
+//   l1_query (claims in (group, coordinate, tile) order, the next tile's
+//   permutation and coordinates loaded while the current one is evaluated)
+//   does steps A-D; a thread takes SEG_LEN consecutive positions and one
+//   16-byte slice (QW columns) of their rows, the rest of a row on the
+//   adjacent thread.
+//   Step D, default mode: every value is added into the Acc-type outg with
+//   vector reductions in L2 (no waits; the order of the d additions per
+//   element varies from run to run); l1_finalize then writes
+//   out = outg + R^T Z - R_k 1^T Z in the caller's layout.
+//   Step D, ordered mode (dm_set_deterministic): a tile of coordinate c waits
 //   (bounded spin) until every tile of coordinate c-1 of its group is done,
 //   then adds its values into the FP64 partial output outw with plain loads
-//   and stores, in coordinate order, and the last coordinate writes out.
+//   and stores, in coordinate order; the last coordinate writes out.
 // Every wait is on work claimed earlier by a running CTA: no deadlock.
 // Integer data run the same steps exactly in int64.
 #include <algorithm>
@@ -84,21 +86,6 @@ struct QCfg {
     static constexpr int NV = 2 * KC;                          // scanned quantities
     static_assert(KC % QW == 0, "tile shape");
 };
-
-// Accumulation of the per-coordinate values over the coordinates (the sum
-// over i in [d] of Algorithm 2), two modes:
-//   ordered (l1_query_kernel): coordinate c waits until every tile of
-//             coordinate c-1 has written, then reads, adds and writes the
-//             Wide-type partial output outw (FP64 for FP32 data: the sum over
-//             the coordinates runs in FP64, in a fixed order, so the result
-//             does not depend on scheduling); coordinate 0 stores the
-//             point-linear part R^T Z - R_k 1^T Z first and coordinate d-1
-//             writes the caller's output.
-//   L2 reductions (l1_onepass_kernel): every value is added into the
-//             Acc-type outg with a vector reduction in L2 (no waits; the order
-//             of the d additions per element varies from run to run); a
-//             finalize kernel adds the point-linear part and writes the
-//             caller's output.
 
 template <class V, class Acc, class Wide>
 struct QParams {
@@ -242,309 +229,8 @@ __device__ __forceinline__ bool wait_geq(const uint32_t* p, uint32_t target, uin
     return true;
 }
 
-// ------------------------------------------------------- one-pass kernel
-// The sorted pass of the L2-reduction mode in one launch, without a separate
-// pass of tile sums.  Per tile (TILE_E consecutive sorted positions of one
-// coordinate c of one column group g):
-//   1. its permutation and coordinates, and then its gathered rows of Zg[g],
-//      arrive in shared memory by cp.async while the previous tile is
-//      evaluated (the copies hold no registers);
-//   2. the in-tile scan gives every position its exclusive in-tile prefix
-//      and the tile its sums of z and (x - mu) z, which are published at once
-//      (flag "aggregate");
-//   3. one warp finds the tile's exclusive prefix by a decoupled look-back
-//      over the earlier tiles of (g, c): it adds their published sums back to
-//      the nearest tile that has published its inclusive prefix, then
-//      publishes its own inclusive prefix (flag "inclusive");
-//   4. the values are evaluated as in l1_query_kernel (steps C and E) and
-//      added into outg with vector reductions in L2.
-// Tickets are claimed in (group, tile, coordinate) order, coordinate fastest,
-// so the d look-back chains of a group advance side by side with a few tiles
-// in flight each.  A tile waits only for tiles of smaller tickets, every one
-// of them claimed by a running CTA, so each wait ends; it is bounded anyway
-// (DM_ERR_TIMEOUT, after which the tile goes on with what it has).
-constexpr uint32_t kTileAgg = 1, kTileInc = 2;
-
-template <dm_dtype DT, int KC>
-struct OCfg {
-    using Q = QCfg<DT, KC>;
-    using V = typename Types<DT>::V;
-    static constexpr int SEG_LEN = Q::SEG_LEN, TILE_E = Q::TILE_E, NQ = Q::NQ, QW = Q::QW;
-    static constexpr int SEGS = Q::SEGS, NV = Q::NV;
-    static constexpr int CHUNK = QW * (int)sizeof(V);           // bytes a thread gathers per row
-    static constexpr int ROWB = KC * (int)sizeof(V);            // bytes of a Zg row
-    // A segment's SEG_LEN rows are contiguous, segments 16 bytes apart more:
-    // the 16-byte reads of one row index by the lanes of a warp fall on
-    // different bank groups.
-    static constexpr int SEGB = SEG_LEN * ROWB + 16;
-    static constexpr int ZBUF = SEGS * SEGB;                    // bytes of one tile's rows
-    static constexpr int PSEG = SEG_LEN + 1;                    // padded positions per segment
-    static constexpr int PBUF = SEGS * PSEG;                    // elements of one perm / xs slot
-    static constexpr int PER = TILE_E / kThreads;               // perm / xs elements a thread copies
-    static constexpr size_t smem = 2 * (size_t)ZBUF + 3 * (size_t)PBUF * (4 + sizeof(V));
-    static_assert(TILE_E % kThreads == 0, "tile copy");
-    static_assert((SEG_LEN * ROWB) % 16 == 0, "16-byte aligned segments");
-};
-
-template <int B>
-__device__ __forceinline__ void cp_async_n(void* s, const void* g, bool valid) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    if constexpr (B == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(sa), "l"(g), "r"(valid ? 16 : 0) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" :: "r"(sa), "l"(g), "n"(B), "r"(valid ? B : 0)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-template <dm_dtype DT, int KC>
-__global__ void __launch_bounds__(kThreads, 2)
-l1_onepass_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename Types<DT>::Wide> p,
-                  uint32_t* __restrict__ flags, typename Types<DT>::Wide* __restrict__ agg_st,
-                  typename Types<DT>::Wide* __restrict__ inc_st) {
-    using Cfg = OCfg<DT, KC>;
-    using V = typename Types<DT>::V;
-    using Acc = typename Types<DT>::Acc;
-    using Wide = typename Types<DT>::Wide;
-    constexpr int SEG_LEN = Cfg::SEG_LEN, TILE_E = Cfg::TILE_E, NV = Cfg::NV;
-    constexpr int QW = Cfg::QW, NQ = Cfg::NQ, CHUNK = Cfg::CHUNK, ROWB = Cfg::ROWB;
-    constexpr int SEGB = Cfg::SEGB, ZBUF = Cfg::ZBUF, PSEG = Cfg::PSEG, PBUF = Cfg::PBUF, PER = Cfg::PER;
-    constexpr int SPW = 32 / NQ;   // segments per warp
-    constexpr uint32_t FULL = 0xffffffffu;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char* zb = smem_raw;                                              // [2][ZBUF] bytes
-    int32_t* pb = reinterpret_cast<int32_t*>(smem_raw + 2 * ZBUF);              // [3][PBUF]
-    V* xb = reinterpret_cast<V*>(smem_raw + 2 * ZBUF + 3 * PBUF * 4);           // [3][PBUF]
-    __shared__ Acc wt[kWarps][NV];
-    __shared__ Acc ag_s[2][KC];
-    __shared__ uint32_t s_claim[3];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int quad = tid % NQ, seg = tid / NQ;
-    const int col0 = quad * QW;
-    const int d = p.d, T = p.T;
-    const uint32_t total = (uint32_t)p.G * (uint32_t)d * (uint32_t)T;
-    const int i0 = seg * SEG_LEN;
-    const uint32_t nn = (uint32_t)p.n;
-
-    auto decode = [&](uint32_t tk, int& g, int& t, int& c) {
-        c = (int)(tk % (uint32_t)d);
-        const uint32_t r = tk / (uint32_t)d;
-        t = (int)(r % (uint32_t)T);
-        g = (int)(r / (uint32_t)T);
-    };
-    // permutation and coordinates of ticket tk into slot ps (zeros past the
-    // column's end)
-    auto copy_perm = [&](uint32_t tk, int ps) {
-        int g, t, c;
-        decode(tk, g, t, c);
-        const int64_t e0 = (int64_t)t * TILE_E;
-        const int ne = (int)min64(TILE_E, p.n - e0);
-        const int64_t sbase = (int64_t)c * p.n + e0;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int pos = tid + j * kThreads;
-            const int pi = ps * PBUF + (pos / SEG_LEN) * PSEG + pos % SEG_LEN;
-            const bool ok = pos < ne;
-            cp_async_n<4>(pb + pi, p.perm + (ok ? sbase + pos : 0), ok);
-            cp_async_n<(int)sizeof(V)>(xb + pi, p.xs + (ok ? sbase + pos : 0), ok);
-        }
-    };
-    // this thread's slices of the rows Zg[g][perm[r]] of ticket tk (permutation
-    // in slot ps) into row buffer zs; invalid positions are zero-filled
-    auto issue_gathers = [&](uint32_t tk, int ps, int zs) {
-        int g, t, c;
-        decode(tk, g, t, c);
-        const int ne = (int)min64(TILE_E, p.n - (int64_t)t * TILE_E);
-        const V* zg = p.Zg + (int64_t)g * p.n * KC + col0;
-        unsigned char* dst = zb + zs * ZBUF + seg * SEGB + quad * CHUNK;
-#pragma unroll
-        for (int i = 0; i < SEG_LEN; ++i) {
-            const int32_t pe = pb[ps * PBUF + seg * PSEG + i];
-            const bool ok = i0 + i < ne && (uint32_t)pe < nn;
-            cp_async_n<CHUNK>(dst + i * ROWB, zg + (ok ? (int64_t)pe * KC : 0), ok);
-        }
-    };
-
-    if (tid == 0) {
-        s_claim[0] = atomicAdd(p.counter, 1u);
-        s_claim[1] = atomicAdd(p.counter, 1u);
-    }
-    __syncthreads();
-    uint32_t cur = s_claim[0], nxt = s_claim[1];
-    if (cur < total) copy_perm(cur, 0);
-    cp_commit();
-    cp_wait_all();
-    __syncthreads();
-    if (cur < total) issue_gathers(cur, 0, 0);
-    if (nxt < total) copy_perm(nxt, 1);
-    cp_commit();
-
-    for (int it = 0; cur < total; ++it) {
-        const int ps = it % 3, zs = it & 1;
-        if (tid == 0) s_claim[(it + 2) % 3] = atomicAdd(p.counter, 1u);
-        cp_wait_all();
-        __syncthreads();   // (1) rows of cur and permutation of nxt are in place
-        const uint32_t nx2 = s_claim[(it + 2) % 3];
-        if (nxt < total) issue_gathers(nxt, (it + 1) % 3, zs ^ 1);
-        if (nx2 < total) copy_perm(nx2, (it + 2) % 3);
-        cp_commit();
-
-        int g, t, c;
-        decode(cur, g, t, c);
-        const int ne = (int)min64(TILE_E, p.n - (int64_t)t * TILE_E);
-        const int32_t* pc = pb + ps * PBUF + seg * PSEG;
-        const V* xc = xb + ps * PBUF + seg * PSEG;
-        const V b = xb[ps * PBUF];
-
-        // A. this thread's positions: x - b, checked permutation, staged rows
-        Acc dx[SEG_LEN];
-        int32_t pe[SEG_LEN];
-        {
-            bool bad = false;
-#pragma unroll
-            for (int i = 0; i < SEG_LEN; ++i) {
-                const bool in = i0 + i < ne;
-                pe[i] = pc[i];
-                if (in && (uint32_t)pe[i] >= nn) bad = true;   // never for a valid plan
-                if (!in || (uint32_t)pe[i] >= nn) pe[i] = -1;
-                dx[i] = in ? diff(xc[i], b) : Acc(0);
-            }
-            if (bad) set_error(p.err, kErrInternal);
-        }
-        V zv[SEG_LEN][QW];
-        {
-            const unsigned char* src = zb + zs * ZBUF + seg * SEGB + quad * CHUNK;
-#pragma unroll
-            for (int i = 0; i < SEG_LEN; ++i) ld_vec<V, QW>(reinterpret_cast<const V*>(src + i * ROWB), zv[i]);
-        }
-
-        // B. in-tile exclusive prefixes of this thread's segment, warp totals
-        Acc Lz[QW], Lxz[QW];
-#pragma unroll
-        for (int q = 0; q < QW; ++q) {
-            Acc sz = 0, sxz = 0;
-#pragma unroll
-            for (int i = 0; i < SEG_LEN; ++i) {
-                const Acc z = (Acc)zv[i][q];
-                sz += z;
-                sxz = fmac(dx[i], z, sxz);
-            }
-            Acc iz = sz, ixz = sxz;
-#pragma unroll
-            for (int o = 1; o < SPW; o <<= 1) {
-                const Acc a = __shfl_up_sync(FULL, iz, o * NQ);
-                const Acc bb = __shfl_up_sync(FULL, ixz, o * NQ);
-                if (lane >= o * NQ) { iz += a; ixz += bb; }
-            }
-            Acc ez = __shfl_up_sync(FULL, iz, NQ);
-            Acc exz = __shfl_up_sync(FULL, ixz, NQ);
-            if (lane < NQ) { ez = 0; exz = 0; }
-            if (lane >= 32 - NQ) { wt[warp][col0 + q] = iz; wt[warp][KC + col0 + q] = ixz; }
-            Lz[q] = ez;
-            Lxz[q] = exz;
-        }
-        __syncthreads();   // (2) warp totals in place
-
-        // C. warp 0: the tile's sums, published, and its exclusive prefix by
-        // look-back over the earlier tiles of (g, c); alpha, gamma from it
-        if (warp == 0) {
-            Acc s = 0;
-            if (lane < NV) {
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w) s += wt[w][lane];
-            }
-            const Acc s_col = __shfl_sync(FULL, s, lane >= KC ? lane - KC : lane);   // sum of z of the lane's column
-            const Wide bm = (Wide)b - (Wide)p.mu[(int64_t)c * p.mu_stride];
-            Wide a = 0;
-            if (lane < KC) a = (Wide)s;
-            else if (lane < NV) a = bm * (Wide)s_col + (Wide)s;
-            const int64_t chain = ((int64_t)g * d + c) * T;   // tile 0 of (g, c)
-            const int64_t me = chain + t;
-            Wide ex = 0;
-            if (t == 0) {
-                if (lane < NV) __stcg(inc_st + me * NV + lane, a);
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release(flags + me, kTileInc);
-            } else {
-                if (lane < NV) __stcg(agg_st + me * NV + lane, a);
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release(flags + me, kTileAgg);
-                int j = t - 1;   // the nearest earlier tile not yet added
-                uint32_t spins = 0;
-                while (true) {
-                    const int jj = j - lane;
-                    const uint32_t f = jj >= 0 ? ld_acquire(flags + chain + jj) : kTileInc;
-                    const uint32_t incm = __ballot_sync(FULL, f == kTileInc);
-                    const uint32_t unp = __ballot_sync(FULL, f == 0u);
-                    const int first = incm ? __ffs((int)incm) - 1 : 32;
-                    const uint32_t before = first >= 32 ? FULL : ((1u << first) - 1u);
-                    if (unp & before) {   // a tile before the nearest inclusive one is not published yet
-                        if (++spins > p.spin_limit) { set_error(p.err, kErrTimeout); break; }
-                        __nanosleep(64);
-                        continue;
-                    }
-                    __syncwarp();
-                    if (lane < NV) {
-                        for (int u = 0; u < first; ++u) ex += __ldcg(agg_st + (chain + j - u) * NV + lane);
-                        if (first < 32 && j - first >= 0) ex += __ldcg(inc_st + (chain + j - first) * NV + lane);
-                    }
-                    if (first < 32) break;
-                    j -= 32;
-                }
-                if (lane < NV) __stcg(inc_st + me * NV + lane, ex + a);
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) st_release(flags + me, kTileInc);
-            }
-            const Wide pz_col = __shfl_sync(FULL, ex, lane >= KC ? lane - KC : lane);
-            if (lane < KC) ag_s[0][lane] = (Acc)ex;
-            else if (lane < NV) ag_s[1][lane - KC] = (Acc)(ex - bm * pz_col);
-        }
-#pragma unroll
-        for (int q = 0; q < QW; ++q) {
-            Acc pz = 0, pxz = 0;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const Acc a = wt[w][col0 + q], bb = wt[w][KC + col0 + q];
-                if (w < warp) { pz += a; pxz += bb; }
-            }
-            Lz[q] += pz;
-            Lxz[q] += pxz;
-        }
-        __syncthreads();   // (3) alpha, gamma in place
-
-        // D. evaluate and add into outg
-        {
-            Acc al[QW], gm[QW];
-#pragma unroll
-            for (int q = 0; q < QW; ++q) { al[q] = ag_s[0][col0 + q]; gm[q] = ag_s[1][col0 + q]; }
-            Acc* og = p.outg + (int64_t)g * p.n * KC + col0;
-#pragma unroll
-            for (int i = 0; i < SEG_LEN; ++i) {
-                Acc val[QW];
-#pragma unroll
-                for (int q = 0; q < QW; ++q) {
-                    val[q] = Acc(2) * fmac(dx[i], al[q] + Lz[q], -(gm[q] + Lxz[q]));
-                    const Acc z = (Acc)zv[i][q];
-                    Lz[q] += z;
-                    Lxz[q] = fmac(dx[i], z, Lxz[q]);
-                }
-                if (pe[i] >= 0) red_add<QW>(og + (int64_t)pe[i] * KC, val);
-            }
-        }
-        cur = nxt;
-        nxt = nx2;
-    }
-    cp_wait_all();   // no copy left in flight at exit
-}
-
 // ---------------------------------------------------------------- kernel
-template <dm_dtype DT, int KC>
+template <dm_dtype DT, int KC, bool ORDERED>
 __global__ void __launch_bounds__(kThreads)
 l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename Types<DT>::Wide> p) {
     using Cfg = QCfg<DT, KC>;
@@ -660,14 +346,14 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
             const Wide Pz = pr[tid], Pxz = pr[KC + tid];
             ag_s[slot][0][tid] = (Acc)Pz;
             ag_s[slot][1][tid] = (Acc)(Pxz - bm * Pz);
-            if (c == 0) {
+            if (ORDERED && c == 0) {
                 const int gc = g * KC + tid;
                 ag_w[slot][0][tid] = gc < k ? p.res[gc] : Wide(0);       // R^T Z
                 ag_w[slot][1][tid] = gc < k ? p.res[k + gc] : Wide(0);   // 1^T Z
             }
         }
-        // D. coordinate order: wait for every tile of coordinate c-1
-        {
+        // D. (ordered) coordinate order: wait for every tile of coordinate c-1
+        if (ORDERED) {
             if (c > 0 && tid == 0) wait_geq(p.done + (int64_t)g * d + c - 1, (uint32_t)T, p.err, p.spin_limit);
         }
         __syncthreads();
@@ -692,9 +378,24 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
             Acc al[QW], gm[QW];
 #pragma unroll
             for (int q = 0; q < QW; ++q) { al[q] = ag_s[slot][0][col0 + q]; gm[q] = ag_s[slot][1][col0 + q]; }
-            // Wide-type partial sums: the sum over the coordinates runs in
-            // the Wide type (FP64 for FP32 data), each term added once
-            {
+            if constexpr (!ORDERED) {
+                // every value added into outg with a vector reduction in L2
+                Acc* og = p.outg + (int64_t)g * p.n * KC + col0;
+#pragma unroll
+                for (int i = 0; i < SEG_LEN; ++i) {
+                    Acc val[QW];
+#pragma unroll
+                    for (int q = 0; q < QW; ++q) {
+                        val[q] = Acc(2) * fmac(dx[i], al[q] + Lz[q], -(gm[q] + Lxz[q]));
+                        const Acc z = (Acc)zv[i][q];
+                        Lz[q] += z;
+                        Lxz[q] = fmac(dx[i], z, Lxz[q]);
+                    }
+                    if (pe[i] >= 0) red_add<QW>(og + (int64_t)pe[i] * KC, val);
+                }
+            } else {
+                // Wide-type partial sums: the sum over the coordinates runs in
+                // the Wide type (FP64 for FP32 data), each term added once
                 const bool first = c == 0, final_ = c == d - 1;
                 const int kg = min(KC, k - g * KC);
                 Wide rz[QW], uz[QW];
@@ -743,10 +444,13 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
             }
         }
 
-        // F. this tile's values are in place before it is counted
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) red_release_add(p.done + (int64_t)g * d + c, 1u);
+        // F. (ordered) this tile's values are in place before it is counted;
+        // the L2-reduction mode needs no barrier here (double buffers)
+        if constexpr (ORDERED) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) red_release_add(p.done + (int64_t)g * d + c, 1u);
+        }
         claim = next;
         slot ^= 1;
 #pragma unroll
@@ -1081,7 +785,7 @@ int prologue_blocks(int64_t n, int num_sms) {
 
 struct ScratchLayout {
     int kc; int64_t G, T;
-    size_t counter, done, flags, memset_bytes, pre, inc, partial, res, zg, outg, total;
+    size_t counter, done, memset_bytes, pre, partial, res, zg, outg, total;
 };
 
 // Every region starts on a 256-byte boundary (the arena itself comes from
@@ -1098,11 +802,9 @@ ScratchLayout scratch_layout(dm_dtype t, int64_t n, int64_t d, int64_t k, int nu
     const size_t tiles = (size_t)(L.G * d * L.T);
     L.counter = 0;
     L.done = 16;
-    L.flags = align256(L.done + 4 * (size_t)(L.G * d));
-    L.memset_bytes = align256(L.flags + 4 * tiles);
-    L.pre = L.memset_bytes;                                   // tile sums / exclusive prefixes
-    L.inc = align256(L.pre + wide * tiles * 2 * L.kc);        // inclusive prefixes (one-pass kernel)
-    L.partial = align256(L.inc + wide * tiles * 2 * L.kc);
+    L.memset_bytes = align256(L.done + 4 * (size_t)(L.G * d));
+    L.pre = L.memset_bytes;                                   // tile sums, then exclusive prefixes
+    L.partial = align256(L.pre + wide * tiles * 2 * L.kc);
     L.res = align256(L.partial + wide * (size_t)prologue_blocks(n, num_sms) * 2 * k);
     L.zg = align256(L.res + wide * 2 * (size_t)k);
     L.outg = align256(L.zg + vsz * (size_t)(L.G * n * L.kc));
@@ -1169,8 +871,7 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
         return cudaSuccess;
     }
 
-    if (stage == 3) {   // tile aggregates + per-segment exclusive scan (ordered mode)
-        if (atomic) return cudaSuccess;   // the one-pass kernel finds its prefixes itself
+    if (stage == 3) {   // tile aggregates + per-segment exclusive scan
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, l1_aggregate_kernel<DT, KC>, kThreads, 0);
         if (e != cudaSuccess) return e;
@@ -1218,29 +919,11 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
     p.G = (int)L.G;
     p.spin_limit = a.spin_limit;
 
-    const int64_t total_tiles = (int64_t)p.G * p.d * p.T;
-    if (atomic) {
-        using OC = OCfg<DT, KC>;
-        auto okern = l1_onepass_kernel<DT, KC>;
-        if ((e = cudaFuncSetAttribute(okern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OC::smem)) !=
-            cudaSuccess)
-            return e;
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, okern, kThreads, OC::smem);
-        if (e != cudaSuccess) return e;
-        const int64_t blocks = std::max<int64_t>(
-            1, std::min<int64_t>(total_tiles, (int64_t)std::max(occ, 1) * a.num_sms));
-        okern<<<(unsigned)blocks, kThreads, OC::smem, st>>>(
-            p, reinterpret_cast<uint32_t*>(sc + L.flags), reinterpret_cast<Wide*>(sc + L.pre),
-            reinterpret_cast<Wide*>(sc + L.inc));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        ++*launches;
-        return cudaSuccess;
-    }
-    auto kern = l1_query_kernel<DT, KC>;
+    auto kern = atomic ? l1_query_kernel<DT, KC, false> : l1_query_kernel<DT, KC, true>;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0);
     if (e != cudaSuccess) return e;
+    const int64_t total_tiles = (int64_t)p.G * p.d * p.T;
     const int64_t blocks = std::max<int64_t>(
         1, std::min<int64_t>(total_tiles, (int64_t)std::max(occ, 1) * a.num_sms));
     kern<<<(unsigned)blocks, kThreads, 0, st>>>(p);
