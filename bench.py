@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--no-krylov", action="store_true", help="skip the block Krylov measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the variant measurements")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the error study of the two accumulation modes")
     ap.add_argument("--grad-n", type=int, default=1 << 21)
     ap.add_argument("--grad-d", type=int, default=64)
     ap.add_argument("--engine", choices=["auto", "cuda", "tensor"], default="auto",
@@ -564,6 +566,39 @@ def measure_variants(dm, ctx, stream, dev, X, Z, Xd, Zd, reps=5):
     return res
 
 
+def measure_accumulation_error(dm, dev, n=1 << 18):
+    """Relative error of the l1 product against the FP64 oracle (whole block)
+    in both accumulation modes of the sum over the coordinates: vector
+    reductions of FP32 values in L2 (default) and the ordered FP64 partial
+    output (dm_set_deterministic), at d in {32, 64} and k in {16, 40}, on the
+    step's mixture and on the same mixture shifted by 1000 per coordinate."""
+    import torch
+    import oracle
+    from oracle import parallel
+    from paper_2210_15114_gb300 import inputs
+    ctxs = {"l2_reductions_fp32": dm.dm_create(dev.index or 0), "ordered_fp64": dm.dm_create(dev.index or 0)}
+    dm.dm_set_deterministic(ctxs["ordered_fp64"], True)
+    res = {"n": n, "metric": "||out - AZ||_F / ||AZ||_F, whole block, FP64 oracle on the same FP32 values"}
+    for data in ("mixture", "mixture_offset_1000"):
+        for d in (32, 64):
+            for k in (16, 40):
+                if data == "mixture":
+                    X, Z = inputs.workload_mixture_f32(n=n, d=d, k=k)
+                else:
+                    X, Z = inputs.workload_offset_mixture(n, d, k)
+                want = parallel.l1_sort(X, Z)
+                Xd, Zd = torch.from_numpy(X).to(dev), torch.from_numpy(Z).to(dev)
+                entry = {}
+                for mode, ctx in ctxs.items():
+                    plan = dm.dm_prepare(ctx, "l1", Xd)
+                    out = dm.dm_matmat(plan, Zd)
+                    dm.dm_sync(ctx)
+                    entry[mode] = oracle.relative_error(out.cpu().numpy(), want)
+                    del plan
+                res[f"{data} d={d} k={k}"] = entry
+    return res
+
+
 # ------------------------------------------------------------- reference arm
 def run_reference(a):
     rank, world, _ = dist_env()
@@ -727,6 +762,11 @@ def main():
     if not a.no_variants:
         variants = measure_variants(dm, ctx, stream, dev, X, Z, Xd, Zd)
 
+    # ---- error of the sum over the coordinates in both accumulation modes
+    precision = None
+    if not a.no_precision:
+        precision = measure_accumulation_error(dm, dev)
+
     # ---- brute force (the plain method) and accuracy
     brute = None
     if not a.no_brute:
@@ -789,6 +829,7 @@ def main():
             "wall_s_timed_region": t_wall,
             "parts_ms": parts, "kernels": kernels, "roofline": roofline, "l1_query_all_kernels": l1_query_all,
             "bruteforce": brute, "rel_err_sampled_rows": err, "gradient": grad, "krylov": krylov, "batch": batch, "variants": variants,
+            "l1_accumulation_error": precision,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     if world > 1:

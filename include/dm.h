@@ -93,16 +93,24 @@ dm_status dm_set_stream(dm_ctx* ctx, void* cuda_stream);
  * data are deterministic in both settings (integer sums are exact). */
 dm_status dm_set_deterministic(dm_ctx* ctx, int on);
 
-/* Units that run the squared-l2 contraction [X - mu, 1, s]^T Z (Appendix A,
- * the reduce step of DM_L2SQ products, of their gradients and of even-p
- * DM_LPP products).  DM_ENGINE_TENSOR_CORES: FP32 data with d + 2 <= 128 and
- * column blocks the kernel's shared memory holds run on the tensor cores
- * (tcgen05, TF32 operands split as hi + lo, three products per term, FP32
- * accumulation drained every 64 points, FP64 across runs); other shapes and
- * types keep the CUDA-core kernel.  DM_ENGINE_CUDA_CORES: always the
- * CUDA-core kernel.  DM_ENGINE_AUTO (the default): the tensor cores only for
- * the shapes where they measured faster.  Results agree with the FP64 oracle
- * within the FP32 tolerance either way; the bits differ between engines. */
+/* Units that run the two contractions of the squared-l2 product (Appendix
+ * A): the reduce [X - mu, 1, s]^T Z (also of squared-l2 gradients and of
+ * even-p DM_LPP products) and the apply -2 (X - mu) W of
+ * out = s u^T + 1 v^T - 2 (X - mu) W.  Both tensor-core kernels use tcgen05
+ * with TF32 operands split as hi + lo (three products per term, FP32
+ * accumulation).
+ *   DM_ENGINE_TENSOR_CORES: the reduce for FP32 data with d + 2 <= 128 and
+ *     column blocks its shared memory holds (accumulation drained every 64
+ *     points, FP64 across runs); the apply for FP32 data with d a multiple
+ *     of 4 up to 32, k <= 32 and contiguous rows of X; other shapes and types
+ *     keep the CUDA-core kernels.
+ *   DM_ENGINE_CUDA_CORES: always the CUDA-core kernels.
+ *   DM_ENGINE_AUTO (the default): the tensor cores where they measured at
+ *     least as fast: the apply when k >= 16 and d k >= 384; the reduce never
+ *     (its output has d + 2 rows, while a tcgen05 tile has 128, so most of
+ *     every MMA is padding).
+ * Results agree with the FP64 oracle within the FP32 tolerance either way;
+ * the bits differ between engines. */
 typedef enum { DM_ENGINE_AUTO = 0, DM_ENGINE_CUDA_CORES = 1, DM_ENGINE_TENSOR_CORES = 2 } dm_engine;
 dm_status dm_set_engine(dm_ctx* ctx, dm_engine engine);
 

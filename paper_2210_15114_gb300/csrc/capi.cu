@@ -635,6 +635,9 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
         ap.out = static_cast<unsigned char*>(out) + (size_t)j0 * out_size(t);
         ap.ldo = ldo;
         ap.num_sms = ctx->num_sms;
+        ap.engine = ctx->engine;
+        ap.err = ctx->err;
+        ap.spin_limit = ctx->spin_limit;
         ProfScope ps(e, "l2_apply");
         DM_TRY_CUDA(l2apply_launch(ap, e.stream, &ctx->launches));
     }

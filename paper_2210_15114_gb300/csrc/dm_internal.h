@@ -143,6 +143,9 @@ struct L2ApplyArgs {
     int64_t k;
     void* out; int64_t ldo;
     int num_sms;
+    int engine = DM_ENGINE_AUTO;         // dm_engine: the contraction's units
+    uint32_t* err = nullptr;             // device error word (bounded waits)
+    uint32_t spin_limit = kSpinLimit;
 };
 cudaError_t l2apply_launch(const L2ApplyArgs& a, cudaStream_t s, int64_t* launches);
 

@@ -321,12 +321,21 @@ reduce_kernel(const XT* __restrict__ X, int64_t n, int d, int64_t ldx,
 
 // One warp per result entry; lanes stride over the partials and the warp
 // tree-reduces them (a fixed order, so the result is reproducible).
+// With a device error word (the tensor-core reduce): partials of a launch
+// whose bounded wait ran out may be stale, so once the word holds
+// DM_ERR_TIMEOUT the result is poisoned (NaN) instead of summed.
 template <class Wide>
 __global__ void reduce_finalize_kernel(const Wide* __restrict__ partial, int blocks, int total,
-                                       Wide* __restrict__ res) {
+                                       Wide* __restrict__ res, const uint32_t* err) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= total) return;
+    if constexpr (sizeof(Wide) == 8 && Wide(0.5) != Wide(0)) {   // floating point only
+        if (err && ld_acquire(err) == kErrTimeout) {
+            if (lane == 0) res[w] = __longlong_as_double(0x7ff8000000000000ll);
+            return;
+        }
+    }
     Wide acc = 0;
     for (int b = lane; b < blocks; b += 32) acc += partial[(int64_t)b * total + w];
 #pragma unroll
@@ -636,7 +645,13 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ldx,
             __syncthreads();
         }
     }
-    if (failed && err) set_error(err, kErrTimeout);
+    if (failed) {
+        if (err) set_error(err, kErrTimeout);
+        // committed MMAs may still target TMEM and read the operand sets: a
+        // last bounded wait for each before the memory is released
+        for (int b = 0; b < 2; ++b)
+            if ((pending >> b) & 1u) tc_wait(smem_u32(mbar + b), (parity >> b) & 1u);
+    }
     cp_wait<0>();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -716,6 +731,281 @@ __global__ void mean_finalize_kernel(const typename Types<DT>::Wide* __restrict_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) mu[c] = (V)(t / (Wide)n);
+}
+
+// ------------------------------------------------- l2apply on tensor cores
+// FP32 data, d <= 32 coordinates (a multiple of 4, rows contiguous), k <= 32
+// query columns: the apply's contraction -2 (X - mu) W on tcgen05.mma
+// (kind::tf32), one MMA tile of M = 128 points, N = k rounded up to 16,
+// K = d rounded up to 8.  This is the product's natural orientation: a
+// point's coordinates are its K dimension and lie contiguous in X, so the
+// operand is X's own row-major tile (K-major), shifted and split on the way.
+//   A: 128 x Kp, rows of [x_i - mu] split as v = hi + lo (split_tf32: both
+//      parts exact TF32 values, |v - hi - lo| < 2^-20 |v|);
+//   B: Np x Kp, the columns of W (W^T), split the same way once per CTA;
+//   D (TMEM, lane = point, column = query column) = A_hi B_hi + A_hi B_lo
+//      + A_lo B_hi: three MMAs per K step of 8 (FP32 accumulation over at
+//      most 12 products).
+// Operands sit in the canonical K-major layout without swizzle (as in
+// reduce_tc: core matrices of 8 rows x 16 bytes, LBO = 128 bytes along K,
+// SBO = Kp / 4 * 128 bytes between 8-row groups).
+// One CTA (256 threads; threads t and t + 128 share point t of a tile, TMEM
+// lane t, each with half of its coordinates and of its query columns) is
+// persistent over tiles j = blockIdx.x + i gridDim.x.  The raw tiles
+// (128 rows x d floats, contiguous) arrive by bulk copies (cp.async.bulk,
+// completion counted on an mbarrier) kApStages tiles ahead, so that enough
+// bytes are in flight to cover the memory latency; per tile each thread
+// shifts and splits its row into the operand tile and forms
+// s_i = ||x_i - mu||^2, one thread issues the MMAs and commits them to an
+// mbarrier, and every thread reads its row of the accumulator (tcgen05.ld)
+// and writes out_i = s_i u + v - 2 D_i.
+// Every wait is bounded: on expiry the CTA latches DM_ERR_TIMEOUT, waits
+// (bounded) for its own copies and MMAs in flight, frees its TMEM and exits.
+constexpr int kApM = 128;
+constexpr int kApT = 256;     // threads: two per point (row) of a tile
+constexpr int kApStages = 2;
+
+// v = hi + lo with hi = v with its 13 low mantissa bits cleared and lo the
+// same of v - hi (both exact TF32 values, whatever conversion the tensor
+// core applies to its inputs): |v - hi - lo| < 2^-20 |v|.
+__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
+    hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+    lo = __uint_as_float(__float_as_uint(v - hi) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ uint64_t tc_desc_sbo(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((128u >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+
+// Bounded wait on an mbarrier phase with an explicit round limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+// One bulk copy global -> shared of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned), completion counted on mbar (the caller's arrive carries
+// the transaction count).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+size_t apply_tc_smem(int d, int k) {
+    const int Kp = (d + 7) / 8 * 8, Np = (k + 15) / 16 * 16;
+    return kApStages * (size_t)kApM * d * 4    // raw tiles
+           + 2 * (size_t)kApM * Kp * 4         // operand tile (hi, lo)
+           + 2 * (size_t)Np * Kp * 4           // B (hi, lo)
+           + 4 * (2 * (size_t)Np + Kp) + 128   // mu, u, v, mbarriers, TMEM slot
+           + 2 * (size_t)kApM * 4;             // partial row norms
+}
+
+__global__ void __launch_bounds__(kApT)
+l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ mu,
+                  const double* __restrict__ res, int k, float* __restrict__ out, int64_t ldo,
+                  int Kp, int Np, uint32_t tmem_cols, int vst, uint32_t* err, uint32_t spin_limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sbo = (uint32_t)(Kp / 4) * 128u;
+    const size_t raw_bytes = (size_t)kApM * d * 4;
+    const size_t a_bytes = (size_t)kApM * Kp * 4, b_bytes = (size_t)Np * Kp * 4;
+    unsigned char* raw = smem_raw;                                     // [kApStages][128][d]
+    unsigned char* ahi = raw + kApStages * raw_bytes;                  // 128 x Kp
+    unsigned char* alo = ahi + a_bytes;
+    unsigned char* bhi = alo + a_bytes;
+    unsigned char* blo = bhi + b_bytes;
+    float* mu_s = reinterpret_cast<float*>(blo + b_bytes);             // [Kp], 16-byte aligned
+    float* u_s = mu_s + Kp;                                            // [Np]
+    float* v_s = u_s + Np;                                             // [Np]
+    float* s_part = v_s + Np;                                          // [2][128]
+    const uintptr_t tail = (reinterpret_cast<uintptr_t>(s_part + 2 * kApM) + 7) & ~uintptr_t(7);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);                // raw_full[kApStages], mma_done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kApStages + 1);
+    const int row = tid & (kApM - 1), half = tid >> 7;
+
+    // B = W^T split, u, v, mu (zero padded)
+    for (int i = tid; i < Np * Kp; i += kApT) {
+        const int nn = i / Kp, kk = i % Kp;
+        const float w = (nn < k && kk < d) ? (float)res[(int64_t)kk * k + nn] : 0.f;
+        float h, l;
+        split_tf32(w, h, l);
+        const size_t off = (size_t)(nn >> 3) * sbo + (size_t)(kk >> 2) * 128 + (size_t)(nn & 7) * 16 +
+                           (size_t)(kk & 3) * 4;
+        *reinterpret_cast<float*>(bhi + off) = h;
+        *reinterpret_cast<float*>(blo + off) = l;
+    }
+    for (int j = tid; j < Np; j += kApT) {
+        u_s[j] = j < k ? (float)res[(int64_t)d * k + j] : 0.f;
+        v_s[j] = j < k ? (float)res[(int64_t)d * k + k + j] : 0.f;
+    }
+    for (int c = tid; c < Kp; c += kApT) mu_s[c] = c < d ? mu[c] : 0.f;
+    if (tid == 0) {
+        for (int b = 0; b <= kApStages; ++b) mbar_init(smem_u32(mbar + b), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Np >> 3) << 17) |
+                           ((uint32_t)(kApM >> 4) << 24);
+    const uint32_t a_h = smem_u32(ahi), a_l = smem_u32(alo), b_h = smem_u32(bhi), b_l = smem_u32(blo);
+    const uint32_t mma_bar = smem_u32(mbar + kApStages);
+
+    const int64_t tiles = (n + kApM - 1) / kApM;
+    auto tile_rows = [&](int64_t tile) { return (int)min64(kApM, n - tile * kApM); };
+    const int64_t my_tiles = blockIdx.x < tiles ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    auto issue = [&](int64_t i) {   // raw tile i of this CTA into stage i % kApStages
+        const int64_t tile = blockIdx.x + i * gridDim.x;
+        const int st = (int)(i % kApStages);
+        bulk_load(smem_u32(raw + (size_t)st * raw_bytes), X + tile * kApM * d,
+                  (uint32_t)(tile_rows(tile) * d * 4), smem_u32(mbar + st));
+    };
+    if (tid == 0)
+        for (int64_t i = 0; i < kApStages && i < my_tiles; ++i) issue(i);
+    int64_t issued = std::min<int64_t>(kApStages, my_tiles);   // raw tiles requested so far
+    uint32_t raw_phase = 0u, mma_phase = 0u;   // parity of the next completion (bit per stage)
+    bool failed = false, mma_open = false;
+    int64_t raw_open = 0;                       // first raw tile not yet waited for
+
+    for (int64_t i = 0; i < my_tiles; ++i) {
+        const int st = (int)(i % kApStages);
+        const int64_t tile = blockIdx.x + i * gridDim.x;
+        const int rows = tile_rows(tile);
+        // a) the raw tile is in place
+        const bool ok = mbar_wait(smem_u32(mbar + st), (raw_phase >> st) & 1u, spin_limit);
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        raw_phase ^= 1u << st;
+        raw_open = i + 1;
+        // b) shift, split and the partial s of this thread's half of its row
+        // (16-byte pieces read in rotated order: the rows of a warp fall in
+        // distinct banks)
+        {
+            const float* xr = reinterpret_cast<const float*>(raw + (size_t)st * raw_bytes) + (size_t)row * d;
+            const size_t rbase = (size_t)(row >> 3) * sbo + (size_t)(row & 7) * 16;
+            const int nq2 = Kp / 8, dq = d / 4;            // 16-byte pieces per half, with data
+            float sp = 0.f;
+            int r = row % nq2;
+            for (int qq = 0; qq < nq2; ++qq, r = r + 1 == nq2 ? 0 : r + 1) {
+                const int q = half * nq2 + r;
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+                if (row < rows && q < dq) {
+                    const float4 x4 = *reinterpret_cast<const float4*>(xr + 4 * q);
+                    const float4 m4 = *reinterpret_cast<const float4*>(mu_s + 4 * q);
+                    v[0] = x4.x - m4.x;
+                    v[1] = x4.y - m4.y;
+                    v[2] = x4.z - m4.z;
+                    v[3] = x4.w - m4.w;
+                }
+                float h[4], l[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    sp = fmaf(v[e], v[e], sp);
+                    split_tf32(v[e], h[e], l[e]);
+                }
+                const size_t off = rbase + (size_t)q * 128;
+                *reinterpret_cast<float4*>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+            s_part[half * kApM + row] = sp;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();   // operand tile written, raw stage st read by every thread
+        if (tid == 0) {
+            // c) the raw tile kApStages ahead into the stage just read
+            if (issued < my_tiles) issue(issued);
+            // d) the MMAs of this tile
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int ks = 0; ks < Kp / 8; ++ks) {
+                const uint32_t o = (uint32_t)ks * 256u;
+                const uint64_t dah = tc_desc_sbo(a_h + o, sbo), dal = tc_desc_sbo(a_l + o, sbo);
+                const uint64_t dbh = tc_desc_sbo(b_h + o, sbo), dbl = tc_desc_sbo(b_l + o, sbo);
+                tc_mma(tmem, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                tc_mma(tmem, dah, dbl, idesc, 1u);
+                tc_mma(tmem, dal, dbh, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(mma_bar) : "memory");
+        }
+        if (issued < my_tiles) ++issued;
+        // e) the accumulator -> out
+        const bool mok = mbar_wait(mma_bar, mma_phase, spin_limit);
+        if (__syncthreads_or(!mok)) { failed = true; mma_open = true; break; }
+        mma_phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows), the columns of
+        // half w / 4 of the padded width
+        const float s_row = s_part[row] + s_part[kApM + row];
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const int jh = Np / 2;
+        for (int j0 = half * jh; j0 < (half + 1) * jh; j0 += 8) {
+            float dv[8];
+            tc_ld8(lane_base + (uint32_t)j0, dv);
+            if (row < rows) {
+                float o[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) o[q] = fmaf(s_row, u_s[j0 + q], v_s[j0 + q]) - 2.f * dv[q];
+                float* dst = out + (tile * kApM + row) * ldo + j0;
+                if (vst && j0 + 8 <= k) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4*>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (j0 + q < k) dst[q] = o[q];
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    if (failed) {
+        if (err) set_error(err, kErrTimeout);
+        // no copy or MMA of this CTA may still target its shared memory or
+        // TMEM when they are released: raw tiles raw_open .. issued - 1 are
+        // still on their way (each in its own stage), and maybe the MMAs
+        for (int64_t j = raw_open; j < issued; ++j) {
+            const int st = (int)(j % kApStages);
+            mbar_wait(smem_u32(mbar + st), (raw_phase >> st) & 1u, spin_limit);
+        }
+        if (mma_open) mbar_wait(mma_bar, mma_phase, spin_limit);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
+    }
 }
 
 // ----------------------------------------------------------------- l2apply
@@ -898,7 +1188,7 @@ cudaError_t reduce_launch_t(const ReduceArgs& a, cudaStream_t st, int64_t* launc
     const int warps_per_block = 8;
     reduce_finalize_kernel<Wide><<<(total + warps_per_block - 1) / warps_per_block, 32 * warps_per_block,
                                    0, st>>>(static_cast<const Wide*>(a.partial), blocks, total,
-                                            static_cast<Wide*>(a.res));
+                                            static_cast<Wide*>(a.res), nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 2;
     return cudaSuccess;
@@ -1086,7 +1376,7 @@ cudaError_t reduce_tc_launch(const ReduceArgs& a, cudaStream_t st, int64_t* laun
     const int warps_per_block = 8;
     reduce_finalize_kernel<double><<<(total + warps_per_block - 1) / warps_per_block, 32 * warps_per_block,
                                      0, st>>>(static_cast<const double*>(a.partial), (int)nseg, total,
-                                              static_cast<double*>(a.res));
+                                              static_cast<double*>(a.res), a.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 2;
     return cudaSuccess;
@@ -1228,8 +1518,53 @@ cudaError_t l2prep_launch(const L2PrepArgs& a, cudaStream_t s, int64_t* launches
     }
 }
 
+namespace {
+// DM_ENGINE_AUTO picks the tensor-core apply where it measured at least as
+// fast as the CUDA-core kernel (n = 2^20: d k >= 384 with k >= 16, e.g.
+// d = 32: 0.062 / 0.062 ms at k = 16, 0.089 / 0.113 ms at k = 32); for
+// narrower blocks its fixed cost per tile (12 MMAs, a TMEM round trip) loses.
+bool apply_tc_auto(const L2ApplyArgs& a) { return a.k >= 16 && a.d * a.k >= 384; }
+}  // namespace
+
+// The apply on the tensor cores: FP32, d a multiple of 4 up to 32, k up to
+// 32, rows of X contiguous (ldx = d) and 16-byte aligned.
+bool apply_tc_shape_ok(const L2ApplyArgs& a) {
+    return a.dtype == DM_F32 && a.d % 4 == 0 && a.d >= 4 && a.d <= 32 && a.k >= 1 && a.k <= 32 &&
+           a.ldx == a.d && reinterpret_cast<uintptr_t>(a.X) % 16 == 0;
+}
+
+cudaError_t l2apply_tc_launch(const L2ApplyArgs& a, cudaStream_t st, int64_t* launches, int num_sms) {
+    const int d = (int)a.d, k = (int)a.k;
+    const int Kp = (d + 7) / 8 * 8, Np = (k + 15) / 16 * 16;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(2 * Np)) cols <<= 1;
+    const size_t smem = apply_tc_smem(d, k);
+    auto kern = l2apply_tc_kernel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    // CTAs per SM: shared memory (227 KB usable, 1 KB reserved per CTA) and
+    // TMEM (every resident CTA holds `cols` of the SM's 512 columns) bound it
+    int occ = (int)((227 * 1024) / (smem + 1024));
+    occ = std::max(1, std::min(occ, std::min(2048 / kApT, (int)(512 / cols))));
+    const int64_t tiles = (a.n + kApM - 1) / kApM;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)occ * num_sms));
+    const bool vst = a.k % 4 == 0 && a.ldo % 4 == 0 && reinterpret_cast<uintptr_t>(a.out) % 16 == 0;
+    kern<<<(unsigned)blocks, kApT, smem, st>>>(
+        static_cast<const float*>(a.X), a.n, d, static_cast<const float*>(a.mu),
+        static_cast<const double*>(a.res), k, static_cast<float*>(a.out), a.ldo, Kp, Np, cols,
+        vst ? 1 : 0, a.err, a.spin_limit);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *launches += 1;
+    return cudaSuccess;
+}
+
 cudaError_t l2apply_launch(const L2ApplyArgs& a, cudaStream_t s, int64_t* launches) {
     const int sms = sm_count(a.num_sms);
+    if (a.engine != DM_ENGINE_CUDA_CORES && apply_tc_shape_ok(a) &&
+        (a.engine == DM_ENGINE_TENSOR_CORES || apply_tc_auto(a)))
+        return l2apply_tc_launch(a, s, launches, sms);
     switch (a.dtype) {
         case DM_F32: return l2apply_launch_t<DM_F32>(a, s, launches, sms);
         case DM_F64: return l2apply_launch_t<DM_F64>(a, s, launches, sms);

@@ -166,3 +166,13 @@ def simplex_points(n: int, d: int, seed: int = SEED_X, dtype=np.float32) -> np.n
     """Discrete distributions over d outcomes (Dirichlet(1, ..., 1) rows),
     the inputs of the total-variation product."""
     return np.random.default_rng(seed).dirichlet(np.ones(d), size=n).astype(dtype)
+
+
+def workload_offset_mixture(n: int, d: int, k: int, offset: float = 1000.0):
+    """The 16-cluster mixture shifted by `offset` in every coordinate, FP32
+    (the shift costs the FP32 coordinates about log2(offset / 10) bits of the
+    spread), with an N(0, 1) query block of k columns (mixed signs)."""
+    X = (gaussian_mixture(n, d, 16, SEED_X, 10.0, 1.0, dtype=np.float64) + offset).astype(np.float32)
+    Z = gaussian_queries(n, k, SEED_Z, dtype=np.float32)
+    return X, Z
+

@@ -443,6 +443,31 @@ def test_l2sq_tensor_engine(dm, ctx_tensor, n, d, k):
     assert oracle.relative_error(out[rows], oracle.l2sq_rows(X, Z, rows)) <= 1e-5
 
 
+@pytest.mark.parametrize("n,d,k", [(1, 4, 1), (127, 8, 5), (128, 12, 16), (129, 20, 31), (4097, 28, 32),
+                                   (70001, 32, 16), (300, 32, 17), (5000, 4, 3)])
+def test_l2sq_tensor_apply_shapes(dm, ctx_tensor, n, d, k):
+    # the apply on tcgen05 (d a multiple of 4 up to 32, k up to 32): ragged
+    # tiles of 128 points, k padded to 16 / 32, one-point tiles; the whole
+    # block against the p = 2 identity, on points shifted far from the origin
+    rng = np.random.default_rng(7 * n + d + k)
+    X = (rng.normal(0, 3, size=(n, d)) + 50.0).astype(np.float32)
+    Z = rng.normal(size=(n, k)).astype(np.float32)
+    out = gpu_product(dm, ctx_tensor, "l2sq", X, Z)
+    want = oracle.l2sq_identity(X, Z) if n > 1 else oracle.l2sq_rows(X, Z)
+    assert oracle.relative_error(out, want) <= 1e-5
+
+
+def test_l2sq_tensor_apply_strided_points_fall_back(dm, ctx_tensor):
+    # rows of X not contiguous (ldx > d): the CUDA-core apply takes over
+    rng = np.random.default_rng(3)
+    Xw = rng.normal(size=(2000, 12)).astype(np.float32)
+    Z = rng.normal(size=(2000, 6)).astype(np.float32)
+    plan = dm.dm_prepare(ctx_tensor, "l2sq", dev(Xw)[:, :8])
+    out = dm.dm_matmat(plan, dev(Z)).cpu().numpy()
+    dm.dm_sync(ctx_tensor)
+    assert oracle.relative_error(out, oracle.l2sq_identity(Xw[:, :8], Z)) <= 1e-5
+
+
 def test_l2sq_tensor_engine_full_size(dm, ctx_tensor, full_fp32, full_fp32_ref):
     X, Z = full_fp32
     want, scale = full_fp32_ref["l2sq"]
