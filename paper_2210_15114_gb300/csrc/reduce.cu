@@ -824,10 +824,11 @@ size_t apply_tc_smem(int d, int k) {
            + 2 * (size_t)kApM * 4;             // partial row norms
 }
 
+template <int Kp>
 __global__ void __launch_bounds__(kApT)
 l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ mu,
                   const double* __restrict__ res, int k, float* __restrict__ out, int64_t ldo,
-                  int Kp, int Np, uint32_t tmem_cols, int vst, uint32_t* err, uint32_t spin_limit) {
+                  int Np, uint32_t tmem_cols, int vst, uint32_t* err, uint32_t spin_limit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbo = (uint32_t)(Kp / 4) * 128u;
@@ -907,19 +908,21 @@ l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __
         if (__syncthreads_or(!ok)) { failed = true; break; }
         raw_phase ^= 1u << st;
         raw_open = i + 1;
-        // b) shift, split and the partial s of this thread's half of its row
-        // (16-byte pieces read in rotated order: the rows of a warp fall in
-        // distinct banks)
+        // b) shift, split and the partial s of one half of a row: threads 2r
+        // and 2r + 1 share row r, so a warp's 16-byte reads of the raw rows and
+        // writes of the operand rows each cover eight distinct bank groups
         {
-            const float* xr = reinterpret_cast<const float*>(raw + (size_t)st * raw_bytes) + (size_t)row * d;
-            const size_t rbase = (size_t)(row >> 3) * sbo + (size_t)(row & 7) * 16;
-            const int nq2 = Kp / 8, dq = d / 4;            // 16-byte pieces per half, with data
+            const int srow = tid >> 1, shalf = tid & 1;
+            const float* xr = reinterpret_cast<const float*>(raw + (size_t)st * raw_bytes) + (size_t)srow * d;
+            const size_t rbase = (size_t)(srow >> 3) * sbo + (size_t)(srow & 7) * 16;
+            constexpr int nq2 = Kp / 8;                   // 16-byte pieces per half
+            const int dq = d / 4;                         // pieces with data
             float sp = 0.f;
-            int r = row % nq2;
-            for (int qq = 0; qq < nq2; ++qq, r = r + 1 == nq2 ? 0 : r + 1) {
-                const int q = half * nq2 + r;
+#pragma unroll
+            for (int qq = 0; qq < nq2; ++qq) {
+                const int q = shalf * nq2 + (srow + qq) % nq2;
                 float v[4] = {0.f, 0.f, 0.f, 0.f};
-                if (row < rows && q < dq) {
+                if (srow < rows && q < dq) {
                     const float4 x4 = *reinterpret_cast<const float4*>(xr + 4 * q);
                     const float4 m4 = *reinterpret_cast<const float4*>(mu_s + 4 * q);
                     v[0] = x4.x - m4.x;
@@ -937,7 +940,7 @@ l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __
                 *reinterpret_cast<float4*>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
                 *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
             }
-            s_part[half * kApM + row] = sp;
+            s_part[shalf * kApM + srow] = sp;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -947,6 +950,7 @@ l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __
             if (issued < my_tiles) issue(issued);
             // d) the MMAs of this tile
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
             for (int ks = 0; ks < Kp / 8; ++ks) {
                 const uint32_t o = (uint32_t)ks * 256u;
                 const uint64_t dah = tc_desc_sbo(a_h + o, sbo), dal = tc_desc_sbo(a_l + o, sbo);
@@ -1520,10 +1524,12 @@ cudaError_t l2prep_launch(const L2PrepArgs& a, cudaStream_t s, int64_t* launches
 
 namespace {
 // DM_ENGINE_AUTO picks the tensor-core apply where it measured at least as
-// fast as the CUDA-core kernel (n = 2^20: d k >= 384 with k >= 16, e.g.
-// d = 32: 0.062 / 0.062 ms at k = 16, 0.089 / 0.113 ms at k = 32); for
-// narrower blocks its fixed cost per tile (12 MMAs, a TMEM round trip) loses.
-bool apply_tc_auto(const L2ApplyArgs& a) { return a.k >= 16 && a.d * a.k >= 384; }
+// fast as the CUDA-core kernel (n = 2^20, tensor / CUDA cores: d = 32,
+// k = 16: 0.060 / 0.061 ms; d = 32, k = 32: 0.090 / 0.113 ms; d = 16,
+// k = 32: 0.076 / 0.076 ms).  Its time has a floor of about 0.055 ms at
+// d = 32 whatever k (reading, shifting and splitting X), so narrower blocks
+// stay on the CUDA cores (d = 24, k = 16: 0.055 / 0.053 ms).
+bool apply_tc_auto(const L2ApplyArgs& a) { return a.k >= 16 && a.d * a.k >= 512; }
 }  // namespace
 
 // The apply on the tensor cores: FP32, d a multiple of 4 up to 32, k up to
@@ -1539,7 +1545,8 @@ cudaError_t l2apply_tc_launch(const L2ApplyArgs& a, cudaStream_t st, int64_t* la
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * Np)) cols <<= 1;
     const size_t smem = apply_tc_smem(d, k);
-    auto kern = l2apply_tc_kernel;
+    auto kern = Kp == 8 ? l2apply_tc_kernel<8> : Kp == 16 ? l2apply_tc_kernel<16>
+              : Kp == 24 ? l2apply_tc_kernel<24> : l2apply_tc_kernel<32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1553,7 +1560,7 @@ cudaError_t l2apply_tc_launch(const L2ApplyArgs& a, cudaStream_t st, int64_t* la
     const bool vst = a.k % 4 == 0 && a.ldo % 4 == 0 && reinterpret_cast<uintptr_t>(a.out) % 16 == 0;
     kern<<<(unsigned)blocks, kApT, smem, st>>>(
         static_cast<const float*>(a.X), a.n, d, static_cast<const float*>(a.mu),
-        static_cast<const double*>(a.res), k, static_cast<float*>(a.out), a.ldo, Kp, Np, cols,
+        static_cast<const double*>(a.res), k, static_cast<float*>(a.out), a.ldo, Np, cols,
         vst ? 1 : 0, a.err, a.spin_limit);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
