@@ -440,11 +440,14 @@ def measure_krylov(dm, ctx, stream, dev, n=1 << 22, d=16, k=40, q=8, rank=32, re
         prof = dm.dm_profile_read(ctx)
         dm.dm_profile_enable(ctx, False)
         prep = ("sort_keygen_hist", "sort_onesweep", "l1_rowsum") if metric == "l1" else ("l2_prepare",)
-        prod_ms = sum(t for g, (l, t) in prof.items() if g not in prep) / reps
+        dense = ("dense_tn", "dense_nn")
+        prod_ms = sum(t for g, (l, t) in prof.items() if g not in prep and g not in dense) / reps
         prep_ms = sum(t for g, (l, t) in prof.items() if g in prep) / reps
+        dense_ms = {g: prof[g][1] / reps for g in dense if g in prof}
         ms = statistics.mean(times)
         entry = {"ms": ms, "prepare_ms": prep_ms, "products_ms": prod_ms,
                  "dense_linear_algebra_ms": ms - prod_ms - prep_ms,
+                 "dense_kernels_ms": dense_ms,
                  "top_singular_values": [abs(float(t)) for t in theta[:8].cpu()]}
         if metric == "l2sq":
             Xc = X.astype(np.float64)

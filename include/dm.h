@@ -246,6 +246,29 @@ void dm_batch_destroy(dm_batch* batch);
  * error latched since the last dm_sync. */
 dm_status dm_sync(dm_ctx* ctx);
 
+/* ------------------------------------------------- dense tall-skinny products
+ * The dense steps of the block Krylov iteration that the paper draws from
+ * fast products (Appendix C, Theorems "musco" and "singular_values_system"):
+ * projections of a block against the earlier ones, Gram matrices of Cholesky
+ * QR, the Rayleigh-Ritz matrix and the Ritz vectors.  FP32 device matrices,
+ * row-major with a leading dimension (rows contiguous), n rows in the
+ * millions, the other dimensions small; FP32 arithmetic.  Asynchronous on the
+ * context's stream.
+ *
+ * dm_dense_tn: C (m x k, ldc) = alpha A^T B with A n x m (lda), B n x k (ldb).
+ *   The rows are split into chunks whose FP32 partial products are added in
+ *   FP64 in a fixed order (reproducible); the partials live in the context's
+ *   scratch arena.  C must not overlap A or B. */
+dm_status dm_dense_tn(dm_ctx* ctx, const float* A, int64_t n, int64_t m, int64_t lda, const float* B,
+                      int64_t k, int64_t ldb, float* C, int64_t ldc, float alpha);
+
+/* dm_dense_nn: C (n x k, ldc) = beta C + alpha A T with A n x m (lda) and T
+ * m x k (ldt), 1 <= k <= 64 (DM_ERR_UNSUPPORTED beyond); beta = 0 does not
+ * read C.  C may be the same block as the one read through beta but must not
+ * overlap A or T. */
+dm_status dm_dense_nn(dm_ctx* ctx, const float* A, int64_t n, int64_t m, int64_t lda, const float* T,
+                      int64_t k, int64_t ldt, float* C, int64_t ldc, float alpha, float beta);
+
 /* Rounds a device-side wait of this context's kernels may spin before it
  * gives up (the radix passes' decoupled look-back over earlier tiles of a
  * column, Algorithm 1's sort; the ordered mode of the l1 query waiting for

@@ -87,6 +87,8 @@ def load() -> ctypes.CDLL:
             "dm_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int), P, P, P], I32),
             "dm_l2sq_matmat_noalloc": ([I32, P, I64, I64, I64, P, I64, I64, P, I64, P], I32),
             "dm_set_wait_limit": ([P, ctypes.c_uint32], I32),
+            "dm_dense_tn": ([P, P, I64, I64, I64, P, I64, I64, P, I64, ctypes.c_float], I32),
+            "dm_dense_nn": ([P, P, I64, I64, I64, P, I64, I64, P, I64, ctypes.c_float, ctypes.c_float], I32),
             "dm_test_unpublished_wait": ([P], I32),
         }
         for name, (args, res) in sigs.items():
@@ -420,6 +422,56 @@ def dm_batch_destroy(batch: Batch) -> None:
 
 def dm_sync(ctx: Context) -> None:
     _check(load().dm_sync(ctx.handle), "dm_sync")
+
+
+def _dense_operand(t, device: int, what: str):
+    import torch
+    if t.dtype != torch.float32 or t.ndim != 2:
+        raise DMError(DM_ERR_INVALID_ARG, f"{what} must be a 2-D FP32 tensor")
+    _on_device(device, t)
+    return t, _ld(t)
+
+
+def dm_dense_tn(ctx: Context, A, B, alpha: float = 1.0, out=None):
+    """dm_dense_tn: alpha A^T B for FP32 blocks A (n x m) and B (n x k)."""
+    import torch
+    A, lda = _dense_operand(A, ctx.device, "A")
+    B, ldb = _dense_operand(B, ctx.device, "B")
+    n, m = A.shape
+    if B.shape[0] != n:
+        raise DMError(DM_ERR_INVALID_ARG, "A and B must have the same number of rows")
+    k = B.shape[1]
+    if out is None:
+        out = torch.empty((m, k), dtype=torch.float32, device=A.device)
+    out, ldc = _dense_operand(out, ctx.device, "out")
+    if tuple(out.shape) != (m, k):
+        raise DMError(DM_ERR_INVALID_ARG, f"out must be ({m}, {k})")
+    _check(load().dm_dense_tn(ctx.handle, ctypes.c_void_p(A.data_ptr()), n, m, lda,
+                              ctypes.c_void_p(B.data_ptr()), k, ldb, ctypes.c_void_p(out.data_ptr()), ldc,
+                              float(alpha)), "dm_dense_tn")
+    return out
+
+
+def dm_dense_nn(ctx: Context, A, T, out=None, alpha: float = 1.0, beta: float = 0.0):
+    """dm_dense_nn: beta out + alpha A T for FP32 blocks A (n x m), T (m x k);
+    out is allocated (and beta ignored) when None."""
+    import torch
+    A, lda = _dense_operand(A, ctx.device, "A")
+    T, ldt = _dense_operand(T, ctx.device, "T")
+    n, m = A.shape
+    if T.shape[0] != m:
+        raise DMError(DM_ERR_INVALID_ARG, "T must have as many rows as A has columns")
+    k = T.shape[1]
+    if out is None:
+        out = torch.empty((n, k), dtype=torch.float32, device=A.device)
+        beta = 0.0
+    out, ldc = _dense_operand(out, ctx.device, "out")
+    if tuple(out.shape) != (n, k):
+        raise DMError(DM_ERR_INVALID_ARG, f"out must be ({n}, {k})")
+    _check(load().dm_dense_nn(ctx.handle, ctypes.c_void_p(A.data_ptr()), n, m, lda,
+                              ctypes.c_void_p(T.data_ptr()), k, ldt, ctypes.c_void_p(out.data_ptr()), ldc,
+                              float(alpha), float(beta)), "dm_dense_nn")
+    return out
 
 
 def dm_set_wait_limit(ctx: Context, rounds: int = 0) -> None:

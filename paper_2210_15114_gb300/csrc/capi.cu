@@ -1298,6 +1298,33 @@ dm_status dm_matvec_l2sq(dm_plan* p, const void* z, void* out) {
     return dm_matmat(p, z, 1, 1, out, 1);
 }
 
+dm_status dm_dense_tn(dm_ctx* ctx, const float* A, int64_t n, int64_t m, int64_t lda, const float* B,
+                      int64_t k, int64_t ldb, float* C, int64_t ldc, float alpha) {
+    if (!ctx || ctx->destroyed || !A || !B || !C || n < 1 || m < 1 || k < 1 || lda < m || ldb < k || ldc < k)
+        return DM_ERR_INVALID_ARG;
+    if (m > INT_MAX / 2 || k > INT_MAX / 2) return DM_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    int chunks = 0;
+    int64_t rpc = 0;
+    dense_tn_plan(n, m, k, ctx->num_sms, &chunks, &rpc);
+    DM_TRY(ensure_arena(ctx, (size_t)chunks * (size_t)m * (size_t)k * sizeof(float)));
+    ProfScope ps(ctx, "dense_tn");
+    DM_TRY_CUDA(dense_tn_launch(A, n, m, lda, B, k, ldb, C, ldc, alpha, static_cast<float*>(ctx->arena),
+                                ctx->num_sms, ctx->stream, &ctx->launches));
+    return DM_OK;
+}
+
+dm_status dm_dense_nn(dm_ctx* ctx, const float* A, int64_t n, int64_t m, int64_t lda, const float* T,
+                      int64_t k, int64_t ldt, float* C, int64_t ldc, float alpha, float beta) {
+    if (!ctx || ctx->destroyed || !A || !T || !C || n < 1 || m < 1 || k < 1 || lda < m || ldt < k || ldc < k)
+        return DM_ERR_INVALID_ARG;
+    if (k > 64 || m > INT_MAX / 2) return DM_ERR_UNSUPPORTED;
+    DeviceGuard g(ctx->device);
+    ProfScope ps(ctx, "dense_nn");
+    DM_TRY_CUDA(dense_nn_launch(A, n, m, lda, T, k, ldt, C, ldc, alpha, beta, ctx->stream, &ctx->launches));
+    return DM_OK;
+}
+
 dm_status dm_sync(dm_ctx* ctx) {
     if (!ctx || ctx->destroyed) return DM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);

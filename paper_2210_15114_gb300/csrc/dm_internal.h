@@ -220,6 +220,18 @@ struct OddArgs {
 size_t oddp_scratch_bytes(int64_t n, int64_t d, int64_t k, int p);
 cudaError_t oddp_launch(const OddArgs& a, int stage, cudaStream_t s, int64_t* launches);
 
+// Dense products on tall-skinny FP32 blocks (dense.cu), for the block Krylov
+// iteration.  dense_tn: C (m x k) = alpha A^T B (A n x m, B n x k), partial
+// tiles in `part` (dense_tn_plan's chunks x m x k floats), then added in FP64.
+// dense_nn: C (n x k) = beta C + alpha A T (A n x m, T m x k), k <= 64.
+void dense_tn_plan(int64_t n, int64_t m, int64_t k, int num_sms, int* chunks, int64_t* rows_per_chunk);
+cudaError_t dense_tn_launch(const float* A, int64_t n, int64_t m, int64_t lda, const float* B, int64_t k,
+                            int64_t ldb, float* C, int64_t ldc, float alpha, float* part, int num_sms,
+                            cudaStream_t st, int64_t* launches);
+cudaError_t dense_nn_launch(const float* A, int64_t n, int64_t m, int64_t lda, const float* T, int64_t k,
+                            int64_t ldt, float* C, int64_t ldc, float alpha, float beta, cudaStream_t st,
+                            int64_t* launches);
+
 // Variants (variants.cu).
 cudaError_t scale_launch(dm_dtype t, void* out, int64_t n, int64_t k, int64_t ldo, double s,
                          int num_sms, cudaStream_t st, int64_t* launches);

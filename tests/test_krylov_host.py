@@ -1,7 +1,9 @@
 """Host-side steps of the block Krylov iteration (torch on the CPU): the
 orthonormalization of a block against the earlier basis, for full-rank,
-rank-deficient and zero blocks.  The products A Z are the library's and are
-tested on the GPU; these steps are dense linear algebra on tall blocks."""
+rank-deficient and zero blocks.  The products A Z and the dense tall-skinny
+products (dm_dense_tn / dm_dense_nn) are the library's and are tested on the
+GPU; here the dense products are replaced by torch products on the CPU, which
+checks the iteration's logic, not the kernels."""
 import types
 
 import numpy as np
@@ -12,6 +14,24 @@ torch = pytest.importorskip("torch")
 from paper_2210_15114_gb300 import krylov  # noqa: E402
 
 N, K = 3000, 10
+
+
+@pytest.fixture(autouse=True)
+def dense_on_cpu(monkeypatch):
+    from paper_2210_15114_gb300 import binding
+
+    def tn(ctx, A, B, alpha=1.0, out=None):
+        return alpha * (A.T @ B)
+
+    def nn(ctx, A, T, out=None, alpha=1.0, beta=0.0):
+        r = alpha * (A @ T)
+        if out is None:
+            return r
+        out.mul_(beta).add_(r)
+        return out
+
+    monkeypatch.setattr(binding, "dm_dense_tn", tn)
+    monkeypatch.setattr(binding, "dm_dense_nn", nn)
 
 
 def _basis(n, m, seed):
@@ -41,8 +61,8 @@ def gen():
 def test_full_rank_block(gen):
     prev = _basis(N, 6, 1)
     g = torch.Generator().manual_seed(2)
-    W = krylov._project_out(torch.randn(N, K, generator=g), prev)
-    Q = krylov._orthonormalize(W, prev, gen)
+    W = krylov._project_out(None, torch.randn(N, K, generator=g), prev)
+    Q = krylov._orthonormalize(None, W, prev, gen)
     _check_orthonormal(Q, prev)
     assert _in_span(W, Q, 1e-5)
 
@@ -51,9 +71,9 @@ def test_rank_deficient_block_keeps_resolved_directions(gen):
     prev = _basis(N, 6, 3)
     g = torch.Generator().manual_seed(4)
     low = torch.randn(N, 4, generator=g) @ torch.randn(4, K, generator=g)   # rank 4
-    W = krylov._project_out(low + 1e-9 * torch.randn(N, K, generator=g), prev)
-    assert krylov._cholqr2(W) is None                 # deficient: the fallback runs
-    Q = krylov._orthonormalize(W, prev, gen)
+    W = krylov._project_out(None, low + 1e-9 * torch.randn(N, K, generator=g), prev)
+    assert krylov._cholqr2(None, W) is None                 # deficient: the fallback runs
+    Q = krylov._orthonormalize(None, W, prev, gen)
     assert Q.shape == (N, K)
     _check_orthonormal(Q, prev)
     assert _in_span(W, Q, 1e-5)                       # the rank-4 range is kept
@@ -69,22 +89,22 @@ def test_long_deficient_block_needs_no_householder(gen, monkeypatch):
     def no_qr(*a, **k):
         raise AssertionError("Householder fallback used")
     monkeypatch.setattr(torch.linalg, "qr", no_qr)
-    Q = krylov._orthonormalize(W, prev, gen)
+    Q = krylov._orthonormalize(None, W, prev, gen)
     _check_orthonormal(Q, prev, tol=1e-5)
     assert _in_span(W, Q, 1e-5)
 
 
 def test_zero_block_gets_fill(gen):
     prev = _basis(N, 6, 5)
-    Q = krylov._orthonormalize(torch.zeros(N, K), prev, gen)
+    Q = krylov._orthonormalize(None, torch.zeros(N, K), prev, gen)
     _check_orthonormal(Q, prev)
 
 
 def test_fill_is_seeded():
     prev = _basis(N, 3, 6)
     W = torch.zeros(N, K)
-    a = krylov._orthonormalize(W, prev, torch.Generator().manual_seed(9))
-    b = krylov._orthonormalize(W, prev, torch.Generator().manual_seed(9))
+    a = krylov._orthonormalize(None, W, prev, torch.Generator().manual_seed(9))
+    b = krylov._orthonormalize(None, W, prev, torch.Generator().manual_seed(9))
     assert torch.equal(a, b)
 
 
