@@ -89,8 +89,14 @@ def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
         Q[:, i * k:(i + 1) * k] = W
         binding.dm_matmat(plan, Q[:, i * k:(i + 1) * k], out=AQ[:, i * k:(i + 1) * k])
         W = AQ[:, i * k:(i + 1) * k].clone()
-    M = _tn(ctx, Q, AQ).double()
-    M = 0.5 * (M + M.T)
+    # Rayleigh-Ritz matrix Q^T (A Q): symmetric, so only the block columns'
+    # upper parts are formed (block column j: blocks 0..j), and the strict
+    # upper triangle is mirrored
+    M = torch.zeros((q * k, q * k), dtype=torch.float64, device=dev)
+    for j in range(q):
+        M[: (j + 1) * k, j * k:(j + 1) * k] = _tn(ctx, Q[:, : (j + 1) * k], AQ[:, j * k:(j + 1) * k]).double()
+    upper = torch.triu(M, diagonal=1)
+    M = upper + upper.T + torch.diag(torch.diagonal(M))
     theta, V = torch.linalg.eigh(M)
     order = torch.argsort(theta.abs(), descending=True)[:rank]
     U = _nn(ctx, Q, V[:, order].to(dt))
