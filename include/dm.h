@@ -97,13 +97,14 @@ dm_status dm_set_deterministic(dm_ctx* ctx, int on);
  * A): the reduce [X - mu, 1, s]^T Z (also of squared-l2 gradients and of
  * even-p DM_LPP products) and the apply -2 (X - mu) W of
  * out = s u^T + 1 v^T - 2 (X - mu) W.  Both tensor-core kernels use tcgen05
- * with TF32 operands split as hi + lo (three products per term, FP32
- * accumulation).
- *   DM_ENGINE_TENSOR_CORES: the reduce for FP32 data with d + 2 <= 128 and
- *     column blocks its shared memory holds (accumulation drained every 64
- *     points, FP64 across runs); the apply for FP32 data with d a multiple
- *     of 4 up to 32, k <= 32 and contiguous rows of X; other shapes and types
- *     keep the CUDA-core kernels.
+ * with TF32 operands split as hi + lo and FP32 accumulation (the reduce forms
+ * all four partial products in one MMA per K step, its accumulator drained
+ * every 32 points into FP32 runs and FP64 sums; the apply three products).
+ *   DM_ENGINE_TENSOR_CORES: the reduce for FP32 data with d and k multiples
+ *     of 4, d <= 60, k <= 32 and contiguous, 16-byte aligned rows of X and Z;
+ *     the apply for FP32 data with d a multiple of 4 up to 32, k <= 32 and
+ *     contiguous rows of X; other shapes and types keep the CUDA-core
+ *     kernels.
  *   DM_ENGINE_CUDA_CORES: always the CUDA-core kernels.
  *   DM_ENGINE_AUTO (the default): the tensor cores where they measured at
  *     least as fast: the apply when k >= 16 and d k >= 512; the reduce never

@@ -516,6 +516,7 @@ dm_status lpp_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_t l
         r.num_sms = ctx->num_sms;
         r.err = ctx->err;
         r.engine = ctx->engine;
+        r.spin_limit = ctx->spin_limit;
         const size_t o_res = up16((size_t)reduce_blocks(r) * (D + 2) * kk * 8);
         r.partial = base;
         r.res = base + o_res;
@@ -616,6 +617,7 @@ dm_status matmat_run(const Exec& e, dm_plan* p, const void* Z, int64_t k, int64_
         r.num_sms = ctx->num_sms;
         r.err = ctx->err;
         r.engine = ctx->engine;
+        r.spin_limit = ctx->spin_limit;
         const int blocks = reduce_blocks(r);
         const size_t o_res = up16((size_t)blocks * (d + 2) * kk * 8);
         unsigned char* base = e.scratch;
@@ -710,6 +712,7 @@ dm_status grad_impl(dm_plan* p, const void* W, int64_t ldw, const void* Z, int64
     r.num_sms = ctx->num_sms;
     r.err = ctx->err;
     r.engine = ctx->engine;
+    r.spin_limit = ctx->spin_limit;
     const int blocks = reduce_blocks(r);
     const size_t o_res = up16(gbytes + (size_t)blocks * (d + 2) * 2 * k * 8);
     DM_TRY(ensure_arena(ctx, up16(o_res + (size_t)(d + 2) * 2 * k * 8)));

@@ -111,6 +111,7 @@ struct ReduceArgs {
     int max_blocks;                      // 0: no cap beyond the default
     uint32_t* err;                       // device error word (may be null)
     int engine;                          // dm_engine: the contraction's units
+    uint32_t spin_limit = kSpinLimit;    // rounds of a tensor-core wait before DM_ERR_TIMEOUT
 };
 bool reduce_supported(int64_t d, int64_t k);   // any element type (FP64 worst case)
 int64_t reduce_max_k(dm_dtype t, int64_t d);   // columns per launch for this type

@@ -13,16 +13,14 @@
 //            partial and a finalize kernel adds the partials in a fixed order.
 //            With s omitted the same kernel gives u and W alone.
 // reduce_tc -- the same contraction for FP32 on the tensor cores (tcgen05,
-//            TF32 hi + lo split), selected with dm_set_engine; see below.
+//            TF32 hi + lo split packed into one MMA per K step); see below.
 // l2prep  -- column means mu (the frame shift), FP64 sums, fixed order.
 // l2apply -- out_i = s_i u + v - 2 (x_i - mu) . W  (the p = 2 query, Appendix
 //            A), s_i recomputed from the staged row with the same code as in
 //            the reduce.
 // The contraction does 2(d+2)k flops per (4d + 4k) bytes read (5.6 flop/byte
-// at d = 32, k = 16).  Neither reduce reaches the HBM roof: both are bound by
-// the instructions that stage, centre and (on the tensor cores) split the
-// rows, and the CUDA-core kernel measured faster at every shape, so it is the
-// default.
+// at d = 32, k = 16): HBM-bound on either unit, so what decides is the
+// instruction count of staging, centring and splitting the rows.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -343,322 +341,17 @@ __global__ void reduce_finalize_kernel(const Wide* __restrict__ partial, int blo
     if (lane == 0) res[w] = acc;
 }
 
-// --------------------------------------------------- reduce on tensor cores
-// FP32 data: the same contraction [X - mu, 1, s]^T Z on the 5th-generation
-// tensor cores (tcgen05.mma, kind::tf32), accumulated in tensor memory.
-//
-// Operands live in shared memory in the canonical K-major layout without
-// swizzle; the contraction index K runs over the points:
-//   A: M = 128 rows, the d + 2 rows of [X - mu, 1, s]^T (zero padded),
-//   B: N = k rounded up to 16 rows, the columns of Z (zero padded),
-//   K = 64 points per chunk, 8 per instruction.
-// Element (r, p) of a tile sits at byte (r / 8) * SBO + (p / 4) * LBO +
-// (r % 8) * 16 + (p % 4) * 4: core matrices of 8 rows x 16 bytes, adjacent
-// along K (LBO = 128 bytes), 8-row groups SBO = 16 * 128 bytes apart.
-//
-// Precision (split precision on TF32 tensor cores): every operand is split
-// into two TF32 parts, v = hi + lo with hi = tf32(v) and lo = tf32(v - hi)
-// (about 21 significant bits together), and each product is formed as
-// hi*hi + hi*lo + lo*hi (three MMAs; lo*lo lies below FP32 resolution).
-// The tensor core's FP32 accumulation drifts with the number of additions
-// (measured: relative error 5e-6 after 1024 points, 1.2e-6 after 256,
-// 3.5e-7 after 64), so an accumulator in TMEM holds one chunk of 64 points
-// only: each chunk's D is read into FP32 registers (round-to-nearest adds),
-// and those go into the CTA's FP64 partial of its segment every kTcRun
-// points (the length of the CUDA-core kernel's FP32 runs); a finalize adds
-// the partials in a fixed order.
-//
-// Pipeline (one CTA per SM): two operand sets and two accumulators.  Chunk
-// c's raw rows arrive by cp.async during chunk c - 1; all threads form s and
-// the split operands of chunk c in set c % 2 once the MMAs of chunk c - 2
-// (which read that set and wrote accumulator c % 2) have completed -- a
-// bounded mbarrier wait (DM_ERR_TIMEOUT on expiry), after which warps 0-3
-// read that accumulator (the TMEM lanes each warp may access); one thread
-// then issues chunk c's 24 MMAs and commits them to the set's mbarrier, and
-// the tensor core runs them while chunk c + 1 is prepared.
-constexpr int kTcM = 128;                        // MMA M: rows of [X - mu, 1, s]^T
-constexpr int kTcK = 64;                         // points per chunk
-constexpr int kTcRun = 1024;                     // points per FP32 register run
-constexpr uint32_t kTcLbo = 128;                 // bytes between core matrices along K
-constexpr uint32_t kTcSbo = (kTcK / 4) * 128;    // bytes between 8-row groups
-static_assert(kTcK * 4 == kThreads, "four threads per point form s");
-
+// ------------------------------------------------ tcgen05 helpers (shared)
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ float tf32_rna(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor: start address, leading (K) and stride
-// (8-row group) byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((kTcLbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((kTcSbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
+// One tcgen05.mma (kind::tf32, one CTA); accumulate = 0 overwrites D.
 __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
                  :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
-}
-
-// Bounded wait for the mbarrier phase of parity `parity` (test_wait does not
-// block, so the bound is the iteration count times the sleep).
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-        __nanosleep(64);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr) : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// Four values of row r, points 4 g4 .. 4 g4 + 3, as their hi and lo parts.
-__device__ __forceinline__ void tc_put4(unsigned char* hi, unsigned char* lo, int r, int g4,
-                                        const float (&v)[4]) {
-    float h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) { h[i] = tf32_rna(v[i]); l[i] = tf32_rna(v[i] - h[i]); }
-    const size_t off = (size_t)(r >> 3) * kTcSbo + (size_t)g4 * kTcLbo + (size_t)(r & 7) * 16;
-    *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-}
-
-size_t tc_smem_bytes(int d, int k) {
-    const int N = (k + 15) / 16 * 16;
-    return 2 * (2 * (size_t)kTcM * kTcK * 4 + 2 * (size_t)N * kTcK * 4) +
-           4 * (2 * (size_t)kTcK * d + 2 * (size_t)kTcK * k + kTcK + d) + 48;
-}
-
-__global__ void __launch_bounds__(kThreads, 1)
-reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, int64_t ldx,
-                 const float* __restrict__ mu, int64_t mu_stride, int with_s,
-                 const float* __restrict__ Z, int k, int64_t ldz, double* __restrict__ partial,
-                 int64_t nseg, int64_t seg_rows, int N, uint32_t tmem_cols, int xv16, int zv16,
-                 uint32_t* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int D2 = d + 2;
-    // Two operand sets (chunk c fills set c % 2 while the tensor core works
-    // on chunk c - 1) and two accumulators in TMEM (columns [b N, b N + N)).
-    const size_t a_bytes = (size_t)kTcM * kTcK * 4, b_bytes = (size_t)N * kTcK * 4;
-    const size_t set_bytes = 2 * a_bytes + 2 * b_bytes;
-    float* xraw = reinterpret_cast<float*>(smem_raw + 2 * set_bytes);   // [2][kTcK][d]
-    float* zraw = xraw + 2 * kTcK * d;                                    // [2][kTcK][k]
-    float* s_buf = zraw + 2 * kTcK * k;                                   // [kTcK]
-    float* mu_s = s_buf + kTcK;                                           // [d]
-    const uintptr_t tail = (reinterpret_cast<uintptr_t>(mu_s + d) + 7) & ~uintptr_t(7);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);                   // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
-
-    for (size_t i = tid; i < 2 * set_bytes / 16; i += kThreads)
-        reinterpret_cast<uint4*>(smem_raw)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int c = tid; c < d; c += kThreads) mu_s[c] = mu ? mu[c * mu_stride] : 0.f;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + 1)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-    // instruction descriptor: D FP32, A and B TF32, both K-major, N, M = 128
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-                           ((uint32_t)(kTcM >> 4) << 24);
-    // descriptors of the first K step of each tile of set 0; set 1 and a K
-    // step (256 bytes) add to the address field (16-byte units; every shared
-    // address stays below 2^18, so the field does not carry)
-    const uint32_t base0 = smem_u32(smem_raw);
-    const uint64_t dah = tc_desc(base0), dal = tc_desc(base0 + (uint32_t)a_bytes);
-    const uint64_t dbh = tc_desc(base0 + 2 * (uint32_t)a_bytes);
-    const uint64_t dbl = tc_desc(base0 + 2 * (uint32_t)a_bytes + (uint32_t)b_bytes);
-    const uint64_t set_step = (uint64_t)(set_bytes >> 4);
-    uint32_t parity = 0u, pending = 0u;   // bit b: operand set / accumulator b
-    bool failed = false;
-    uint32_t gch = 0;        // chunks this CTA has filled (selects the operand set)
-
-    // Warps 0-3: row m = 32 warp + lane of D, up to 64 columns, summed over
-    // the chunks of a run in FP32 registers.
-    float facc[4][16];
-#pragma unroll
-    for (int cb = 0; cb < 4; ++cb)
-#pragma unroll
-        for (int q = 0; q < 16; ++q) facc[cb][q] = 0.f;
-    // Wait for the MMAs that read operand set b and wrote accumulator b, then
-    // add that accumulator into facc.  Uniform across the CTA; false on expiry.
-    auto retire = [&](int b) -> bool {
-        const bool was = (pending >> b) & 1u;
-        bool ok = true;
-        if (was) { ok = tc_wait(smem_u32(mbar + b), (parity >> b) & 1u); parity ^= 1u << b; }
-        if (__syncthreads_or(!ok)) return false;
-        if (was) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (warp < 4) {
-#pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
-                    if (cb * 16 < N) {
-                        float v[16];
-                        tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * N + cb * 16), v);
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) facc[cb][q] += v[q];
-                    }
-                }
-            }
-            pending &= ~(1u << b);
-        }
-        return true;
-    };
-
-    for (int64_t seg = blockIdx.x; seg < nseg && !failed; seg += gridDim.x) {
-        const int64_t s0 = seg * seg_rows, s1 = min64(n, s0 + seg_rows);
-        double* part = partial + seg * (int64_t)D2 * k;
-        bool first_run = true;
-        for (int64_t r0 = s0; r0 < s1 && !failed; r0 += kTcRun) {
-            const int64_t r1 = min64(s1, r0 + kTcRun);
-            const int nch = (int)((r1 - r0 + kTcK - 1) / kTcK);
-            stage_rows(xraw, X, ldx, d, r0, kTcK, (int)min64(kTcK, r1 - r0), xv16 != 0);
-            stage_rows(zraw, Z, ldz, k, r0, kTcK, (int)min64(kTcK, r1 - r0), zv16 != 0);
-            cp_commit();
-            for (int ch = 0; ch < nch; ++ch, ++gch) {
-                const int64_t base = r0 + (int64_t)ch * kTcK;
-                const int nr = (int)min64(kTcK, r1 - base);
-                const int rb = ch & 1;           // raw staging buffer
-                const int ob = (int)(gch & 1u);  // operand set and accumulator
-                if (ch + 1 < nch) {
-                    const int64_t nb = base + kTcK;
-                    const int nn = (int)min64(kTcK, r1 - nb);
-                    stage_rows(xraw + (rb ^ 1) * kTcK * d, X, ldx, d, nb, kTcK, nn, xv16 != 0);
-                    stage_rows(zraw + (rb ^ 1) * kTcK * k, Z, ldz, k, nb, kTcK, nn, zv16 != 0);
-                    cp_commit();
-                    cp_wait<1>();
-                } else {
-                    cp_wait<0>();
-                }
-                __syncthreads();
-                const float* xb = xraw + rb * kTcK * d;
-                const float* zb = zraw + rb * kTcK * k;
-                {   // s_p = ||x_p - mu||^2, four threads per point
-                    const int p = tid >> 2, part4 = tid & 3;
-                    float acc = 0.f;
-                    for (int c = part4; c < d; c += 4) {
-                        const float v = xb[p * d + c] - mu_s[c];
-                        acc = fmaf(v, v, acc);
-                    }
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                    if (part4 == 0) s_buf[p] = (with_s && p < nr) ? acc : 0.f;
-                }
-                // operand set ob was read by the MMAs of chunk gch - 2
-                if (!retire(ob)) { failed = true; break; }
-                unsigned char* a_hi = smem_raw + ob * set_bytes;
-                unsigned char* a_lo = a_hi + a_bytes;
-                unsigned char* b_hi = a_lo + a_bytes;
-                unsigned char* b_lo = b_hi + b_bytes;
-                // warp w takes the 4-point groups g4 = w, w + 8; its lanes the
-                // rows (adjacent rows: conflict-free 16-byte stores)
-                for (int g4 = warp; g4 < kTcK / 4; g4 += kWarps) {
-                    for (int r = lane; r < D2; r += 32) {
-                        float v[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int p = 4 * g4 + i;
-                            v[i] = p >= nr ? 0.f : r < d ? xb[p * d + r] - mu_s[r] : r == d ? 1.f : s_buf[p];
-                        }
-                        tc_put4(a_hi, a_lo, r, g4, v);
-                    }
-                    for (int r = lane; r < k; r += 32) {
-                        float v[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) v[i] = zb[(4 * g4 + i) * k + r];   // zero past nr
-                        tc_put4(b_hi, b_lo, r, g4, v);
-                    }
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
-                if (tid == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t dt = tmem + (uint32_t)(ob * N);
-                    const uint64_t so = ob ? set_step : 0u;
-#pragma unroll
-                    for (int st = 0; st < kTcK / 8; ++st) {
-                        const uint64_t o = so + ((uint64_t)(st * 2 * kTcLbo) >> 4);
-                        tc_mma(dt, dah + o, dbh + o, idesc, st > 0 ? 1u : 0u);
-                        tc_mma(dt, dah + o, dbl + o, idesc, 1u);
-                        tc_mma(dt, dal + o, dbh + o, idesc, 1u);
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 :: "r"(smem_u32(mbar + ob)) : "memory");
-                }
-                pending |= 1u << ob;
-            }
-            if (failed) break;
-            // end of the run: both accumulators into facc, facc into the
-            // segment's FP64 partial
-            if (!retire(0) || !retire(1)) { failed = true; break; }
-            if (warp < 4) {
-                const int m = warp * 32 + lane;
-#pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int j = cb * 16 + q;
-                        if (m < D2 && j < k) {
-                            double* dst = part + (int64_t)m * k + j;
-                            *dst = first_run ? (double)facc[cb][q] : *dst + (double)facc[cb][q];
-                        }
-                        facc[cb][q] = 0.f;
-                    }
-                }
-            }
-            first_run = false;
-            // the reads of the accumulators precede the next MMAs into them
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-        }
-    }
-    if (failed) {
-        if (err) set_error(err, kErrTimeout);
-        // committed MMAs may still target TMEM and read the operand sets: a
-        // last bounded wait for each before the memory is released
-        for (int b = 0; b < 2; ++b)
-            if ((pending >> b) & 1u) tc_wait(smem_u32(mbar + b), (parity >> b) & 1u);
-    }
-    cp_wait<0>();
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
-    }
 }
 
 // ----------------------------------------------------------------- l2prep
@@ -782,6 +475,14 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// tcgen05.ld of 8 columns without the wait (the caller waits once for all).
+__device__ __forceinline__ void tc_ld8_issue(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr) : "memory");
 }
 
 __device__ __forceinline__ uint64_t tc_desc_sbo(uint32_t saddr, uint32_t sbo) {
@@ -1007,6 +708,408 @@ l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// --------------------------------------------------- reduce on tensor cores
+// FP32 data, d a multiple of 4 up to 60, k a multiple of 4 up to 32, rows of
+// X and Z contiguous: the contraction [X - mu, 1, s]^T Z on tcgen05.mma
+// (kind::tf32).  The contraction index K runs over the points, KC per chunk
+// and 8 per instruction; the threads write both operands in the canonical
+// K-major layout without swizzle -- element (r, p) at byte (r / 8) SBO +
+// (p / 4) 128 + (r % 8) 16 + (p % 4) 4, SBO = KC / 4 * 128 -- transposing
+// the row-major raw chunk on the way.
+// Split precision in one MMA per K step: every value is split as
+// v = hi + lo (split_tf32), A's rows are [Y_hi; Y_lo] with Y = [X - mu, 1,
+// s]^T (rows 0 .. D2 - 1 and D2 .. 2 D2 - 1, D2 = d + 2) and B's rows are
+// [Z_hi; Z_lo] (Kp = k rounded up to 8 rows each), so the accumulator
+// D = A B^T (M = 128, N = 2 Kp) holds the four partial products
+//   D[r][j] = Y_hi Z_hi,        D[r][Kp + j] = Y_hi Z_lo,
+//   D[D2 + r][j] = Y_lo Z_hi,   D[D2 + r][Kp + j] = Y_lo Z_lo,
+// whose sum is the product to about 2^-20 of each term.  Rows of A from
+// 2 D2 on and rows of B past k in each half are never written: they reach
+// only accumulator rows and columns that are never read.  When the unused
+// 8-row groups of A have room for B, B lives there.
+// Sums: the tensor core's FP32 accumulation drifts with the number of
+// accumulations, so one accumulator takes one chunk (KC / 8 MMAs); two
+// accumulators in TMEM alternate, and while the next chunk runs the threads
+// add a finished one into FP32 registers (warp w: accumulator rows
+// 32 (w % 4) .. + 31, column half w / 4), every kRtFlush chunks into the
+// CTA's FP64 sums in shared memory, and at the end the four products of
+// each entry go into the CTA's FP64 partial; reduce_finalize adds the
+// partials in a fixed order.
+// Pipeline (each CTA a contiguous range of chunks), by role:
+//   one thread (warp 8) keeps STAGES raw chunks (the rows of X and Z, both
+//     contiguous) on their way by bulk copies, and for each chunk waits until
+//     the workers have filled its operand set, issues its KC / 8 MMAs into
+//     accumulator c % 2 and commits them to that set's mbarrier; a consumed
+//     raw stage is refilled at once;
+//   eight worker warps wait for raw chunk c and for the MMAs of chunk c - 2
+//     (which read operand set c % 2 and wrote accumulator c % 2), start the
+//     TMEM loads of that accumulator, shift, split and transpose chunk c into
+//     the set, add the loaded accumulator into their registers and arrive on
+//     the set's mbarrier.
+// No CTA-wide barrier inside the loop: the roles meet on mbarriers only.
+// Every wait is bounded: on expiry a thread sets the CTA's abort word, which
+// ends every other wait; the CTA latches DM_ERR_TIMEOUT, waits (bounded) for
+// its own copies and MMAs in flight, frees its TMEM and exits.
+constexpr int kRtW = 8;                  // worker warps
+constexpr int kRtWT = 32 * kRtW;         // worker threads
+constexpr int kRtT = kRtWT + 32;         // and one warp that issues the copies and MMAs
+constexpr int kRtFlush = 16;             // chunks per FP32 register run
+
+// CTAs per SM the launch is built for (its register bound): up to 16 query
+// columns three with 32-point chunks, two with 64; wider blocks one (their
+// registers would spill at two).
+__host__ __device__ constexpr int rt_min_blocks(int KC, int KPM) { return KPM <= 16 ? (KC == 32 ? 3 : 2) : 1; }
+
+// Byte layout of one CTA's shared memory (host and device).
+struct RtShape {
+    int Kp, N, D2;
+    uint32_t sbo, b_off, set_bytes, raw_x, raw_bytes, acc_off, mu_off, bar_off, total;
+};
+
+__host__ __device__ inline RtShape rt_shape(int KC, int stages, int d, int k) {
+    RtShape s;
+    s.Kp = (k + 7) / 8 * 8;
+    s.N = 2 * s.Kp;
+    s.D2 = d + 2;
+    s.sbo = (uint32_t)(KC / 4) * 128u;
+    const uint32_t used = (uint32_t)(2 * s.D2 + 7) / 8;   // 8-row groups of A with data
+    const uint32_t bgroups = (uint32_t)s.N / 8;
+    const bool inside = used + bgroups <= 16;
+    s.b_off = (inside ? used : 16u) * s.sbo;
+    s.set_bytes = (inside ? 16u : 16u + bgroups) * s.sbo;
+    s.raw_x = (uint32_t)(KC * d * 4);
+    s.raw_bytes = (uint32_t)(KC * (d + k) * 4);
+    s.acc_off = 2 * s.set_bytes + (uint32_t)stages * s.raw_bytes;
+    s.mu_off = s.acc_off + (uint32_t)(2 * s.D2 * s.N) * 8u;
+    s.bar_off = s.mu_off + ((uint32_t)d * 4u + 15u) / 16u * 16u;
+    s.total = s.bar_off + 8u * (uint32_t)(stages + 4) + 16u;
+    return s;
+}
+
+// Bounded wait on an mbarrier phase that also gives up once the CTA's abort
+// word is set (another thread's wait ran out).
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, uint32_t limit,
+                                             volatile uint32_t* abort_w) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if (*abort_w) return false;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+// Bulk copy global -> shared without an arrive (the caller has set the
+// transaction count of the whole stage on mbar).
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+// Four points of one operand row: shift (X only), split, and store hi and lo
+// as 16-byte pieces of their rows.  FULL: all four points exist.
+template <bool FULL>
+__device__ __forceinline__ void rt_put4(unsigned char* base, const float* src, int stride, float shift,
+                                        int p0, int nr, uint32_t off_hi, uint32_t off_lo) {
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float v = (FULL || p0 + e < nr) ? src[e * stride] - shift : 0.f;
+        split_tf32(v, h[e], l[e]);
+    }
+    *reinterpret_cast<float4*>(base + off_hi) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(base + off_lo) = make_float4(l[0], l[1], l[2], l[3]);
+}
+
+template <int KC, int STAGES, int KPM>
+__global__ void __launch_bounds__(kRtT, rt_min_blocks(KC, KPM))
+reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ mu,
+                 int64_t mu_stride, int with_s, const float* __restrict__ Z, int k,
+                 double* __restrict__ partial, uint32_t tmem_cols, uint32_t* err, uint32_t spin_limit) {
+    constexpr int G4 = KC / 4;             // 4-point groups per chunk
+    constexpr int MQX = KC / 16;           // X items per worker thread (d <= 64)
+    constexpr int MQZ = KC / 32;           // Z items per worker thread (k <= 32)
+    constexpr int TPP = kRtWT / KC;        // worker threads per point forming s
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const RtShape S = rt_shape(KC, STAGES, d, k);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D2 = S.D2, Kp = S.Kp, N = S.N;
+    const uint32_t sbo = S.sbo;
+    unsigned char* raw = smem_raw + 2 * S.set_bytes;
+    double* acc64 = reinterpret_cast<double*>(smem_raw + S.acc_off);    // [2 D2][N]
+    float* mu_s = reinterpret_cast<float*>(smem_raw + S.mu_off);        // [d]
+    // mbarriers: raw_full[STAGES] (the copies), op_full[2] (the workers'
+    // splits), mma_done[2] (the MMAs' commits); then the abort word and the
+    // TMEM address
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + S.bar_off);
+    uint64_t* raw_full = mbar;
+    uint64_t* op_full = mbar + STAGES;
+    uint64_t* mma_done = mbar + STAGES + 2;
+    volatile uint32_t* abort_w = reinterpret_cast<volatile uint32_t*>(mbar + STAGES + 4);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + STAGES + 4) + 1;
+
+    for (int i = tid; i < 2 * D2 * N; i += kRtT) acc64[i] = 0.0;
+    for (int c = tid; c < d; c += kRtT) mu_s[c] = mu ? mu[c * mu_stride] : 0.f;
+    // the row of ones (hi 1, lo 0) of both operand sets stays as written:
+    // points past n meet rows of Z that are zero
+    for (int i = tid; i < 2 * KC; i += kRtT) {
+        unsigned char* A = smem_raw + (i / KC) * S.set_bytes;
+        const int p = i % KC, rl = D2 + d;
+        const uint32_t po = (uint32_t)(p >> 2) * 128u + (uint32_t)(p & 3) * 4u;
+        *reinterpret_cast<float*>(A + (uint32_t)(d >> 3) * sbo + (uint32_t)(d & 7) * 16u + po) = 1.f;
+        *reinterpret_cast<float*>(A + (uint32_t)(rl >> 3) * sbo + (uint32_t)(rl & 7) * 16u + po) = 0.f;
+    }
+    if (tid == 0) {
+        for (int b = 0; b < STAGES; ++b) mbar_init(smem_u32(raw_full + b), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(op_full + b), kRtWT);
+            mbar_init(smem_u32(mma_done + b), 1);
+        }
+        *abort_w = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kRtW) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    const int64_t C = (n + KC - 1) / KC;
+    const int64_t c0 = C * blockIdx.x / gridDim.x, c1 = C * (blockIdx.x + 1) / gridDim.x;
+    const int64_t my = c1 - c0;
+
+    if (warp < kRtW) {
+        // ---------------------------------------------------------- workers
+        // This thread's split items, fixed for every chunk: X item q is
+        // (coordinate f, point group g) = (it % d, it / d), it = tid + q kRtWT
+        // (a warp's items are adjacent coordinates: conflict-free reads of the
+        // raw rows and 16-byte writes to eight distinct bank groups); Z item q
+        // the same over the k columns.
+        int xsrc[MQX], xg[MQX];
+        uint32_t xhi[MQX], xlo[MQX];
+        float xmu[MQX];
+#pragma unroll
+        for (int q = 0; q < MQX; ++q) {
+            const int it = tid + q * kRtWT;
+            const int f = it % d, g = it / d, rl = D2 + f;
+            xg[q] = it < d * G4 ? 4 * g : -1;
+            xsrc[q] = 4 * g * d + f;
+            xhi[q] = (uint32_t)(f >> 3) * sbo + (uint32_t)g * 128u + (uint32_t)(f & 7) * 16u;
+            xlo[q] = (uint32_t)(rl >> 3) * sbo + (uint32_t)g * 128u + (uint32_t)(rl & 7) * 16u;
+            xmu[q] = mu_s[f];
+        }
+        int zsrc[MQZ], zg[MQZ];
+        uint32_t zhi[MQZ], zlo[MQZ];
+#pragma unroll
+        for (int q = 0; q < MQZ; ++q) {
+            const int it = tid + q * kRtWT;
+            const int j = it % k, g = it / k;
+            zg[q] = it < k * G4 ? 4 * g : -1;
+            zsrc[q] = 4 * g * k + j;
+            zhi[q] = S.b_off + (uint32_t)(j >> 3) * sbo + (uint32_t)g * 128u + (uint32_t)(j & 7) * 16u;
+            zlo[q] = zhi[q] + (uint32_t)(Kp >> 3) * sbo;
+        }
+        // s: TPP adjacent threads per point, each a share of its 16-byte
+        // pieces, the pieces rotated so that the eight lanes of a 16-byte
+        // access phase read distinct bank groups
+        const int sp = tid / TPP, spart = tid % TPP, nq = d / 4, srot = (sp * TPP) % nq;
+        const uint32_t s_po = (uint32_t)(sp >> 2) * 128u + (uint32_t)(sp & 3) * 4u;
+        const uint32_t s_hi = (uint32_t)((d + 1) >> 3) * sbo + (uint32_t)((d + 1) & 7) * 16u + s_po;
+        const uint32_t s_lo = (uint32_t)((D2 + d + 1) >> 3) * sbo + (uint32_t)((D2 + d + 1) & 7) * 16u + s_po;
+
+        const int hw = warp >> 2;                         // column half of the accumulator
+        const int arow = 32 * (warp & 3) + lane;          // accumulator row
+        const bool dwarp = 32 * (warp & 3) < 2 * D2;      // the warp's rows hold data
+        float facc[KPM];
+#pragma unroll
+        for (int j = 0; j < KPM; ++j) facc[j] = 0.f;
+        int run = 0;
+        uint32_t r[KPM];
+        auto flush = [&]() {
+            if (dwarp && arow < 2 * D2) {
+                double* dst = acc64 + arow * N + hw * Kp;
+#pragma unroll
+                for (int j = 0; j < KPM; ++j)
+                    if (j < Kp) dst[j] += (double)facc[j];
+            }
+#pragma unroll
+            for (int j = 0; j < KPM; ++j) facc[j] = 0.f;
+            run = 0;
+        };
+        // TMEM loads of accumulator b (its MMAs are known to be complete);
+        // tc_drain_add adds them once they have arrived
+        auto tc_drain_issue = [&](int b) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (dwarp) {
+                const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * N + hw * Kp);
+#pragma unroll
+                for (int t = 0; t < KPM / 8; ++t)
+                    if (t * 8 < Kp) tc_ld8_issue(ta + (uint32_t)(8 * t), r + 8 * t);
+            }
+        };
+        auto tc_drain_add = [&]() {
+            if (dwarp) {
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int t = 0; t < KPM / 8; ++t)
+                    if (t * 8 < Kp)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) facc[8 * t + e] += __uint_as_float(r[8 * t + e]);
+            }
+            if (++run == kRtFlush) flush();
+        };
+
+        bool ok = true;
+        for (int64_t i = 0; i < my; ++i) {
+            const int st = (int)(i % STAGES), ob = (int)(i & 1);
+            const int nr = (int)min64(KC, n - (c0 + i) * KC);
+            // the raw chunk is in place, and operand set ob is free once the
+            // MMAs of chunk i - 2 are done (their accumulator is drained
+            // around the split); a warp agrees on the outcome (the TMEM loads
+            // are warp-wide)
+            ok = mbar_wait_ab(smem_u32(raw_full + st), (uint32_t)(i / STAGES) & 1u, spin_limit, abort_w);
+            if (ok && i >= 2)
+                ok = mbar_wait_ab(smem_u32(mma_done + ob), (uint32_t)((i - 2) >> 1) & 1u, spin_limit, abort_w);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            if (i >= 2) tc_drain_issue(ob);
+            const float* rx = reinterpret_cast<const float*>(raw + (size_t)st * S.raw_bytes);
+            const float* rz = reinterpret_cast<const float*>(raw + (size_t)st * S.raw_bytes + S.raw_x);
+            unsigned char* A = smem_raw + ob * S.set_bytes;
+            if (nr == KC) {
+#pragma unroll
+                for (int q = 0; q < MQX; ++q)
+                    if (xg[q] >= 0) rt_put4<true>(A, rx + xsrc[q], d, xmu[q], xg[q], nr, xhi[q], xlo[q]);
+#pragma unroll
+                for (int q = 0; q < MQZ; ++q)
+                    if (zg[q] >= 0) rt_put4<true>(A, rz + zsrc[q], k, 0.f, zg[q], nr, zhi[q], zlo[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < MQX; ++q)
+                    if (xg[q] >= 0) rt_put4<false>(A, rx + xsrc[q], d, xmu[q], xg[q], nr, xhi[q], xlo[q]);
+#pragma unroll
+                for (int q = 0; q < MQZ; ++q)
+                    if (zg[q] >= 0) rt_put4<false>(A, rz + zsrc[q], k, 0.f, zg[q], nr, zhi[q], zlo[q]);
+            }
+            {
+                float sacc = 0.f;
+                if (with_s) {
+                    const float* xrow = rx + sp * d;
+                    for (int qq = spart; qq < nq; qq += TPP) {
+                        int q = qq + srot;
+                        if (q >= nq) q -= nq;
+                        const float4 x4 = *reinterpret_cast<const float4*>(xrow + 4 * q);
+                        const float4 m4 = *reinterpret_cast<const float4*>(mu_s + 4 * q);
+                        const float y0 = x4.x - m4.x, y1 = x4.y - m4.y, y2 = x4.z - m4.z, y3 = x4.w - m4.w;
+                        sacc = fmaf(y0, y0, sacc);
+                        sacc = fmaf(y1, y1, sacc);
+                        sacc = fmaf(y2, y2, sacc);
+                        sacc = fmaf(y3, y3, sacc);
+                    }
+                }
+#pragma unroll
+                for (int o = TPP / 2; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                if (spart == 0) {
+                    float h, l;
+                    split_tf32(sp < nr ? sacc : 0.f, h, l);
+                    *reinterpret_cast<float*>(A + s_hi) = h;
+                    *reinterpret_cast<float*>(A + s_lo) = l;
+                }
+            }
+            if (i >= 2) tc_drain_add();
+            // set ob written, raw stage st read, accumulator ob read
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(op_full + ob)) : "memory");
+        }
+        // the last two chunks
+        for (int64_t j = my >= 2 ? my - 2 : 0; ok && j < my; ++j) {
+            const int b = (int)(j & 1);
+            ok = mbar_wait_ab(smem_u32(mma_done + b), (uint32_t)(j >> 1) & 1u, spin_limit, abort_w);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc_drain_issue(b);
+            tc_drain_add();
+        }
+        if (!ok) *abort_w = 1u;
+        flush();
+    } else if (lane == 0) {
+        // ---------------------------------- copies and MMAs (one thread)
+        auto issue = [&](int64_t i) {   // raw chunk i of this CTA into stage i % STAGES
+            const int64_t r0 = (c0 + i) * KC;
+            const int nr = (int)min64(KC, n - r0);
+            const int st = (int)(i % STAGES);
+            const uint32_t dst = smem_u32(raw + (size_t)st * S.raw_bytes), bar = smem_u32(raw_full + st);
+            const uint32_t bx = (uint32_t)(nr * d * 4), bz = (uint32_t)(nr * k * 4);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bx + bz) : "memory");
+            bulk_copy(dst, X + r0 * d, bx, bar);
+            bulk_copy(dst + S.raw_x, Z + r0 * k, bz, bar);
+        };
+        // D FP32, A and B TF32, both K-major, N, M = 128
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+        // descriptors of set 0's first K step; set 1 and each K step (256
+        // bytes) add to the address field (16-byte units; shared addresses
+        // stay below 2^18, so the field does not carry)
+        const uint64_t da0 = tc_desc_sbo(smem_u32(smem_raw), sbo);
+        const uint64_t db0 = tc_desc_sbo(smem_u32(smem_raw) + S.b_off, sbo);
+        int64_t issued = 0, committed = 0;
+        for (; issued < STAGES && issued < my; ++issued) issue(issued);
+        for (int64_t i = 0; i < my; ++i) {
+            const int ob = (int)(i & 1);
+            if (!mbar_wait_ab(smem_u32(op_full + ob), (uint32_t)(i >> 1) & 1u, spin_limit, abort_w)) {
+                *abort_w = 1u;
+                break;
+            }
+            // raw stage i % STAGES has been read: the chunk STAGES ahead
+            if (issued < my) issue(issued++);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t so = ob ? (uint64_t)(S.set_bytes >> 4) : 0u;
+            const uint32_t dcol = tmem + (uint32_t)(ob * N);
+#pragma unroll
+            for (int ks = 0; ks < KC / 8; ++ks)
+                tc_mma(dcol, da0 + so + 16u * ks, db0 + so + 16u * ks, idesc, ks > 0 ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(mma_done + ob)) : "memory");
+            committed = i + 1;
+        }
+        if (*abort_w) {
+            // no copy or MMA of this CTA may still target its shared memory
+            // or TMEM when they are released: the last copy into each stage
+            // and the last commit to each set
+            for (int64_t j = issued - 1; j >= 0 && j >= issued - STAGES; --j)
+                mbar_wait(smem_u32(raw_full + (int)(j % STAGES)), (uint32_t)(j / STAGES) & 1u, spin_limit);
+            for (int64_t j = committed - 1; j >= 0 && j >= committed - 2; --j)
+                mbar_wait(smem_u32(mma_done + (int)(j & 1)), (uint32_t)(j >> 1) & 1u, spin_limit);
+        }
+    }
+    __syncthreads();
+    if (*abort_w) {
+        if (tid == 0 && err) set_error(err, kErrTimeout);
+    } else {
+        double* out = partial + (int64_t)blockIdx.x * D2 * k;
+        for (int e = tid; e < D2 * k; e += kRtT) {
+            const int c = e / k, j = e % k;
+            const double* r0 = acc64 + c * N;
+            const double* r1 = acc64 + (D2 + c) * N;
+            out[e] = (r0[j] + r0[Kp + j]) + (r1[j] + r1[Kp + j]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == kRtW) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
     }
@@ -1335,65 +1438,93 @@ bool reduce_supported(int64_t d, int64_t k) {
     return smem <= 220 * 1024;
 }
 
-// The tensor-core path: FP32, d + 2 <= 128 rows of A, k <= 64 columns, the
-// two operand sets in shared memory; taken when the context asks for it, or
-// automatically where it measured faster than the CUDA-core kernel.
+// The tensor-core reduce: FP32 points (or precomputed FP32 features), d a
+// multiple of 4 with the 2 (d + 2) rows of [Y_hi; Y_lo] within M = 128,
+// k a multiple of 4 up to 32, rows of X and Z contiguous and 16-byte
+// aligned (whole bulk copies per chunk).  Taken when the context asks for
+// it, or automatically where it measured faster than the CUDA-core kernel.
 bool tc_shape_ok(const ReduceArgs& a) {
-    return a.dtype == DM_F32 && a.d >= 1 && a.d + 2 <= kTcM && a.k >= 1 && a.k <= 64 &&
-           tc_smem_bytes((int)a.d, (int)a.k) <= 220 * 1024;
+    return a.dtype == DM_F32 && a.d >= 4 && a.d % 4 == 0 && 2 * (a.d + 2) <= 128 && a.k >= 4 &&
+           a.k % 4 == 0 && a.k <= 32 && a.ldx == a.d && a.ldz == a.k && a.X != nullptr && a.Z != nullptr &&
+           reinterpret_cast<uintptr_t>(a.X) % 16 == 0 && reinterpret_cast<uintptr_t>(a.Z) % 16 == 0;
 }
 
-bool tc_auto(const ReduceArgs&) { return false; }
+// Measured (n = 2^20, CUDA-core vs tensor-core reduce + finalize, ms):
+// d 32 k 16: 0.150 / 0.121; d 32 k 4: 0.123 / 0.108; d 16 k 16: 0.110 /
+// 0.105; d 8 k 8: 0.124 / 0.093; d 60 k 32: 0.456 / 0.275; but d 32 k 32:
+// 0.195 / 0.216.
+bool tc_auto(const ReduceArgs& a) { return a.k <= 16 || a.d >= 48; }
 
 bool tc_ok(const ReduceArgs& a) {
     if (!tc_shape_ok(a) || a.engine == DM_ENGINE_CUDA_CORES) return false;
     return a.engine == DM_ENGINE_TENSOR_CORES || tc_auto(a);
 }
 
-// Points per segment (one FP64 partial each): kTcRun, or longer when the
-// number of partials is capped.
-int64_t tc_seg_rows(const ReduceArgs& a) {
-    const int64_t cap = a.max_blocks > 0 ? a.max_blocks : (int64_t)1 << 20;
-    const int64_t want = (a.n + cap - 1) / cap;
-    return std::max<int64_t>(kTcRun, (want + kTcK - 1) / kTcK * kTcK);
-}
+// Points per chunk of the tensor-core reduce and its raw stages.
+#ifndef DM_RT_KC
+#define DM_RT_KC 64
+#endif
+constexpr int kRtKC = DM_RT_KC;
+constexpr int kRtStages = kRtKC == 32 ? 3 : 2;
 
-cudaError_t reduce_tc_launch(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
-    const int N = (int)((a.k + 15) / 16 * 16);
-    uint32_t cols = 32;
-    while (cols < 2u * (uint32_t)N) cols <<= 1;    // two accumulators
-    const size_t smem = tc_smem_bytes((int)a.d, (int)a.k);
-    cudaError_t e = cudaFuncSetAttribute(reduce_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reduce_tc_kernel, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t seg_rows = tc_seg_rows(a);
-    const int64_t nseg = (a.n + seg_rows - 1) / seg_rows;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, (int64_t)std::max(occ, 1) * sm_count(a.num_sms)));
-    reduce_tc_kernel<<<blocks, kThreads, smem, st>>>(
-        static_cast<const float*>(a.X), a.n, (int)a.d, a.ldx, static_cast<const float*>(a.mu), a.mu_stride,
-        a.with_s ? 1 : 0, static_cast<const float*>(a.Z), (int)a.k, a.ldz, static_cast<double*>(a.partial),
-        nseg, seg_rows, N, cols, rows16(a.X, a.ldx, a.d, 4) ? 1 : 0, rows16(a.Z, a.ldz, a.k, 4) ? 1 : 0, a.err);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int total = (int)((a.d + 2) * a.k);
-    const int warps_per_block = 8;
-    reduce_finalize_kernel<double><<<(total + warps_per_block - 1) / warps_per_block, 32 * warps_per_block,
-                                     0, st>>>(static_cast<const double*>(a.partial), (int)nseg, total,
-                                              static_cast<double*>(a.res), a.err);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *launches += 2;
-    return cudaSuccess;
-}
-
-int reduce_blocks(const ReduceArgs& a) {
-    if (tc_ok(a)) return (int)((a.n + tc_seg_rows(a) - 1) / tc_seg_rows(a));
+// Partials of the CUDA-core reduce: one per CTA, at most 3 per SM, a CTA
+// per 1024 rows at least.  Scratch sized from this count holds the partials
+// of either kernel.
+int reduce_blocks_cc(const ReduceArgs& a) {
     const int sms = sm_count(a.num_sms);
     int64_t cap = 3 * (int64_t)sms;
     if (a.max_blocks > 0) cap = std::min<int64_t>(cap, a.max_blocks);
     const int64_t want = (a.n + 1023) / 1024;
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
+
+uint32_t rt_tmem_cols(int k) {
+    const uint32_t N = 2u * (uint32_t)((k + 7) / 8 * 8);
+    uint32_t cols = 32;
+    while (cols < 2u * N) cols <<= 1;     // two accumulators
+    return cols;
+}
+
+// CTAs of the tensor-core reduce (one partial each): all resident at once,
+// shared memory (227 KB per SM, 1 KB reserved per CTA), TMEM and the
+// register bound of the launch limiting the CTAs per SM; never more than the
+// CUDA-core kernel's count.
+int rt_grid(const ReduceArgs& a) {
+    const RtShape S = rt_shape(kRtKC, kRtStages, (int)a.d, (int)a.k);
+    int per_sm = (int)((227 * 1024) / (S.total + 1024));
+    per_sm = std::min(per_sm, (int)(512 / rt_tmem_cols((int)a.k)));
+    per_sm = std::max(1, std::min(per_sm, rt_min_blocks(kRtKC, (a.k + 7) / 8 * 8 <= 16 ? 16 : 32)));
+    const int64_t chunks = (a.n + kRtKC - 1) / kRtKC;
+    const int64_t g = std::min<int64_t>(chunks, (int64_t)per_sm * sm_count(a.num_sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, reduce_blocks_cc(a)));
+}
+
+cudaError_t reduce_tc_launch(const ReduceArgs& a, cudaStream_t st, int64_t* launches) {
+    const int d = (int)a.d, k = (int)a.k;
+    const RtShape S = rt_shape(kRtKC, kRtStages, d, k);
+    const uint32_t cols = rt_tmem_cols(k);
+    auto kern = S.Kp <= 16 ? reduce_tc_kernel<kRtKC, kRtStages, 16> : reduce_tc_kernel<kRtKC, kRtStages, 32>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    const int blocks = rt_grid(a);
+    kern<<<blocks, kRtT, S.total, st>>>(
+        static_cast<const float*>(a.X), a.n, d, static_cast<const float*>(a.mu), a.mu_stride,
+        a.with_s ? 1 : 0, static_cast<const float*>(a.Z), k, static_cast<double*>(a.partial), cols, a.err,
+        a.spin_limit);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int total = (d + 2) * k;
+    const int warps_per_block = 8;
+    reduce_finalize_kernel<double><<<(total + warps_per_block - 1) / warps_per_block, 32 * warps_per_block,
+                                     0, st>>>(static_cast<const double*>(a.partial), blocks, total,
+                                              static_cast<double*>(a.res), a.err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *launches += 2;
+    return cudaSuccess;
+}
+
+int reduce_blocks(const ReduceArgs& a) { return tc_ok(a) ? rt_grid(a) : reduce_blocks_cc(a); }
 
 int l2prep_blocks(const L2PrepArgs& a) {
     const int sms = sm_count(0);
