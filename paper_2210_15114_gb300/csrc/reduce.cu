@@ -494,16 +494,21 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
 }
 
+// One try_wait on an mbarrier phase: the thread is suspended until the
+// phase completes or a hardware time limit passes, so a waiting warp takes
+// no issue slots.
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
 // Bounded wait on an mbarrier phase with an explicit round limit.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-        __nanosleep(32);
-    }
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try(mbar, parity)) return true;
     return false;
 }
 
@@ -796,13 +801,8 @@ __host__ __device__ inline RtShape rt_shape(int KC, int stages, int d, int k) {
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, uint32_t limit,
                                              volatile uint32_t* abort_w) {
     for (uint32_t i = 0; i < limit; ++i) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
+        if (mbar_try(mbar, parity)) return true;
         if (*abort_w) return false;
-        __nanosleep(32);
     }
     return false;
 }
@@ -844,7 +844,9 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __r
     const int D2 = S.D2, Kp = S.Kp, N = S.N;
     const uint32_t sbo = S.sbo;
     unsigned char* raw = smem_raw + 2 * S.set_bytes;
-    double* acc64 = reinterpret_cast<double*>(smem_raw + S.acc_off);    // [2 D2][N]
+    // FP64 sums, column-major [N][2 D2]: the lanes of a warp (adjacent rows)
+    // touch adjacent words
+    double* acc64 = reinterpret_cast<double*>(smem_raw + S.acc_off);
     float* mu_s = reinterpret_cast<float*>(smem_raw + S.mu_off);        // [d]
     // mbarriers: raw_full[STAGES] (the copies), op_full[2] (the workers'
     // splits), mma_done[2] (the MMAs' commits); then the abort word and the
@@ -940,10 +942,10 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __r
         uint32_t r[KPM];
         auto flush = [&]() {
             if (dwarp && arow < 2 * D2) {
-                double* dst = acc64 + arow * N + hw * Kp;
+                double* dst = acc64 + (hw * Kp) * (2 * D2) + arow;
 #pragma unroll
                 for (int j = 0; j < KPM; ++j)
-                    if (j < Kp) dst[j] += (double)facc[j];
+                    if (j < Kp) dst[j * (2 * D2)] += (double)facc[j];
             }
 #pragma unroll
             for (int j = 0; j < KPM; ++j) facc[j] = 0.f;
@@ -1102,9 +1104,9 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __r
         double* out = partial + (int64_t)blockIdx.x * D2 * k;
         for (int e = tid; e < D2 * k; e += kRtT) {
             const int c = e / k, j = e % k;
-            const double* r0 = acc64 + c * N;
-            const double* r1 = acc64 + (D2 + c) * N;
-            out[e] = (r0[j] + r0[Kp + j]) + (r1[j] + r1[Kp + j]);
+            const double* hi = acc64 + j * (2 * D2);           // column j: products with Z_hi
+            const double* lo = acc64 + (Kp + j) * (2 * D2);    // column Kp + j: with Z_lo
+            out[e] = (hi[c] + lo[c]) + (hi[D2 + c] + lo[D2 + c]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
