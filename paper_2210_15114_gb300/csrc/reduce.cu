@@ -439,23 +439,28 @@ __global__ void mean_finalize_kernel(const typename Types<DT>::Wide* __restrict_
 //   D (TMEM, lane = point, column = query column) = A_hi B_hi + A_hi B_lo
 //      + A_lo B_hi: three MMAs per K step of 8 (FP32 accumulation over at
 //      most 12 products).
-// Operands sit in the canonical K-major layout without swizzle (as in
-// reduce_tc: core matrices of 8 rows x 16 bytes, LBO = 128 bytes along K,
-// SBO = Kp / 4 * 128 bytes between 8-row groups).
-// One CTA (256 threads; threads t and t + 128 share point t of a tile, TMEM
-// lane t, each with half of its coordinates and of its query columns) is
-// persistent over tiles j = blockIdx.x + i gridDim.x.  The raw tiles
-// (128 rows x d floats, contiguous) arrive by bulk copies (cp.async.bulk,
-// completion counted on an mbarrier) kApStages tiles ahead, so that enough
-// bytes are in flight to cover the memory latency; per tile each thread
-// shifts and splits its row into the operand tile and forms
-// s_i = ||x_i - mu||^2, one thread issues the MMAs and commits them to an
-// mbarrier, and every thread reads its row of the accumulator (tcgen05.ld)
-// and writes out_i = s_i u + v - 2 D_i.
-// Every wait is bounded: on expiry the CTA latches DM_ERR_TIMEOUT, waits
-// (bounded) for its own copies and MMAs in flight, frees its TMEM and exits.
+// Operands sit in the canonical K-major layout without swizzle.
+// Each CTA is persistent over tiles j = blockIdx.x + i gridDim.x, in two
+// roles: one thread (warp 8) keeps kApStages raw tiles (128 rows x d
+// floats, contiguous) on their way by bulk copies (cp.async.bulk, completion
+// counted on an mbarrier), and for each tile waits until the workers have
+// filled its operand set, issues its MMAs into accumulator j % 2 and commits
+// them to that set's mbarrier; eight worker warps, per tile, wait for the
+// raw tile and for the MMAs of the tile two back (which read operand set
+// j % 2 and wrote accumulator j % 2), start the TMEM loads of that
+// accumulator, shift and split their rows into the set (threads 2r, 2r + 1
+// share row r) and form s_i = ||x_i - mu||^2 by halves, meet on a named
+// barrier (the row norms of a tile reach the threads that write its out),
+// then write out_i = s_i u + v - 2 D_i of the tile two back (threads t and
+// t + 128 share point t, TMEM lane t, each with half of the query columns)
+// and arrive on the set's mbarrier.
+// Every wait is bounded: on expiry a thread sets the CTA's abort word, which
+// ends every other wait; the CTA latches DM_ERR_TIMEOUT, waits (bounded) for
+// its own copies and MMAs in flight, frees its TMEM and exits.
 constexpr int kApM = 128;
-constexpr int kApT = 256;     // threads: two per point (row) of a tile
+constexpr int kApW = 8;                  // worker warps: two threads per point (row) of a tile
+constexpr int kApWT = 32 * kApW;
+constexpr int kApT = kApWT + 32;         // and one warp that issues the copies and MMAs
 constexpr int kApStages = 2;
 
 // v = hi + lo with hi = v with its 13 low mantissa bits cleared and lo the
@@ -524,198 +529,11 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 size_t apply_tc_smem(int d, int k) {
     const int Kp = (d + 7) / 8 * 8, Np = (k + 15) / 16 * 16;
     return kApStages * (size_t)kApM * d * 4    // raw tiles
-           + 2 * (size_t)kApM * Kp * 4         // operand tile (hi, lo)
+           + 4 * (size_t)kApM * Kp * 4         // two operand sets (hi, lo)
            + 2 * (size_t)Np * Kp * 4           // B (hi, lo)
-           + 4 * (2 * (size_t)Np + Kp) + 128   // mu, u, v, mbarriers, TMEM slot
-           + 2 * (size_t)kApM * 4;             // partial row norms
-}
-
-template <int Kp>
-__global__ void __launch_bounds__(kApT)
-l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ mu,
-                  const double* __restrict__ res, int k, float* __restrict__ out, int64_t ldo,
-                  int Np, uint32_t tmem_cols, int vst, uint32_t* err, uint32_t spin_limit) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t sbo = (uint32_t)(Kp / 4) * 128u;
-    const size_t raw_bytes = (size_t)kApM * d * 4;
-    const size_t a_bytes = (size_t)kApM * Kp * 4, b_bytes = (size_t)Np * Kp * 4;
-    unsigned char* raw = smem_raw;                                     // [kApStages][128][d]
-    unsigned char* ahi = raw + kApStages * raw_bytes;                  // 128 x Kp
-    unsigned char* alo = ahi + a_bytes;
-    unsigned char* bhi = alo + a_bytes;
-    unsigned char* blo = bhi + b_bytes;
-    float* mu_s = reinterpret_cast<float*>(blo + b_bytes);             // [Kp], 16-byte aligned
-    float* u_s = mu_s + Kp;                                            // [Np]
-    float* v_s = u_s + Np;                                             // [Np]
-    float* s_part = v_s + Np;                                          // [2][128]
-    const uintptr_t tail = (reinterpret_cast<uintptr_t>(s_part + 2 * kApM) + 7) & ~uintptr_t(7);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);                // raw_full[kApStages], mma_done
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kApStages + 1);
-    const int row = tid & (kApM - 1), half = tid >> 7;
-
-    // B = W^T split, u, v, mu (zero padded)
-    for (int i = tid; i < Np * Kp; i += kApT) {
-        const int nn = i / Kp, kk = i % Kp;
-        const float w = (nn < k && kk < d) ? (float)res[(int64_t)kk * k + nn] : 0.f;
-        float h, l;
-        split_tf32(w, h, l);
-        const size_t off = (size_t)(nn >> 3) * sbo + (size_t)(kk >> 2) * 128 + (size_t)(nn & 7) * 16 +
-                           (size_t)(kk & 3) * 4;
-        *reinterpret_cast<float*>(bhi + off) = h;
-        *reinterpret_cast<float*>(blo + off) = l;
-    }
-    for (int j = tid; j < Np; j += kApT) {
-        u_s[j] = j < k ? (float)res[(int64_t)d * k + j] : 0.f;
-        v_s[j] = j < k ? (float)res[(int64_t)d * k + k + j] : 0.f;
-    }
-    for (int c = tid; c < Kp; c += kApT) mu_s[c] = c < d ? mu[c] : 0.f;
-    if (tid == 0) {
-        for (int b = 0; b <= kApStages; ++b) mbar_init(smem_u32(mbar + b), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Np >> 3) << 17) |
-                           ((uint32_t)(kApM >> 4) << 24);
-    const uint32_t a_h = smem_u32(ahi), a_l = smem_u32(alo), b_h = smem_u32(bhi), b_l = smem_u32(blo);
-    const uint32_t mma_bar = smem_u32(mbar + kApStages);
-
-    const int64_t tiles = (n + kApM - 1) / kApM;
-    auto tile_rows = [&](int64_t tile) { return (int)min64(kApM, n - tile * kApM); };
-    const int64_t my_tiles = blockIdx.x < tiles ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    auto issue = [&](int64_t i) {   // raw tile i of this CTA into stage i % kApStages
-        const int64_t tile = blockIdx.x + i * gridDim.x;
-        const int st = (int)(i % kApStages);
-        bulk_load(smem_u32(raw + (size_t)st * raw_bytes), X + tile * kApM * d,
-                  (uint32_t)(tile_rows(tile) * d * 4), smem_u32(mbar + st));
-    };
-    if (tid == 0)
-        for (int64_t i = 0; i < kApStages && i < my_tiles; ++i) issue(i);
-    int64_t issued = std::min<int64_t>(kApStages, my_tiles);   // raw tiles requested so far
-    uint32_t raw_phase = 0u, mma_phase = 0u;   // parity of the next completion (bit per stage)
-    bool failed = false, mma_open = false;
-    int64_t raw_open = 0;                       // first raw tile not yet waited for
-
-    for (int64_t i = 0; i < my_tiles; ++i) {
-        const int st = (int)(i % kApStages);
-        const int64_t tile = blockIdx.x + i * gridDim.x;
-        const int rows = tile_rows(tile);
-        // a) the raw tile is in place
-        const bool ok = mbar_wait(smem_u32(mbar + st), (raw_phase >> st) & 1u, spin_limit);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        raw_phase ^= 1u << st;
-        raw_open = i + 1;
-        // b) shift, split and the partial s of one half of a row: threads 2r
-        // and 2r + 1 share row r, so a warp's 16-byte reads of the raw rows and
-        // writes of the operand rows each cover eight distinct bank groups
-        {
-            const int srow = tid >> 1, shalf = tid & 1;
-            const float* xr = reinterpret_cast<const float*>(raw + (size_t)st * raw_bytes) + (size_t)srow * d;
-            const size_t rbase = (size_t)(srow >> 3) * sbo + (size_t)(srow & 7) * 16;
-            constexpr int nq2 = Kp / 8;                   // 16-byte pieces per half
-            const int dq = d / 4;                         // pieces with data
-            float sp = 0.f;
-#pragma unroll
-            for (int qq = 0; qq < nq2; ++qq) {
-                const int q = shalf * nq2 + (srow + qq) % nq2;
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-                if (srow < rows && q < dq) {
-                    const float4 x4 = *reinterpret_cast<const float4*>(xr + 4 * q);
-                    const float4 m4 = *reinterpret_cast<const float4*>(mu_s + 4 * q);
-                    v[0] = x4.x - m4.x;
-                    v[1] = x4.y - m4.y;
-                    v[2] = x4.z - m4.z;
-                    v[3] = x4.w - m4.w;
-                }
-                float h[4], l[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    sp = fmaf(v[e], v[e], sp);
-                    split_tf32(v[e], h[e], l[e]);
-                }
-                const size_t off = rbase + (size_t)q * 128;
-                *reinterpret_cast<float4*>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
-            }
-            s_part[shalf * kApM + srow] = sp;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();   // operand tile written, raw stage st read by every thread
-        if (tid == 0) {
-            // c) the raw tile kApStages ahead into the stage just read
-            if (issued < my_tiles) issue(issued);
-            // d) the MMAs of this tile
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int ks = 0; ks < Kp / 8; ++ks) {
-                const uint32_t o = (uint32_t)ks * 256u;
-                const uint64_t dah = tc_desc_sbo(a_h + o, sbo), dal = tc_desc_sbo(a_l + o, sbo);
-                const uint64_t dbh = tc_desc_sbo(b_h + o, sbo), dbl = tc_desc_sbo(b_l + o, sbo);
-                tc_mma(tmem, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                tc_mma(tmem, dah, dbl, idesc, 1u);
-                tc_mma(tmem, dal, dbh, idesc, 1u);
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(mma_bar) : "memory");
-        }
-        if (issued < my_tiles) ++issued;
-        // e) the accumulator -> out
-        const bool mok = mbar_wait(mma_bar, mma_phase, spin_limit);
-        if (__syncthreads_or(!mok)) { failed = true; mma_open = true; break; }
-        mma_phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows), the columns of
-        // half w / 4 of the padded width
-        const float s_row = s_part[row] + s_part[kApM + row];
-        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        const int jh = Np / 2;
-        for (int j0 = half * jh; j0 < (half + 1) * jh; j0 += 8) {
-            float dv[8];
-            tc_ld8(lane_base + (uint32_t)j0, dv);
-            if (row < rows) {
-                float o[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) o[q] = fmaf(s_row, u_s[j0 + q], v_s[j0 + q]) - 2.f * dv[q];
-                float* dst = out + (tile * kApM + row) * ldo + j0;
-                if (vst && j0 + 8 <= k) {
-                    *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-                    *reinterpret_cast<float4*>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (j0 + q < k) dst[q] = o[q];
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    }
-    if (failed) {
-        if (err) set_error(err, kErrTimeout);
-        // no copy or MMA of this CTA may still target its shared memory or
-        // TMEM when they are released: raw tiles raw_open .. issued - 1 are
-        // still on their way (each in its own stage), and maybe the MMAs
-        for (int64_t j = raw_open; j < issued; ++j) {
-            const int st = (int)(j % kApStages);
-            mbar_wait(smem_u32(mbar + st), (raw_phase >> st) & 1u, spin_limit);
-        }
-        if (mma_open) mbar_wait(mma_bar, mma_phase, spin_limit);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
-    }
+           + 4 * (2 * (size_t)Np + Kp)         // mu, u, v
+           + 8 * (size_t)kApM * 4              // partial row norms of four tiles
+           + 8 * (kApStages + 4) + 32;         // mbarriers, abort word, TMEM slot, alignment
 }
 
 // --------------------------------------------------- reduce on tensor cores
@@ -1112,6 +930,244 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __r
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == kRtW) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// ------------------------------------------- l2apply on tensor cores: kernel
+template <int Kp>
+__global__ void __launch_bounds__(kApT, 2)
+l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ mu,
+                  const double* __restrict__ res, int k, float* __restrict__ out, int64_t ldo,
+                  int Np, uint32_t tmem_cols, int vst, uint32_t* err, uint32_t spin_limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sbo = (uint32_t)(Kp / 4) * 128u;
+    const size_t raw_bytes = (size_t)kApM * d * 4;
+    const size_t a_bytes = (size_t)kApM * Kp * 4, b_bytes = (size_t)Np * Kp * 4;
+    unsigned char* raw = smem_raw;                                     // [kApStages][128][d]
+    unsigned char* aset = raw + kApStages * raw_bytes;                 // [2] x (hi, lo): 128 x Kp each
+    unsigned char* bhi = aset + 4 * a_bytes;
+    unsigned char* blo = bhi + b_bytes;
+    float* mu_s = reinterpret_cast<float*>(blo + b_bytes);             // [Kp], 16-byte aligned
+    float* u_s = mu_s + Kp;                                            // [Np]
+    float* v_s = u_s + Np;                                             // [Np]
+    float* s_part = v_s + Np;                                          // [4 tiles][2 halves][128]
+    const uintptr_t tail = (reinterpret_cast<uintptr_t>(s_part + 8 * kApM) + 7) & ~uintptr_t(7);
+    // mbarriers raw_full[kApStages], op_full[2], mma_done[2]; the abort word;
+    // the TMEM address
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
+    uint64_t* raw_full = mbar;
+    uint64_t* op_full = mbar + kApStages;
+    uint64_t* mma_done = mbar + kApStages + 2;
+    volatile uint32_t* abort_w = reinterpret_cast<volatile uint32_t*>(mbar + kApStages + 4);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kApStages + 4) + 1;
+
+    // B = W^T split, u, v, mu (zero padded)
+    for (int i = tid; i < Np * Kp; i += kApT) {
+        const int nn = i / Kp, kk = i % Kp;
+        const float w = (nn < k && kk < d) ? (float)res[(int64_t)kk * k + nn] : 0.f;
+        float h, l;
+        split_tf32(w, h, l);
+        const size_t off = (size_t)(nn >> 3) * sbo + (size_t)(kk >> 2) * 128 + (size_t)(nn & 7) * 16 +
+                           (size_t)(kk & 3) * 4;
+        *reinterpret_cast<float*>(bhi + off) = h;
+        *reinterpret_cast<float*>(blo + off) = l;
+    }
+    for (int j = tid; j < Np; j += kApT) {
+        u_s[j] = j < k ? (float)res[(int64_t)d * k + j] : 0.f;
+        v_s[j] = j < k ? (float)res[(int64_t)d * k + k + j] : 0.f;
+    }
+    for (int c = tid; c < Kp; c += kApT) mu_s[c] = c < d ? mu[c] : 0.f;
+    if (tid == 0) {
+        for (int b = 0; b < kApStages; ++b) mbar_init(smem_u32(raw_full + b), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(op_full + b), kApWT);
+            mbar_init(smem_u32(mma_done + b), 1);
+        }
+        *abort_w = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kApW) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    const int64_t tiles = (n + kApM - 1) / kApM;
+    auto tile_rows = [&](int64_t tile) { return (int)min64(kApM, n - tile * kApM); };
+    const int64_t my_tiles = blockIdx.x < tiles ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+    if (warp < kApW) {
+        // ---------------------------------------------------------- workers
+        const int row = tid & (kApM - 1), half = tid >> 7;   // epilogue: TMEM lane, column half
+        const int srow = tid >> 1, shalf = tid & 1;          // split: row, coordinate half
+        const int jh = Np / 2;
+        uint32_t r[16];
+        // TMEM loads of accumulator b (its MMAs are complete): this thread's
+        // row, its half of the columns
+        auto acc_issue = [&](int b) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * Np + half * jh);
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                if (t * 8 < jh) tc_ld8_issue(ta + (uint32_t)(8 * t), r + 8 * t);
+        };
+        // out for tile j from the loaded accumulator and its row norms
+        auto epilogue = [&](int64_t j) {
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int64_t tile = blockIdx.x + j * gridDim.x;
+            const int rows = tile_rows(tile);
+            const float* sp = s_part + (int)(j & 3) * 2 * kApM;
+            const float s_row = sp[row] + sp[kApM + row];
+            if (row < rows) {
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (t * 8 >= jh) continue;
+                    const int j0 = half * jh + 8 * t;
+                    float o[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        o[q] = fmaf(s_row, u_s[j0 + q], v_s[j0 + q]) - 2.f * __uint_as_float(r[8 * t + q]);
+                    float* dst = out + (tile * kApM + row) * ldo + j0;
+                    if (vst && j0 + 8 <= k) {
+                        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+                        *reinterpret_cast<float4*>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (j0 + q < k) dst[q] = o[q];
+                    }
+                }
+            }
+        };
+        bool ok = true;
+        for (int64_t i = 0; i < my_tiles; ++i) {
+            const int st = (int)(i % kApStages), ob = (int)(i & 1);
+            const int64_t tile = blockIdx.x + i * gridDim.x;
+            const int rows = tile_rows(tile);
+            // the raw tile is in place, and operand set ob and accumulator ob
+            // are free once the MMAs of tile i - 2 are done (whose out is
+            // written around this tile's split); a warp agrees on the outcome
+            ok = mbar_wait_ab(smem_u32(raw_full + st), (uint32_t)(i / kApStages) & 1u, spin_limit, abort_w);
+            if (ok && i >= 2)
+                ok = mbar_wait_ab(smem_u32(mma_done + ob), (uint32_t)((i - 2) >> 1) & 1u, spin_limit, abort_w);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            if (i >= 2) acc_issue(ob);
+            // shift, split and the partial s of one half of a row: threads 2r
+            // and 2r + 1 share row r, so a warp's 16-byte reads of the raw rows
+            // and writes of the operand rows each cover eight distinct bank groups
+            {
+                unsigned char* ahi = aset + (size_t)ob * 2 * a_bytes;
+                unsigned char* alo = ahi + a_bytes;
+                const float* xr = reinterpret_cast<const float*>(raw + (size_t)st * raw_bytes) + (size_t)srow * d;
+                const size_t rbase = (size_t)(srow >> 3) * sbo + (size_t)(srow & 7) * 16;
+                constexpr int nq2 = Kp / 8;                   // 16-byte pieces per half
+                const int dq = d / 4;                         // pieces with data
+                float sp = 0.f;
+#pragma unroll
+                for (int qq = 0; qq < nq2; ++qq) {
+                    const int q = shalf * nq2 + (srow + qq) % nq2;
+                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (srow < rows && q < dq) {
+                        const float4 x4 = *reinterpret_cast<const float4*>(xr + 4 * q);
+                        const float4 m4 = *reinterpret_cast<const float4*>(mu_s + 4 * q);
+                        v[0] = x4.x - m4.x;
+                        v[1] = x4.y - m4.y;
+                        v[2] = x4.z - m4.z;
+                        v[3] = x4.w - m4.w;
+                    }
+                    float h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        sp = fmaf(v[e], v[e], sp);
+                        split_tf32(v[e], h[e], l[e]);
+                    }
+                    const size_t off = rbase + (size_t)q * 128;
+                    *reinterpret_cast<float4*>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
+                }
+                s_part[(int)(i & 3) * 2 * kApM + shalf * kApM + srow] = sp;
+            }
+            // the workers' row norms of this tile are visible to every worker
+            // before its out is written (two tiles later)
+            asm volatile("bar.sync 1, %0;" :: "n"(kApWT) : "memory");
+            if (i >= 2) epilogue(i - 2);
+            // set ob written, raw stage st read, accumulator ob read
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(op_full + ob)) : "memory");
+        }
+        // the last two tiles
+        for (int64_t j = my_tiles >= 2 ? my_tiles - 2 : 0; ok && j < my_tiles; ++j) {
+            const int b = (int)(j & 1);
+            ok = mbar_wait_ab(smem_u32(mma_done + b), (uint32_t)(j >> 1) & 1u, spin_limit, abort_w);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            acc_issue(b);
+            epilogue(j);
+        }
+        if (!ok) *abort_w = 1u;
+    } else if ((tid & 31) == 0) {
+        // ---------------------------------- copies and MMAs (one thread)
+        auto issue = [&](int64_t i) {   // raw tile i of this CTA into stage i % kApStages
+            const int64_t tile = blockIdx.x + i * gridDim.x;
+            const int st = (int)(i % kApStages);
+            bulk_load(smem_u32(raw + (size_t)st * raw_bytes), X + tile * kApM * d,
+                      (uint32_t)(tile_rows(tile) * d * 4), smem_u32(raw_full + st));
+        };
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Np >> 3) << 17) |
+                               ((uint32_t)(kApM >> 4) << 24);
+        // descriptors of set 0's first K step (hi, lo) and of B; set 1 and
+        // each K step (256 bytes) add to the address field (16-byte units)
+        const uint64_t dah = tc_desc_sbo(smem_u32(aset), sbo), dal = tc_desc_sbo(smem_u32(aset) + (uint32_t)a_bytes, sbo);
+        const uint64_t dbh = tc_desc_sbo(smem_u32(bhi), sbo), dbl = tc_desc_sbo(smem_u32(blo), sbo);
+        const uint64_t set_step = (uint64_t)((2 * a_bytes) >> 4);
+        int64_t issued = 0, committed = 0;
+        for (; issued < kApStages && issued < my_tiles; ++issued) issue(issued);
+        for (int64_t i = 0; i < my_tiles; ++i) {
+            const int ob = (int)(i & 1);
+            if (!mbar_wait_ab(smem_u32(op_full + ob), (uint32_t)(i >> 1) & 1u, spin_limit, abort_w)) {
+                *abort_w = 1u;
+                break;
+            }
+            // raw stage i % kApStages has been read: the tile kApStages ahead
+            if (issued < my_tiles) issue(issued++);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t so = ob ? set_step : 0u;
+            const uint32_t dcol = tmem + (uint32_t)(ob * Np);
+#pragma unroll
+            for (int ks = 0; ks < Kp / 8; ++ks) {
+                const uint64_t o = 16u * ks;
+                tc_mma(dcol, dah + so + o, dbh + o, idesc, ks > 0 ? 1u : 0u);
+                tc_mma(dcol, dah + so + o, dbl + o, idesc, 1u);
+                tc_mma(dcol, dal + so + o, dbh + o, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(mma_done + ob)) : "memory");
+            committed = i + 1;
+        }
+        if (*abort_w) {
+            // no copy or MMA of this CTA may still target its shared memory
+            // or TMEM when they are released
+            for (int64_t j = issued - 1; j >= 0 && j >= issued - kApStages; --j)
+                mbar_wait(smem_u32(raw_full + (int)(j % kApStages)), (uint32_t)(j / kApStages) & 1u, spin_limit);
+            for (int64_t j = committed - 1; j >= 0 && j >= committed - 2; --j)
+                mbar_wait(smem_u32(mma_done + (int)(j & 1)), (uint32_t)(j >> 1) & 1u, spin_limit);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && *abort_w && err) set_error(err, kErrTimeout);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == kApW) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tmem_cols) : "memory");
     }
@@ -1687,7 +1743,7 @@ cudaError_t l2apply_tc_launch(const L2ApplyArgs& a, cudaStream_t st, int64_t* la
     // CTAs per SM: shared memory (227 KB usable, 1 KB reserved per CTA) and
     // TMEM (every resident CTA holds `cols` of the SM's 512 columns) bound it
     int occ = (int)((227 * 1024) / (smem + 1024));
-    occ = std::max(1, std::min(occ, std::min(2048 / kApT, (int)(512 / cols))));
+    occ = std::max(1, std::min(occ, std::min(2, (int)(512 / cols))));   // 2: the launch's register bound
     const int64_t tiles = (a.n + kApM - 1) / kApM;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)occ * num_sms));
     const bool vst = a.k % 4 == 0 && a.ldo % 4 == 0 && reinterpret_cast<uintptr_t>(a.out) % 16 == 0;
