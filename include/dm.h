@@ -107,9 +107,8 @@ dm_status dm_set_deterministic(dm_ctx* ctx, int on);
  *     kernels.
  *   DM_ENGINE_CUDA_CORES: always the CUDA-core kernels.
  *   DM_ENGINE_AUTO (the default): the tensor cores where they measured at
- *     least as fast: the apply when k >= 16 and d k >= 512; the reduce never
- *     (its output has d + 2 rows, while a tcgen05 tile has 128, so most of
- *     every MMA is padding).
+ *     least as fast: the apply when k >= 16 and d k >= 512; the reduce when
+ *     k <= 16 or d >= 48.
  * Results agree with the FP64 oracle within the FP32 tolerance either way;
  * the bits differ between engines. */
 typedef enum { DM_ENGINE_AUTO = 0, DM_ENGINE_CUDA_CORES = 1, DM_ENGINE_TENSOR_CORES = 2 } dm_engine;
