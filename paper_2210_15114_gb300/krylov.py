@@ -15,10 +15,11 @@ steps touches A.
 
 For symmetric A the Krylov space of the iteration is spanned by powers of A:
 Q_1 = orth(A Pi); W = A Q_i; Q_{i+1} = orth(W minus its projections on
-Q_1..Q_i), the projections removed twice before and twice after an
-orthonormalization (a low-rank A makes late blocks rounding noise, whose
-normalized directions must be projected out again; one pass each leaves
-the basis far from orthonormal in FP32).  Orthonormalization is
+Q_1..Q_i), the projections removed twice before an orthonormalization and
+then checked: the coefficients Q^T W of the orthonormalized block are formed
+once more, and where one exceeds _REORTH_TOL (a low-rank A makes late blocks
+rounding noise, whose normalized directions lie largely in the span of the
+basis) they are removed and the block is orthonormalized again.  Orthonormalization is
 Cholesky QR applied twice (Gram matrix W^T W, its Cholesky factor R in
 FP64, W R^-1): two skinny matrix products instead of a Householder QR of a
 tall block.  A numerically rank-deficient block (A of rank below the Krylov
@@ -42,6 +43,10 @@ from . import binding
 # ratios near 1e-6) mark the block as rank deficient.
 _RANK_TOL = 1e-5
 _SPREAD = 1e3
+# Cosine between an orthonormalized block and the basis above which the
+# block is projected and orthonormalized once more (FP32 Cholesky QR leaves
+# cosines near 1e-7 when the block is well resolved).
+_REORTH_TOL = 1e-5
 _FILL_SEED = 0x5EED
 
 
@@ -83,9 +88,13 @@ def block_krylov(plan, Pi: torch.Tensor, q: int, rank: int):
     W = binding.dm_matmat(plan, Pi.contiguous())
     for i in range(q):
         prev = Q[:, : i * k]
-        for _ in range(2):
-            W = _project_out(ctx, W, prev)
-            W = _orthonormalize(ctx, W, prev, gen)
+        W = _project_out(ctx, W, prev)
+        W = _orthonormalize(ctx, W, prev, gen)
+        if prev.shape[1]:
+            C = _tn(ctx, prev, W)
+            if float(C.abs().max()) > _REORTH_TOL:
+                W = _nn(ctx, prev, C, out=W, alpha=-1.0, beta=1.0)
+                W = _orthonormalize(ctx, W, prev, gen)
         Q[:, i * k:(i + 1) * k] = W
         binding.dm_matmat(plan, Q[:, i * k:(i + 1) * k], out=AQ[:, i * k:(i + 1) * k])
         W = AQ[:, i * k:(i + 1) * k].clone()
@@ -154,4 +163,4 @@ def _orthonormalize(ctx, W: torch.Tensor, prev: torch.Tensor, gen: torch.Generat
     fill /= W.shape[0] ** 0.5
     Wf = _project_out(ctx, torch.cat([good, fill], dim=1), prev)
     Q = _cholqr2(ctx, Wf)
-    return Q if Q is not None else torch.linalg.qr(Wf).Q
+    return Q if Q is not None else torch.linalg.qr(Wf).Q.contiguous()
