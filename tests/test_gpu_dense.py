@@ -84,3 +84,23 @@ def test_dense_rejects(dm, ctx):
         dm.dm_dense_nn(ctx, A, torch.zeros((3, 65), device="cuda"))       # k > 64
     with pytest.raises(dm.DMError):
         dm.dm_dense_tn(ctx, A.double(), A.double())                         # FP32 only
+
+
+@pytest.mark.parametrize("n", [1, 129, 100003])
+@pytest.mark.parametrize("m", [1, 5, 17, 33, 280])
+@pytest.mark.parametrize("k", [1, 3, 40, 64])
+def test_dense_nn_ragged_strided_rows(dm, ctx, n, m, k):
+    # A as the first m columns of a block whose width is a multiple of 4
+    # (16-byte aligned rows at a leading dimension above m): chunks of A's
+    # columns cut off at m, tiles of rows cut off at n
+    rng = np.random.default_rng(n + 7 * m + 31 * k)
+    width = m + (-m) % 4
+    Aw = rng.normal(size=(n, width)).astype(np.float32)
+    T = rng.normal(size=(m, k)).astype(np.float32)
+    C0 = rng.normal(size=(n, k)).astype(np.float32)
+    Ad = torch.from_numpy(Aw).cuda()[:, :m]
+    out = torch.from_numpy(C0.copy()).cuda()
+    dm.dm_dense_nn(ctx, Ad, torch.from_numpy(T).cuda(), out=out, alpha=-0.5, beta=2.0)
+    dm.dm_sync(ctx)
+    want = 2.0 * C0.astype(np.float64) - 0.5 * Aw[:, :m].astype(np.float64) @ T.astype(np.float64)
+    assert rel(out.cpu().numpy(), want) <= 1e-5
