@@ -795,29 +795,62 @@ def main():
     err["l1"] = oracle.relative_error(got1[rows], oracle.l1_rows(X, Z, rows))
     err["l2sq"] = oracle.relative_error(got2[rows], oracle.l2sq_rows(X, Z, rows))
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: the two products of
+    # the step as two dm_matmat_host calls, each on a context of its own and
+    # issued from its own host thread, so that one call's copies overlap the
+    # other's kernels (the sequential form is reported beside it)
     e2e = None
     if not a.no_e2e:
+        import threading
         Xh = torch.from_numpy(X).pin_memory().numpy()
         Zh = torch.from_numpy(Z).pin_memory().numpy()
         out_h = torch.empty((a.n, a.k), dtype=torch.float32).pin_memory().numpy()
-        for _ in range(2):
+        out_h2 = torch.empty((a.n, a.k), dtype=torch.float32).pin_memory().numpy()
+        stream2 = torch.cuda.Stream(device=dev)
+        ctx2 = dm.dm_create(local, stream2.cuda_stream)
+
+        def concurrent_step():
+            failure = []
+
+            def second():
+                try:
+                    dm.dm_matmat_host(ctx2, "l2sq", Xh, Zh, out_h2)
+                except Exception as exc:      # re-raised on the calling thread
+                    failure.append(exc)
+            t = threading.Thread(target=second)
+            t.start()
             dm.dm_matmat_host(ctx, "l1", Xh, Zh, out_h)
-            dm.dm_matmat_host(ctx, "l2sq", Xh, Zh, out_h)
-        e_ms = []
-        for _ in range(min(10, max(3, a.steps // 2))):
-            flush.zero_()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
+            t.join()
+            if failure:
+                raise failure[0]
+
+        def sequential_step():
             dm.dm_matmat_host(ctx, "l1", Xh, Zh, out_h)
-            dm.dm_matmat_host(ctx, "l2sq", Xh, Zh, out_h)
-            e.record(stream)
-            e.synchronize()
-            e_ms.append(s.elapsed_time(e))
-        em = statistics.mean(e_ms)
+            dm.dm_matmat_host(ctx, "l2sq", Xh, Zh, out_h2)
+
+        def timed(step_fn):
+            for _ in range(2):
+                step_fn()
+            ms_list = []
+            for _ in range(min(10, max(3, a.steps // 2))):
+                flush.zero_()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                step_fn()
+                e.record(stream)
+                e.synchronize()
+                ms_list.append(s.elapsed_time(e))
+            return statistics.mean(ms_list)
+
+        em = timed(concurrent_step)
+        em_seq = timed(sequential_step)
         e2e = {"value": units_step / (em / 1e3), "unit": UNIT, "ms_per_step": em,
                "h2d_bytes_per_step": 2 * (X.nbytes + Z.nbytes),
-               "d2h_bytes_per_step": 2 * out_h.nbytes}
+               "d2h_bytes_per_step": out_h.nbytes + out_h2.nbytes,
+               "calls": "two dm_matmat_host calls (l1, squared l2) on two contexts from two host threads",
+               "sequential_ms_per_step": em_seq,
+               "sequential_value": units_step / (em_seq / 1e3)}
+        dm.dm_destroy(ctx2)
 
     cpu = None
     if not a.no_cpu and world == 1:
