@@ -431,9 +431,9 @@ def ctx_tensor(dm):
 @pytest.mark.parametrize("n,d,k", [(1, 1, 1), (63, 3, 5), (1000, 8, 16), (3001, 32, 17),
                                    (2048, 126, 16), (70001, 16, 40), (5000, 30, 64)])
 def test_l2sq_tensor_engine(dm, ctx_tensor, n, d, k):
-    # tcgen05 contraction (TF32 hi + lo split) where the shape allows it --
-    # ragged n (partial chunks), k not a multiple of 16, d + 2 = 128 -- and the
-    # CUDA-core kernel for k = 64 (two operand sets no longer fit)
+    # the tensor engine at shapes its kernels partly refuse: k not a multiple
+    # of 4 or above 32, d + 2 = 128 (the CUDA-core reduce then takes over),
+    # ragged n
     rng = np.random.default_rng(n + d + k)
     X = rng.normal(0, 3, size=(n, d)).astype(np.float32)
     Z = rng.normal(size=(n, k)).astype(np.float32)
@@ -455,6 +455,47 @@ def test_l2sq_tensor_apply_shapes(dm, ctx_tensor, n, d, k):
     out = gpu_product(dm, ctx_tensor, "l2sq", X, Z)
     want = oracle.l2sq_identity(X, Z) if n > 1 else oracle.l2sq_rows(X, Z)
     assert oracle.relative_error(out, want) <= 1e-5
+
+
+@pytest.mark.parametrize("n,d,k", [(1, 4, 4), (63, 8, 8), (64, 12, 16), (65, 28, 12), (1000, 32, 4),
+                                   (4097, 32, 32), (70001, 16, 20), (3000, 44, 16), (2500, 60, 32),
+                                   (129, 60, 4), (100003, 32, 16)])
+def test_l2sq_tensor_reduce_shapes(dm, ctx, n, d, k):
+    # the tensor-core reduce (the default engine for these shapes: d and k
+    # multiples of 4, d <= 60, k <= 16 or d >= 48, and the tensor engine
+    # beyond): 64-point chunks cut off at n, 2 (d + 2) rows of hi and lo
+    # packed into the 128-row tile, k rounded up to 8; points shifted far from
+    # the origin (the centring) -- whole block against the p = 2 identity,
+    # under the default engine and under DM_ENGINE_TENSOR_CORES
+    rng = np.random.default_rng(11 * n + d + k)
+    X = (rng.normal(0, 3, size=(n, d)) + 50.0).astype(np.float32)
+    Z = rng.normal(size=(n, k)).astype(np.float32)
+    want = oracle.l2sq_identity(X, Z) if n > 1 else oracle.l2sq_rows(X, Z)
+    for c in (ctx, dm.dm_create(0)):
+        if c is not ctx:
+            dm.dm_set_engine(c, "tensor")
+        out = gpu_product(dm, c, "l2sq", X, Z)
+        assert oracle.relative_error(out, want) <= 1e-5
+
+
+def test_l2sq_tensor_reduce_without_norms(dm, ctx):
+    # the reduce without the s row (the squared-l2 gradient packs (z, w) as
+    # 2k columns; k = 2 and 8 give 4 and 16 packed columns) and with
+    # precomputed features and no shift (even p: d p = 16 columns)
+    rng = np.random.default_rng(23)
+    n, d = 5003, 8
+    X = rng.normal(size=(n, d)).astype(np.float32)
+    plan = dm.dm_prepare(ctx, "l2sq", dev(X))
+    for k in (2, 8):
+        W = rng.normal(size=(n, k)).astype(np.float32)
+        Z = rng.normal(size=(n, k)).astype(np.float32)
+        G = dm.dm_grad(plan, dev(W), dev(Z)).cpu().numpy()
+        assert oracle.relative_error(G, oracle.l2sq_grad_closed(X, W, Z)) <= 1e-5
+    X4 = rng.normal(size=(n, 4)).astype(np.float32)
+    Z4 = rng.normal(size=(n, 4)).astype(np.float32)
+    out = dm.dm_matmat(dm.dm_prepare_lpp(ctx, dev(X4), 4), dev(Z4)).cpu().numpy()
+    assert oracle.relative_error(out, oracle.lpp_even_expansion(X4, Z4, 4)) <= 1e-5
+    dm.dm_sync(ctx)
 
 
 def test_l2sq_tensor_apply_strided_points_fall_back(dm, ctx_tensor):
