@@ -617,6 +617,7 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __r
     const int64_t C = (n + KC - 1) / KC;
     const int64_t c0 = C * blockIdx.x / gridDim.x, c1 = C * (blockIdx.x + 1) / gridDim.x;
     const int64_t my = c1 - c0;
+    int64_t issued = 0, committed = 0;   // the copy/MMA thread's chunks in flight
 
     if (warp < kRtW) {
         // ---------------------------------------------------------- workers
@@ -792,7 +793,6 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __r
         // stay below 2^18, so the field does not carry)
         const uint64_t da0 = tc_desc_sbo(smem_u32(smem_raw), sbo);
         const uint64_t db0 = tc_desc_sbo(smem_u32(smem_raw) + S.b_off, sbo);
-        int64_t issued = 0, committed = 0;
         for (; issued < STAGES && issued < my; ++issued) issue(issued);
         for (int64_t i = 0; i < my; ++i) {
             const int ob = (int)(i & 1);
@@ -812,19 +812,21 @@ reduce_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __r
                          :: "r"(smem_u32(mma_done + ob)) : "memory");
             committed = i + 1;
         }
-        if (*abort_w) {
-            // no copy or MMA of this CTA may still target its shared memory
-            // or TMEM when they are released: the last copy into each stage
-            // and the last commit to each set
-            for (int64_t j = issued - 1; j >= 0 && j >= issued - STAGES; --j)
-                mbar_wait(smem_u32(raw_full + (int)(j % STAGES)), (uint32_t)(j / STAGES) & 1u, spin_limit);
-            for (int64_t j = committed - 1; j >= 0 && j >= committed - 2; --j)
-                mbar_wait(smem_u32(mma_done + (int)(j & 1)), (uint32_t)(j >> 1) & 1u, spin_limit);
-        }
     }
     __syncthreads();
     if (*abort_w) {
         if (tid == 0 && err) set_error(err, kErrTimeout);
+        // no copy or MMA of this CTA may still target its shared memory or
+        // TMEM when they are released: the copy/MMA thread waits for the last
+        // copy into each stage and the last commit to each set (operations
+        // that complete by themselves: the long limit, whatever the
+        // configured one)
+        if (tid == kRtWT) {
+            for (int64_t j = issued - 1; j >= 0 && j >= issued - STAGES; --j)
+                mbar_wait(smem_u32(raw_full + (int)(j % STAGES)), (uint32_t)(j / STAGES) & 1u, kSpinLimit);
+            for (int64_t j = committed - 1; j >= 0 && j >= committed - 2; --j)
+                mbar_wait(smem_u32(mma_done + (int)(j & 1)), (uint32_t)(j >> 1) & 1u, kSpinLimit);
+        }
     } else {
         double* out = partial + (int64_t)blockIdx.x * D2 * k;
         for (int e = tid; e < D2 * k; e += kRtT) {
@@ -910,6 +912,7 @@ l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __
     const int64_t tiles = (n + kApM - 1) / kApM;
     auto tile_rows = [&](int64_t tile) { return (int)min64(kApM, n - tile * kApM); };
     const int64_t my_tiles = blockIdx.x < tiles ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    int64_t issued = 0, committed = 0;   // the copy/MMA thread's tiles in flight
 
     if (warp < kApW) {
         // ---------------------------------------------------------- workers
@@ -1037,7 +1040,6 @@ l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __
         const uint64_t dah = tc_desc_sbo(smem_u32(aset), sbo), dal = tc_desc_sbo(smem_u32(aset) + (uint32_t)a_bytes, sbo);
         const uint64_t dbh = tc_desc_sbo(smem_u32(bhi), sbo), dbl = tc_desc_sbo(smem_u32(blo), sbo);
         const uint64_t set_step = (uint64_t)((2 * a_bytes) >> 4);
-        int64_t issued = 0, committed = 0;
         for (; issued < kApStages && issued < my_tiles; ++issued) issue(issued);
         for (int64_t i = 0; i < my_tiles; ++i) {
             const int ob = (int)(i & 1);
@@ -1061,17 +1063,20 @@ l2apply_tc_kernel(const float* __restrict__ X, int64_t n, int d, const float* __
                          :: "r"(smem_u32(mma_done + ob)) : "memory");
             committed = i + 1;
         }
-        if (*abort_w) {
-            // no copy or MMA of this CTA may still target its shared memory
-            // or TMEM when they are released
-            for (int64_t j = issued - 1; j >= 0 && j >= issued - kApStages; --j)
-                mbar_wait(smem_u32(raw_full + (int)(j % kApStages)), (uint32_t)(j / kApStages) & 1u, spin_limit);
-            for (int64_t j = committed - 1; j >= 0 && j >= committed - 2; --j)
-                mbar_wait(smem_u32(mma_done + (int)(j & 1)), (uint32_t)(j >> 1) & 1u, spin_limit);
-        }
     }
     __syncthreads();
-    if (tid == 0 && *abort_w && err) set_error(err, kErrTimeout);
+    if (*abort_w) {
+        if (tid == 0 && err) set_error(err, kErrTimeout);
+        // no copy or MMA of this CTA may still target its shared memory or
+        // TMEM when they are released (the long limit: these complete by
+        // themselves)
+        if (tid == kApWT) {
+            for (int64_t j = issued - 1; j >= 0 && j >= issued - kApStages; --j)
+                mbar_wait(smem_u32(raw_full + (int)(j % kApStages)), (uint32_t)(j / kApStages) & 1u, kSpinLimit);
+            for (int64_t j = committed - 1; j >= 0 && j >= committed - 2; --j)
+                mbar_wait(smem_u32(mma_done + (int)(j & 1)), (uint32_t)(j >> 1) & 1u, kSpinLimit);
+        }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == kApW) {

@@ -9,6 +9,11 @@ device-side wait (through the C ABI).
   (the decoupled look-back of Algorithm 1's sort) gives up after the
   context's wait limit, dm_sync reports DM_ERR_TIMEOUT, and the same context
   then computes a correct product.
+* The tensor-core squared-l2 kernels (two roles meeting on mbarriers) with a
+  wait limit of one round: every call either reports DM_ERR_TIMEOUT (a
+  role's wait ran out, the CTA drained its own copies and MMAs and freed its
+  tensor memory) or returns a correct product; the context then computes
+  correct products at the default limit.
 """
 import os
 import subprocess
@@ -100,3 +105,29 @@ def test_wait_limit_argument_checks(dm):
     lib = dm.load()
     assert lib.dm_set_wait_limit(None, 5) == dm.DM_ERR_INVALID_ARG
     assert lib.dm_test_unpublished_wait(None) == dm.DM_ERR_INVALID_ARG
+
+
+def test_tensor_core_kernels_give_up_cleanly(dm):
+    ctx = dm.dm_create(0)
+    X, Z = inputs.workload_mixture_f32(n=300007, d=32, k=16)
+    Xd, Zd = torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda()
+    want = oracle.l2sq_identity(X, Z)
+    plan = dm.dm_prepare(ctx, "l2sq", Xd)
+    dm.dm_sync(ctx)
+    dm.dm_set_wait_limit(ctx, 1)
+    outcomes = []
+    for _ in range(5):
+        out = dm.dm_matmat(plan, Zd)
+        try:
+            dm.dm_sync(ctx)
+            outcomes.append("ok")
+            assert oracle.relative_error(out.cpu().numpy(), want) <= 1e-5
+        except dm.DMError as e:
+            assert e.status == dm.DM_ERR_TIMEOUT
+            outcomes.append("timeout")
+    dm.dm_set_wait_limit(ctx, 0)
+    for _ in range(2):
+        out = dm.dm_matmat(plan, Zd)
+        dm.dm_sync(ctx)
+        assert oracle.relative_error(out.cpu().numpy(), want) <= 1e-5
+    print("outcomes at a one-round wait limit:", outcomes)
