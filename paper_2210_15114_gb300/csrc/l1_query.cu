@@ -26,15 +26,18 @@
 //   outg[g], n*KC elements each (32 + 32 MiB at n = 2^20) -- stays resident
 //   in L2 while the sorted columns stream past it.  Work unit: a tile of
 //   TILE_E consecutive sorted positions of one coordinate of one group,
-//   claimed from an atomic counter by persistent CTAs.  Per tile:
+//   claimed by one warp from an atomic counter (persistent CTAs whose warps
+//   never wait on one another) and walked in 8 sub-tiles of SUB_E positions.
+//   Per sub-tile:
 //   A. each thread takes SEG_LEN consecutive positions: x - b (b = the tile's
 //      first sorted value), the checked permutation and the gathered QW-wide
 //      slices of the rows Zg[g][perm[r]];
 //   B. in-tile exclusive prefix sums Lz, Lxz of z and (x - b) z (FP32 for
-//      FP32 data): in-thread, then across the warp by shuffles, then across
-//      the warps through shared totals;
+//      FP32 data): in-thread, then across the warp by shuffles, plus the
+//      running sums of the tile's earlier sub-tiles (carried in registers);
 //   C. from the tile's exclusive prefix Pt over the earlier tiles of its
-//      (group, coordinate), two per-column constants formed in FP64:
+//      (group, coordinate), two per-column constants formed in FP64 once per
+//      tile:
 //        alpha = Pt_z,   gamma = Pt_xz - (b - mu) Pt_z,
 //      so that 2 (x_r P_z[r] - P_xz[r]) = 2 ((x_r - b)(alpha + Lz_r) - (gamma + Lxz_r)):
 //      the large terms are combined in FP64 once per tile and each element
@@ -45,11 +48,11 @@
 //   l1_aggregate + l1_tile_scan form every tile's sums of z and (x - mu) z
 //   (one warp per tile, 256-bit row loads) and their exclusive scan over the
 //   tiles of each (group, coordinate) in FP64: Pt.
-//   l1_query (claims in (group, coordinate, tile) order, the next tile's
-//   permutation and coordinates loaded while the current one is evaluated)
-//   does steps A-D; a thread takes SEG_LEN consecutive positions and one
-//   16-byte slice (QW columns) of their rows, the rest of a row on the
-//   adjacent thread.
+//   l1_query (claims in (group, coordinate, tile) order, the next
+//   sub-tile's permutation and coordinates loaded while the current one is
+//   evaluated) does steps A-D; a thread takes SEG_LEN consecutive positions
+//   and one 16-byte slice (QW columns) of their rows, the rest of a row on
+//   the adjacent lane.  No shared memory and no block barrier.
 //   Step D, default mode: every value is added into the Acc-type outg with
 //   vector reductions in L2 (no waits; the order of the d additions per
 //   element varies from run to run); l1_finalize then writes
@@ -58,7 +61,9 @@
 //   (bounded spin) until every tile of coordinate c-1 of its group is done,
 //   then adds its values into the FP64 partial output outw with plain loads
 //   and stores, in coordinate order; the last coordinate writes out.
-// Every wait is on work claimed earlier by a running CTA: no deadlock.
+// Every wait is on tiles claimed earlier by running warps (a warp claims its
+// next tile before finishing the current one, never before starting it): the
+// unfinished tile claimed first waits on nothing unfinished, so no deadlock.
 // Integer data run the same steps exactly in int64.
 #include <algorithm>
 
@@ -80,9 +85,10 @@ struct QCfg {
     // The tile lives in registers: no shared-memory staging.
     static constexpr int QW = (16 / (int)sizeof(V)) < KC ? (16 / (int)sizeof(V)) : KC;
     static constexpr int NQ = KC / QW;
-    static constexpr int SEGS = kThreads / NQ;
+    static constexpr int SEGS = 32 / NQ;                       // segments per sub-tile (one warp)
     static constexpr int SEG_LEN = sizeof(Acc) == 8 ? 4 : 8;
-    static constexpr int TILE_E = SEGS * SEG_LEN;              // sorted positions per tile
+    static constexpr int SUB_E = SEGS * SEG_LEN;               // sorted positions per sub-tile
+    static constexpr int TILE_E = 8 * SUB_E;                   // sorted positions per tile
     static constexpr int NV = 2 * KC;                          // scanned quantities
     static_assert(KC % QW == 0, "tile shape");
 };
@@ -238,146 +244,131 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
     using Acc = typename Types<DT>::Acc;
     using Wide = typename Types<DT>::Wide;
     using Out = typename Types<DT>::Out;
-    constexpr int SEG_LEN = Cfg::SEG_LEN, TILE_E = Cfg::TILE_E, NV = Cfg::NV;
-    constexpr int QW = Cfg::QW, NQ = Cfg::NQ;
-    constexpr int SPW = 32 / NQ;   // segments per warp
+    constexpr int SEG_LEN = Cfg::SEG_LEN, SUB_E = Cfg::SUB_E, TILE_E = Cfg::TILE_E, NV = Cfg::NV;
+    constexpr int QW = Cfg::QW, NQ = Cfg::NQ, SPW = Cfg::SEGS;
+    constexpr unsigned kFull = 0xffffffffu;
 
-    // Double-buffered by the iteration's slot: a warp writes buffer b of the
-    // next-but-one iteration only after the first barrier of the iteration in
-    // between, which every warp reaches only after its last read of b.
-    __shared__ Acc wt[2][kWarps][NV];
-    __shared__ Acc ag_s[2][2][KC];     // alpha, gamma
-    __shared__ Wide ag_w[2][2][KC];    // R^T Z, 1^T Z (coordinate 0)
-    __shared__ uint32_t s_claim[2];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int quad = tid % NQ, seg = tid / NQ;
+    // Every warp works alone (no block barrier): it claims whole tiles from
+    // the counter and walks each in sub-tiles of SUB_E positions, carrying
+    // the running in-tile sums from one sub-tile to the next.
+    const int lane = threadIdx.x & 31;
+    const int quad = lane % NQ, seg = lane / NQ;
     const int col0 = quad * QW;                 // first column of this thread
     const int d = p.d, T = p.T, k = p.k;
     const uint32_t total_tiles = (uint32_t)p.G * (uint32_t)d * (uint32_t)T;
     const int i0 = seg * SEG_LEN;
 
-    // The permutation and coordinates of the next tile are loaded while the
-    // current tile is evaluated (claims stay in order, one tile ahead).
+    // The permutation and coordinates of the next sub-tile (of this tile or
+    // of the next claimed one) are loaded while the current one is evaluated.
     int32_t pe[SEG_LEN];
     V xv[SEG_LEN];
-    auto load_tile = [&](uint32_t claim, int32_t (&pv)[SEG_LEN], V (&xw)[SEG_LEN]) {
+    auto load_sub = [&](uint32_t claim, int s, int32_t (&pv)[SEG_LEN], V (&xw)[SEG_LEN]) {
         const int t = (int)(claim % (uint32_t)T);
         const int c = (int)((claim / (uint32_t)T) % (uint32_t)d);
         const int64_t e0 = (int64_t)t * TILE_E;
         const int ne = (int)min64(TILE_E, p.n - e0);
-        const int64_t sbase = (int64_t)c * p.n + e0;
+        const int64_t sbase = (int64_t)c * p.n + e0 + s * SUB_E + i0;
+        const int lim = ne - s * SUB_E - i0;
 #pragma unroll
         for (int i = 0; i < SEG_LEN; ++i) {
             pv[i] = -1;
             xw[i] = V(0);
-            if (i0 + i < ne) { pv[i] = __ldcs(p.perm + sbase + i0 + i); xw[i] = __ldcs(p.xs + sbase + i0 + i); }
+            if (i < lim) { pv[i] = __ldcs(p.perm + sbase + i); xw[i] = __ldcs(p.xs + sbase + i); }
         }
     };
-    if (tid == 0) s_claim[0] = atomicAdd(p.counter, 1u);
-    __syncthreads();
-    uint32_t claim = s_claim[0];
-    if (claim < total_tiles) load_tile(claim, pe, xv);
-    int slot = 0;
+    uint32_t mine = 0;
+    if (lane == 0) mine = atomicAdd(p.counter, 1u);
+    uint32_t claim = __shfl_sync(kFull, mine, 0);
+    if (claim < total_tiles) load_sub(claim, 0, pe, xv);
+    bool bad = false;
 
     while (claim < total_tiles) {
-        if (tid == 0) s_claim[slot ^ 1] = atomicAdd(p.counter, 1u);
+        if (lane == 0) mine = atomicAdd(p.counter, 1u);     // the next tile
         const int t = (int)(claim % (uint32_t)T);
         const int c = (int)((claim / (uint32_t)T) % (uint32_t)d);
         const int g = (int)(claim / ((uint32_t)T * (uint32_t)d));
         const int64_t e0 = (int64_t)t * TILE_E;
         const int ne = (int)min64(TILE_E, p.n - e0);
+        const int nsub = (ne + SUB_E - 1) / SUB_E;
         const int64_t sbase = (int64_t)c * p.n + e0;
         const V b = __ldcs(p.xs + sbase);
-
-        // A. this thread's positions: x - b, checked permutation, gathered columns
-        Acc dx[SEG_LEN];
+        // C. the tile's exclusive prefix Pt over the earlier tiles (from the
+        // tile scan), this thread's columns -> alpha, gamma (formed in Wide)
+        Acc al[QW], gm[QW];
         {
-            bool bad = false;
+            const Wide* pr = p.pre + (((int64_t)g * d + c) * T + t) * NV;
+            const Wide bm = (Wide)b - (Wide)p.mu[(int64_t)c * p.mu_stride];
 #pragma unroll
-            for (int i = 0; i < SEG_LEN; ++i) {
-                if (i0 + i < ne && (uint32_t)pe[i] >= (uint32_t)p.n) { bad = true; pe[i] = -1; }   // never for a valid plan
-                dx[i] = i0 + i < ne ? diff(xv[i], b) : Acc(0);
+            for (int q = 0; q < QW; ++q) {
+                const Wide Pz = pr[col0 + q], Pxz = pr[KC + col0 + q];
+                al[q] = (Acc)Pz;
+                gm[q] = (Acc)(Pxz - bm * Pz);
             }
-            if (bad) set_error(p.err, kErrInternal);
         }
-        V zv[SEG_LEN][QW];
-        {
-            const V* zg = p.Zg + (int64_t)g * p.n * KC + col0;
+        Acc Cz[QW], Cxz[QW];                    // in-tile sums of the earlier sub-tiles
+#pragma unroll
+        for (int q = 0; q < QW; ++q) { Cz[q] = 0; Cxz[q] = 0; }
+        uint32_t next = 0;
+
+        for (int s = 0; s < nsub; ++s) {
+            const int lim = ne - s * SUB_E - i0;
+            // A. this thread's positions: x - b, checked permutation, gathered columns
+            Acc dx[SEG_LEN];
 #pragma unroll
             for (int i = 0; i < SEG_LEN; ++i) {
-                if (pe[i] >= 0) ld_vec<V, QW>(zg + (int64_t)pe[i] * KC, zv[i]);
-                else {
+                if (i < lim && (uint32_t)pe[i] >= (uint32_t)p.n) { bad = true; pe[i] = -1; }   // never for a valid plan
+                dx[i] = i < lim ? diff(xv[i], b) : Acc(0);
+            }
+            V zv[SEG_LEN][QW];
+            {
+                const V* zg = p.Zg + (int64_t)g * p.n * KC + col0;
 #pragma unroll
-                    for (int q = 0; q < QW; ++q) zv[i][q] = V(0);
+                for (int i = 0; i < SEG_LEN; ++i) {
+                    if (pe[i] >= 0) ld_vec<V, QW>(zg + (int64_t)pe[i] * KC, zv[i]);
+                    else {
+#pragma unroll
+                        for (int q = 0; q < QW; ++q) zv[i][q] = V(0);
+                    }
                 }
             }
-        }
+            // B. exclusive in-tile prefix Lz, Lxz of this thread's segment:
+            // in-thread sums, a shuffle scan over the warp's segments, plus
+            // the carry of the earlier sub-tiles
+            Acc Lz[QW], Lxz[QW];
+#pragma unroll
+            for (int q = 0; q < QW; ++q) {
+                Acc sz = 0, sxz = 0;
+#pragma unroll
+                for (int i = 0; i < SEG_LEN; ++i) {
+                    const Acc z = (Acc)zv[i][q];
+                    sz += z;
+                    sxz = fmac(dx[i], z, sxz);
+                }
+                Acc iz = sz, ixz = sxz;
+#pragma unroll
+                for (int o = 1; o < SPW; o <<= 1) {
+                    const Acc a = __shfl_up_sync(kFull, iz, o * NQ);
+                    const Acc bb = __shfl_up_sync(kFull, ixz, o * NQ);
+                    if (lane >= o * NQ) { iz += a; ixz += bb; }
+                }
+                Lz[q] = Cz[q] + (iz - sz);
+                Lxz[q] = Cxz[q] + (ixz - sxz);
+            }
+            // D. (ordered) coordinate order: wait for every tile of coordinate c-1
+            if (ORDERED && s == 0) {
+                if (c > 0 && lane == 0) wait_geq(p.done + (int64_t)g * d + c - 1, (uint32_t)T, p.err, p.spin_limit);
+                __syncwarp();
+            }
+            int32_t pe_n[SEG_LEN];
+            V xv_n[SEG_LEN];
+            if (s + 1 < nsub) {
+                load_sub(claim, s + 1, pe_n, xv_n);
+            } else {
+                next = __shfl_sync(kFull, mine, 0);
+                if (next < total_tiles) load_sub(next, 0, pe_n, xv_n);
+            }
 
-        // B. in-tile exclusive prefix of this thread's segment and columns
-        Acc Lz[QW], Lxz[QW];
-#pragma unroll
-        for (int q = 0; q < QW; ++q) {
-            Acc sz = 0, sxz = 0;
-#pragma unroll
-            for (int i = 0; i < SEG_LEN; ++i) {
-                const Acc z = (Acc)zv[i][q];
-                sz += z;
-                sxz = fmac(dx[i], z, sxz);
-            }
-            Acc iz = sz, ixz = sxz;
-#pragma unroll
-            for (int o = 1; o < SPW; o <<= 1) {
-                const Acc a = __shfl_up_sync(0xffffffffu, iz, o * NQ);
-                const Acc bb = __shfl_up_sync(0xffffffffu, ixz, o * NQ);
-                if (lane >= o * NQ) { iz += a; ixz += bb; }
-            }
-            Acc ez = __shfl_up_sync(0xffffffffu, iz, NQ);
-            Acc exz = __shfl_up_sync(0xffffffffu, ixz, NQ);
-            if (lane < NQ) { ez = 0; exz = 0; }
-            if (lane >= 32 - NQ) { wt[slot][warp][col0 + q] = iz; wt[slot][warp][KC + col0 + q] = ixz; }
-            Lz[q] = ez;
-            Lxz[q] = exz;
-        }
-        // C. the tile's exclusive prefix (from the tile scan) -> alpha, gamma
-        if (tid < KC) {
-            const Wide bm = (Wide)b - (Wide)p.mu[(int64_t)c * p.mu_stride];
-            const Wide* pr = p.pre + (((int64_t)g * d + c) * T + t) * NV;
-            const Wide Pz = pr[tid], Pxz = pr[KC + tid];
-            ag_s[slot][0][tid] = (Acc)Pz;
-            ag_s[slot][1][tid] = (Acc)(Pxz - bm * Pz);
-            if (ORDERED && c == 0) {
-                const int gc = g * KC + tid;
-                ag_w[slot][0][tid] = gc < k ? p.res[gc] : Wide(0);       // R^T Z
-                ag_w[slot][1][tid] = gc < k ? p.res[k + gc] : Wide(0);   // 1^T Z
-            }
-        }
-        // D. (ordered) coordinate order: wait for every tile of coordinate c-1
-        if (ORDERED) {
-            if (c > 0 && tid == 0) wait_geq(p.done + (int64_t)g * d + c - 1, (uint32_t)T, p.err, p.spin_limit);
-        }
-        __syncthreads();
-        const uint32_t next = s_claim[slot ^ 1];
-        int32_t pe_n[SEG_LEN];
-        V xv_n[SEG_LEN];
-        if (next < total_tiles) load_tile(next, pe_n, xv_n);
-#pragma unroll
-        for (int q = 0; q < QW; ++q) {
-            Acc pz = 0, pxz = 0;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const Acc a = wt[slot][w][col0 + q], bb = wt[slot][w][KC + col0 + q];
-                if (w < warp) { pz += a; pxz += bb; }
-            }
-            Lz[q] += pz;
-            Lxz[q] += pxz;
-        }
-
-        // E. evaluate and accumulate
-        {
-            Acc al[QW], gm[QW];
-#pragma unroll
-            for (int q = 0; q < QW; ++q) { al[q] = ag_s[slot][0][col0 + q]; gm[q] = ag_s[slot][1][col0 + q]; }
+            // E. evaluate and accumulate
             if constexpr (!ORDERED) {
                 // every value added into outg with a vector reduction in L2
                 Acc* og = p.outg + (int64_t)g * p.n * KC + col0;
@@ -398,12 +389,6 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
                 // the Wide type (FP64 for FP32 data), each term added once
                 const bool first = c == 0, final_ = c == d - 1;
                 const int kg = min(KC, k - g * KC);
-                Wide rz[QW], uz[QW];
-#pragma unroll
-                for (int q = 0; q < QW; ++q) {
-                    rz[q] = first ? ag_w[slot][0][col0 + q] : Wide(0);
-                    uz[q] = first ? ag_w[slot][1][col0 + q] : Wide(0);
-                }
                 Wide* ow = p.outw + (int64_t)g * p.n * KC + col0;
                 Out* oc = static_cast<Out*>(p.out) + (int64_t)g * KC + col0;
                 Wide old[SEG_LEN][QW];
@@ -412,9 +397,13 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
                     if (pe[i] >= 0 && !first) {
                         ldcg_vec<Wide, QW>(ow + (int64_t)pe[i] * KC, old[i]);
                     } else if (pe[i] >= 0) {
+                        // coordinate 0 starts from R^T Z - R_k 1^T Z
                         const Wide Rk = (Wide)p.R[pe[i]];
 #pragma unroll
-                        for (int q = 0; q < QW; ++q) old[i][q] = rz[q] - Rk * uz[q];
+                        for (int q = 0; q < QW; ++q) {
+                            const int gc = g * KC + col0 + q;
+                            old[i][q] = gc < k ? p.res[gc] - Rk * p.res[k + gc] : Wide(0);
+                        }
                     } else {
 #pragma unroll
                         for (int q = 0; q < QW; ++q) old[i][q] = 0;
@@ -442,20 +431,24 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
                     }
                 }
             }
+            // the running sums through this sub-tile, from its last segment
+#pragma unroll
+            for (int q = 0; q < QW; ++q) {
+                Cz[q] = __shfl_sync(kFull, Lz[q], (SPW - 1) * NQ + quad);
+                Cxz[q] = __shfl_sync(kFull, Lxz[q], (SPW - 1) * NQ + quad);
+            }
+#pragma unroll
+            for (int i = 0; i < SEG_LEN; ++i) { pe[i] = pe_n[i]; xv[i] = xv_n[i]; }
         }
-
-        // F. (ordered) this tile's values are in place before it is counted;
-        // the L2-reduction mode needs no barrier here (double buffers)
-        if constexpr (ORDERED) {
+        if (ORDERED) {
+            // F. this tile's values are in place before it is counted
             __threadfence();
-            __syncthreads();
-            if (tid == 0) red_release_add(p.done + (int64_t)g * d + c, 1u);
+            __syncwarp();
+            if (lane == 0) red_release_add(p.done + (int64_t)g * d + c, 1u);
         }
         claim = next;
-        slot ^= 1;
-#pragma unroll
-        for (int i = 0; i < SEG_LEN; ++i) { pe[i] = pe_n[i]; xv[i] = xv_n[i]; }
     }
+    if (bad) set_error(p.err, kErrInternal);
 }
 
 // Tile aggregates (the reduce half of reduce-then-scan): one warp per tile
@@ -923,9 +916,11 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0);
     if (e != cudaSuccess) return e;
+    // a warp per claimed tile; every CTA resident (the ordered mode's waits
+    // are on tiles claimed by running warps)
     const int64_t total_tiles = (int64_t)p.G * p.d * p.T;
     const int64_t blocks = std::max<int64_t>(
-        1, std::min<int64_t>(total_tiles, (int64_t)std::max(occ, 1) * a.num_sms));
+        1, std::min<int64_t>((total_tiles + kWarps - 1) / kWarps, (int64_t)std::max(occ, 1) * a.num_sms));
     kern<<<(unsigned)blocks, kThreads, 0, st>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*launches;
