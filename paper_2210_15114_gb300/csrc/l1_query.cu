@@ -524,27 +524,39 @@ l1_aggregate_kernel(const typename Types<DT>::V* __restrict__ xs, const int32_t*
             for (int u = 0; u < U; ++u) { pe[u] = pe_n[u]; dx[u] = dx_n[u]; }
         }
         if (bad) set_error(err, kErrInternal);
-        // Lane q keeps the sums of column q; lanes < NV then convert once.
-        Acc sel_a = 0, sel_x = 0;
+        // Reduce-scatter over the warp: each halving step trades half of the
+        // NV sums with the lane o apart, after which lane L holds the warp
+        // total of quantity L >> (5 - H) (sums of z first, then of (x - b) z).
+        constexpr int H = NV == 16 ? 4 : NV == 8 ? 3 : NV == 4 ? 2 : 1;
+        static_assert((1 << H) == NV, "NV is a power of two up to 16");
+        Acc v[NV];
 #pragma unroll
-        for (int q = 0; q < KC; ++q) {
-            Acc a = sz[q], x = sxz[q];
+        for (int q = 0; q < KC; ++q) { v[q] = sz[q]; v[KC + q] = sxz[q]; }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-                x += __shfl_xor_sync(0xffffffffu, x, o);
+        for (int h = 0; h < H; ++h) {
+            const int o = 16 >> h, half = NV >> (h + 1);
+            const bool up = lane & o;
+#pragma unroll
+            for (int j = 0; j < half; ++j) {
+                const Acc keep = up ? v[j + half] : v[j];
+                const Acc send = up ? v[j] : v[j + half];
+                v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
             }
-            if (lane == q || lane == KC + q) { sel_a = a; sel_x = x; }
         }
-        if (lane < NV) {
+        Acc tot = v[0];
+#pragma unroll
+        for (int o = 16 >> H; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        const int qi = lane >> (5 - H);                       // the quantity this lane holds
+        const Acc tz = __shfl_sync(0xffffffffu, tot, (qi % KC) << (5 - H));   // sum z of its column
+        if ((lane & ((1 << (5 - H)) - 1)) == 0) {
             Wide mine;
-            if (lane < KC) {
-                mine = (Wide)sel_a;
+            if (qi < KC) {
+                mine = (Wide)tot;
             } else {
                 const Wide bm = (Wide)b - (Wide)mu[(int64_t)c * mu_stride];
-                mine = bm * (Wide)sel_a + (Wide)sel_x;
+                mine = bm * (Wide)tz + (Wide)tot;
             }
-            agg[tile * NV + lane] = mine;
+            agg[tile * NV + qi] = mine;
         }
     }
 }
@@ -865,13 +877,14 @@ cudaError_t launch_kc(const L1QueryArgs& a, cudaStream_t st, int64_t* launches, 
     }
 
     if (stage == 3) {   // tile aggregates + per-segment exclusive scan
+        auto kern = l1_aggregate_kernel<DT, KC>;
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, l1_aggregate_kernel<DT, KC>, kThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0);
         if (e != cudaSuccess) return e;
         const int64_t warps = L.G * a.d * L.T;
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(
             (warps + kWarps - 1) / kWarps, (int64_t)std::max(occ, 1) * a.num_sms));
-        l1_aggregate_kernel<DT, KC><<<(unsigned)blocks, kThreads, 0, st>>>(
+        kern<<<(unsigned)blocks, kThreads, 0, st>>>(
             static_cast<const V*>(a.xs), a.perm, a.n, (int)a.d, reinterpret_cast<const V*>(sc + L.zg),
             static_cast<const V*>(a.mu), a.mu_stride, reinterpret_cast<Wide*>(sc + L.pre), (int)L.T,
             (int)L.G, a.err);

@@ -202,9 +202,14 @@ keygen_hist_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64
 template <dm_dtype DT>
 struct PassCfg {
     using Key = typename Types<DT>::Key;
-    static constexpr int ITEMS = sizeof(Key) == 4 ? 12 : 8;   // keys per thread
+    static constexpr int ITEMS = sizeof(Key) == 4 ? 20 : 8;   // keys per thread (20: measured best of 8-32)
     static constexpr int TILE = kThreads * ITEMS;
+    // the tile's keys and payload, staged for the scatter (dynamic shared memory)
+    static constexpr size_t smem = (size_t)TILE * (sizeof(Key) + sizeof(int32_t));
 };
+
+template <dm_dtype DT>
+cudaError_t onesweep_smem_attr();
 
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
@@ -230,8 +235,9 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
     __shared__ uint32_t tile_start[kRadix];
     __shared__ uint32_t gbase[kRadix];
     __shared__ uint32_t warp_tot[kWarps];
-    __shared__ __align__(16) Key sk[TILE];
-    __shared__ int32_t sv[TILE];
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    Key* sk = reinterpret_cast<Key*>(os_smem);                             // [TILE]
+    int32_t* sv = reinterpret_cast<int32_t*>(os_smem + (size_t)TILE * sizeof(Key));   // [TILE]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
@@ -379,6 +385,15 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
 }
 
 template <dm_dtype DT>
+cudaError_t onesweep_smem_attr() {
+    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PassCfg<DT>::smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(onesweep_kernel<DT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared);
+}
+
+template <dm_dtype DT>
 cudaError_t launch_keygen_t(const SortArgs& a, cudaStream_t s) {
     using Cfg = KeygenCfg<DT>;
     auto kern = keygen_hist_kernel<DT>;
@@ -411,11 +426,13 @@ cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, 
     Key* kbuf[2] = {static_cast<Key*>(a.keys_b), static_cast<Key*>(a.keys_a)};
     int32_t* vbuf[2] = {a.vals_b, a.vals_a};
     const size_t lb_stride = (size_t)a.d * T * kRadix;
+    cudaError_t ea = onesweep_smem_attr<DT>();
+    if (ea != cudaSuccess) return ea;
     for (int i = 0; i < npass; ++i) {
         const int first = i == 0, last = i == npass - 1;
         Key* kout = kbuf[i & 1];
         int32_t* vout = vbuf[i & 1];
-        onesweep_kernel<DT><<<(unsigned)(a.d * T), kThreads, 0, s>>>(
+        onesweep_kernel<DT><<<(unsigned)(a.d * T), kThreads, PassCfg<DT>::smem, s>>>(
             kin, vin, kout, vout, static_cast<V*>(a.sorted_out), a.perm_out, a.hist,
             a.lookback + i * lb_stride, a.counters + i, a.n, (int)a.d, pass_list[i], P, T, first,
             last, a.err, a.spin_limit);
@@ -438,7 +455,9 @@ cudaError_t sort_launch_unpublished_wait(const SortArgs& a, cudaStream_t s, int6
     if (a.dtype != DM_F32 || a.d != 1 || a.n != 2 * TILE) return cudaErrorInvalidValue;
     // One CTA; it claims ticket 1 = (column 0, tile 1) and waits for tile 0.
     // First pass (no payload read), not the last (keys_b / vals_b written).
-    onesweep_kernel<DM_F32><<<1, kThreads, 0, s>>>(
+    cudaError_t ea = onesweep_smem_attr<DM_F32>();
+    if (ea != cudaSuccess) return ea;
+    onesweep_kernel<DM_F32><<<1, kThreads, PassCfg<DM_F32>::smem, s>>>(
         static_cast<const Key*>(a.keys_a), nullptr, static_cast<Key*>(a.keys_b), a.vals_b, nullptr,
         nullptr, a.hist, a.lookback, a.counters, a.n, 1, 0, sort_passes(DM_F32), 2, 1, 0, a.err,
         a.spin_limit);
