@@ -307,11 +307,32 @@ dm_status dm_bruteforce(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
 /* End to end with HOST buffers: copies X and Z to the device, preprocesses,
  * computes out = A Z, copies out back and synchronizes.  Host buffers may be
  * pageable or pinned (pinned is faster).  Device buffers are taken from the
- * context's scratch arena. */
+ * context's device buffers for host calls, grown on demand.
+ *
+ * Host-to-device copies of calls on one device (any contexts, any threads)
+ * cross the host link in the order the calls issue them: a call's copies of
+ * X and Z start when the previous call's copies have finished, so that every
+ * call's preprocessing starts as soon as its own inputs are in. */
 dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
                          const void* X_host, int64_t n, int64_t d, int64_t ldx,
                          const void* Z_host, int64_t k, int64_t ldz,
                          void* out_host, int64_t ldo);
+
+/* dm_matmat_host without the final wait: the copies, preprocessing, product
+ * and copy back are issued on the context's streams and the call returns
+ * (for l1 plans after the key histograms have been read back, which waits
+ * for the copy of X and the key pass).  out_host holds the result, and
+ * device-side errors are reported, after the next dm_sync(ctx).  X_host,
+ * Z_host and out_host must stay allocated, and X_host and Z_host unchanged,
+ * until then; with pageable buffers the copies are synchronous, so pinned
+ * buffers are the useful case.  Issuing the calls of several contexts one
+ * after the other from one thread and then calling dm_sync on each runs
+ * them concurrently, their copies in issue order.  A later host call on the
+ * same context waits for this call's copy of Z. */
+dm_status dm_matmat_host_async(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
+                               const void* X_host, int64_t n, int64_t d, int64_t ldx,
+                               const void* Z_host, int64_t k, int64_t ldz,
+                               void* out_host, int64_t ldo);
 
 /* Number of kernels this context has launched so far (all calls). */
 int64_t dm_launch_count(const dm_ctx* ctx);

@@ -82,6 +82,7 @@ def load() -> ctypes.CDLL:
             "dm_plan_export": ([P, P, P], I32),
             "dm_bruteforce": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
             "dm_matmat_host": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
+            "dm_matmat_host_async": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
             "dm_launch_count": ([P], I64),
             "dm_profile_enable": ([P, I32], I32),
             "dm_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int), P, P, P], I32),
@@ -524,8 +525,7 @@ def dm_bruteforce(ctx: Context, metric, X, Z, out=None):
     return out.reshape(-1) if squeeze else out
 
 
-def dm_matmat_host(ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out: np.ndarray = None):
-    """End to end with host (numpy) buffers; returns the numpy result."""
+def _host_call(fn_name, ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out):
     m = METRICS[metric] if isinstance(metric, str) else int(metric)
     if X.ndim == 1:
         X = X.reshape(-1, 1)
@@ -536,10 +536,22 @@ def dm_matmat_host(ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out: np.n
     k = Z2.shape[1]
     if out is None:
         out = np.empty((n, k), dtype=out_numpy_dtype(code))
-    _check(load().dm_matmat_host(ctx.handle, m, code, ctypes.c_void_p(X.ctypes.data), n, d, _ld(X),
-                                 ctypes.c_void_p(Z2.ctypes.data), k, _ld(Z2),
-                                 ctypes.c_void_p(out.ctypes.data), _ld(out)), "dm_matmat_host")
+    _check(getattr(load(), fn_name)(ctx.handle, m, code, ctypes.c_void_p(X.ctypes.data), n, d, _ld(X),
+                                    ctypes.c_void_p(Z2.ctypes.data), k, _ld(Z2),
+                                    ctypes.c_void_p(out.ctypes.data), _ld(out)), fn_name)
     return out.reshape(-1) if squeeze else out
+
+
+def dm_matmat_host(ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out: np.ndarray = None):
+    """End to end with host (numpy) buffers; returns the numpy result."""
+    return _host_call("dm_matmat_host", ctx, metric, X, Z, out)
+
+
+def dm_matmat_host_async(ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out: np.ndarray = None):
+    """dm_matmat_host without the final wait: returns the numpy array the
+    result lands in after the next dm_sync(ctx).  X, Z and the returned array
+    must stay alive (and X, Z unchanged) until then."""
+    return _host_call("dm_matmat_host_async", ctx, metric, X, Z, out)
 
 
 def dm_launch_count(ctx: Context) -> int:

@@ -1365,9 +1365,30 @@ dm_status dm_bruteforce(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const voi
     return DM_OK;
 }
 
-dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* Xh, int64_t n,
-                         int64_t d, int64_t ldx, const void* Zh, int64_t k, int64_t ldz,
-                         void* outh, int64_t ldo) {
+}  // extern "C"
+
+namespace {
+
+// Order of the host-to-device copies of concurrent dm_matmat_host calls on
+// one device: each call's copies of X and Z wait for the previous call's
+// copies, so the calls take the host link one after the other at its full
+// rate instead of sharing it (the first call's preprocessing then starts
+// after its own copies, not after everyone's).  One event per device, moved
+// under the mutex.
+struct LinkOrder {
+    std::mutex mu;
+    std::map<int, cudaEvent_t> last_h2d;
+};
+LinkOrder& link_order() {
+    static LinkOrder* L = new LinkOrder();   // never destroyed: calls may run at exit
+    return *L;
+}
+
+// The copies, preprocessing, product and copy back of dm_matmat_host,
+// issued on the context's streams without waiting for them.
+dm_status matmat_host_issue(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* Xh, int64_t n,
+                            int64_t d, int64_t ldx, const void* Zh, int64_t k, int64_t ldz, void* outh,
+                            int64_t ldo) {
     if (!ctx || ctx->destroyed || !Xh || !Zh || !outh || !valid_metric(metric) || !valid_dtype(dtype))
         return DM_ERR_INVALID_ARG;
     if (n < 1 || n > kMaxN || d < 1 || ldx < d || k < 1 || ldz < k || ldo < k) return DM_ERR_INVALID_ARG;
@@ -1386,13 +1407,21 @@ dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const vo
     // stream while X is preprocessed, and the product waits for it.  (The
     // second stream waits for the X copy, and with it for earlier work on the
     // context's stream, which may still read the previous Z.)
-    DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hx, d * es, Xh, ldx * es, d * es, n, cudaMemcpyHostToDevice,
-                                  ctx->stream));
-    DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->stream));
-    DM_TRY_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->aux_done, 0));
-    DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hz, k * es, Zh, ldz * es, k * es, n, cudaMemcpyHostToDevice,
-                                  ctx->aux));
-    DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->aux));
+    {
+        LinkOrder& L = link_order();
+        std::lock_guard<std::mutex> lock(L.mu);
+        cudaEvent_t& last = L.last_h2d[ctx->device];
+        if (!last) DM_TRY_CUDA(cudaEventCreateWithFlags(&last, cudaEventDisableTiming));
+        else DM_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, last, 0));
+        DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hx, d * es, Xh, ldx * es, d * es, n, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->stream));
+        DM_TRY_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->aux_done, 0));
+        DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hz, k * es, Zh, ldz * es, k * es, n, cudaMemcpyHostToDevice,
+                                      ctx->aux));
+        DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->aux));
+        DM_TRY_CUDA(cudaEventRecord(last, ctx->aux));
+    }
     dm_plan* p = nullptr;
     DM_TRY(dm_prepare(ctx, metric, dtype, ctx->hx, n, d, d, &p));
     DM_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->aux_done, 0));
@@ -1402,9 +1431,28 @@ dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const vo
                                           cudaMemcpyDeviceToHost, ctx->stream);
         s = from_cuda(e);
     }
-    if (s == DM_OK) s = dm_sync(ctx);
+    // the plan's buffers go back to the context's pool: later use of them is
+    // ordered after this product on the same stream
     dm_plan_destroy(p);
     return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+dm_status dm_matmat_host(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* Xh, int64_t n,
+                         int64_t d, int64_t ldx, const void* Zh, int64_t k, int64_t ldz,
+                         void* outh, int64_t ldo) {
+    dm_status s = matmat_host_issue(ctx, metric, dtype, Xh, n, d, ldx, Zh, k, ldz, outh, ldo);
+    if (s == DM_OK) s = dm_sync(ctx);
+    return s;
+}
+
+dm_status dm_matmat_host_async(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, const void* Xh, int64_t n,
+                               int64_t d, int64_t ldx, const void* Zh, int64_t k, int64_t ldz,
+                               void* outh, int64_t ldo) {
+    return matmat_host_issue(ctx, metric, dtype, Xh, n, d, ldx, Zh, k, ldz, outh, ldo);
 }
 
 }  // extern "C"

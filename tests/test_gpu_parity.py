@@ -311,6 +311,30 @@ def test_host_entry_point(dm, ctx, metric):
     check(got, reference(metric, X, Z), np.float32)
 
 
+def test_host_entry_point_async(dm, ctx):
+    # two contexts, calls issued from one thread (copies in issue order on the
+    # host link), results read after dm_sync; a second round with new Z and
+    # the same buffers, then a blocking call on the first context
+    X, Z = inputs.workload_mixture_f32(n=30011, d=12, k=5)
+    Z2 = (Z[::-1] * 0.5 + 1.0).copy()
+    ctx2 = dm.dm_create(0)
+    try:
+        for Zq in (Z, Z2):
+            o1 = dm.dm_matmat_host_async(ctx, "l1", X, Zq)
+            o2 = dm.dm_matmat_host_async(ctx2, "l2sq", X, Zq)
+            dm.dm_sync(ctx)
+            dm.dm_sync(ctx2)
+            check(o1, reference("l1", X, Zq), np.float32)
+            check(o2, reference("l2sq", X, Zq), np.float32)
+        o3 = dm.dm_matmat_host_async(ctx, "l2sq", X, Z)
+        o4 = dm.dm_matmat_host(ctx, "l1", X, Z2)       # waits for the first call's copy of Z
+        dm.dm_sync(ctx)
+        check(o3, reference("l2sq", X, Z), np.float32)
+        check(o4, reference("l1", X, Z2), np.float32)
+    finally:
+        dm.dm_destroy(ctx2)
+
+
 # ----------------------------------------------------------- full size
 @pytest.fixture(scope="module")
 def full_fp32():
