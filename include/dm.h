@@ -334,6 +334,23 @@ dm_status dm_matmat_host_async(dm_ctx* ctx, dm_metric metric, dm_dtype dtype,
                                const void* Z_host, int64_t k, int64_t ldz,
                                void* out_host, int64_t ldo);
 
+/* Several products of the same points and queries end to end with HOST
+ * buffers: out_host[i] = A_i Z for the distance matrix A_i of metrics[i]
+ * (DM_L1 or DM_L2SQ; 1 <= count <= 8), each out_host[i] an n x k buffer with
+ * leading dimension ldo.  X and Z cross the host link once (in the device's
+ * link order, as for dm_matmat_host); each product is preprocessed and
+ * computed on a context of its own (this one for the first, internal peer
+ * contexts with their own streams and scratch for the others, created on
+ * first use and released with this context), so the products run side by
+ * side, and each result is copied back as soon as it is done.  Returns when
+ * every result is in place; the first error of any product is returned.
+ * The context's settings (dm_set_deterministic, dm_set_wait_limit,
+ * dm_set_engine) apply to every product. */
+dm_status dm_matmat_host_multi(dm_ctx* ctx, int count, const dm_metric* metrics, dm_dtype dtype,
+                               const void* X_host, int64_t n, int64_t d, int64_t ldx,
+                               const void* Z_host, int64_t k, int64_t ldz,
+                               void* const* out_host, int64_t ldo);
+
 /* Number of kernels this context has launched so far (all calls). */
 int64_t dm_launch_count(const dm_ctx* ctx);
 

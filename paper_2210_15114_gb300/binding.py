@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
             "dm_bruteforce": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
             "dm_matmat_host": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
             "dm_matmat_host_async": ([P, I32, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
+            "dm_matmat_host_multi": ([P, I32, P, I32, P, I64, I64, I64, P, I64, I64, P, I64], I32),
             "dm_launch_count": ([P], I64),
             "dm_profile_enable": ([P, I32], I32),
             "dm_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int), P, P, P], I32),
@@ -552,6 +553,32 @@ def dm_matmat_host_async(ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out
     result lands in after the next dm_sync(ctx).  X, Z and the returned array
     must stay alive (and X, Z unchanged) until then."""
     return _host_call("dm_matmat_host_async", ctx, metric, X, Z, out)
+
+
+def dm_matmat_host_multi(ctx: Context, metrics, X: np.ndarray, Z: np.ndarray, outs=None):
+    """Products of several metrics for the same host (numpy) X and Z, X and Z
+    copied to the device once; returns the list of numpy results."""
+    codes = [METRICS[m] if isinstance(m, str) else int(m) for m in metrics]
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    squeeze = Z.ndim == 1
+    Z2 = Z.reshape(-1, 1) if squeeze else Z
+    code = dtype_code(X.dtype)
+    n, d = X.shape
+    k = Z2.shape[1]
+    if outs is None:
+        outs = [np.empty((n, k), dtype=out_numpy_dtype(code)) for _ in codes]
+    if len(outs) != len(codes):
+        raise DMError(DM_ERR_INVALID_ARG, "one output per metric")
+    if any(o.dtype != out_numpy_dtype(code) or o.size != n * k or not o.flags.c_contiguous for o in outs):
+        raise DMError(DM_ERR_INVALID_ARG, "outputs must be contiguous n x k arrays of the output type")
+    marr = (ctypes.c_int32 * max(len(codes), 1))(*codes)
+    oarr = (ctypes.c_void_p * max(len(outs), 1))(*[o.ctypes.data for o in outs])
+    _check(load().dm_matmat_host_multi(ctx.handle, len(codes), ctypes.cast(marr, ctypes.c_void_p), code,
+                                       ctypes.c_void_p(X.ctypes.data), n, d, _ld(X),
+                                       ctypes.c_void_p(Z2.ctypes.data), k, _ld(Z2),
+                                       ctypes.cast(oarr, ctypes.c_void_p), k), "dm_matmat_host_multi")
+    return [o.reshape(-1) if squeeze else o for o in outs]
 
 
 def dm_launch_count(ctx: Context) -> int:

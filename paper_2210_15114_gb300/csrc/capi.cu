@@ -35,6 +35,12 @@ struct dm_ctx {
     cudaEvent_t aux_done = nullptr;
     void* hz = nullptr; size_t hz_bytes = 0;
     void* ho = nullptr; size_t ho_bytes = 0;
+    // dm_matmat_host_multi: the event after the copy of X, and one context
+    // (own stream, arena and error word) per product after the first, so
+    // that the products of one call run side by side.
+    cudaEvent_t x_done = nullptr;
+    std::vector<dm_ctx*> peers;
+    std::vector<cudaStream_t> peer_streams;
     // Kernel timing (dm_profile_enable / dm_profile_read).
     struct Pending { std::string name; cudaEvent_t start, stop; int64_t launches; };
     struct Stat { int64_t launches = 0; double ms = 0; };
@@ -104,6 +110,7 @@ namespace {
 using namespace dm;
 
 constexpr int64_t kMaxN = (int64_t(1) << 30) - 1;
+constexpr int kMaxHostProducts = 8;       // products of one dm_matmat_host_multi call
 
 struct DeviceGuard {
     int prev = -1;
@@ -935,6 +942,11 @@ void batch_free(dm_batch* b) {
 // stream (dm_destroy) or the stream may be gone already (the last child of a
 // destroyed context): only device-wide waits are used here.
 void ctx_free(dm_ctx* ctx) {
+    for (size_t i = 0; i < ctx->peers.size(); ++i) {
+        dm_destroy(ctx->peers[i]);             // no plans outlive a host call
+        cudaStreamDestroy(ctx->peer_streams[i]);
+    }
+    if (ctx->x_done) cudaEventDestroy(ctx->x_done);
     if (ctx->arena) cudaFree(ctx->arena);
     for (auto& b : ctx->pool) cudaFree(b.p);
     if (ctx->hx) cudaFree(ctx->hx);
@@ -1453,6 +1465,95 @@ dm_status dm_matmat_host_async(dm_ctx* ctx, dm_metric metric, dm_dtype dtype, co
                                int64_t d, int64_t ldx, const void* Zh, int64_t k, int64_t ldz,
                                void* outh, int64_t ldo) {
     return matmat_host_issue(ctx, metric, dtype, Xh, n, d, ldx, Zh, k, ldz, outh, ldo);
+}
+
+dm_status dm_matmat_host_multi(dm_ctx* ctx, int count, const dm_metric* metrics, dm_dtype dtype,
+                               const void* Xh, int64_t n, int64_t d, int64_t ldx, const void* Zh,
+                               int64_t k, int64_t ldz, void* const* outh, int64_t ldo) {
+    if (!ctx || ctx->destroyed || !metrics || !Xh || !Zh || !outh || !valid_dtype(dtype) || count < 1 ||
+        count > kMaxHostProducts)
+        return DM_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!valid_metric(metrics[i]) || !outh[i]) return DM_ERR_INVALID_ARG;
+    if (n < 1 || n > kMaxN || d < 1 || ldx < d || k < 1 || ldz < k || ldo < k) return DM_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    const size_t es = dtype_size(dtype), os = out_size(dtype);
+    const size_t out_bytes = (size_t)n * k * os;
+    DM_TRY(ensure_buffer(ctx, &ctx->hx, &ctx->hx_bytes, (size_t)n * d * es));
+    if (ctx->aux) DM_TRY_CUDA(cudaStreamSynchronize(ctx->aux));
+    DM_TRY(ensure_buffer(ctx, &ctx->hz, &ctx->hz_bytes, (size_t)n * k * es));
+    DM_TRY(ensure_buffer(ctx, &ctx->ho, &ctx->ho_bytes, out_bytes * count));
+    if (!ctx->aux) {
+        DM_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        DM_TRY_CUDA(cudaEventCreateWithFlags(&ctx->aux_done, cudaEventDisableTiming));
+    }
+    if (!ctx->x_done) DM_TRY_CUDA(cudaEventCreateWithFlags(&ctx->x_done, cudaEventDisableTiming));
+    // one context per product: the call's own for the first, peers for the rest
+    while ((int)ctx->peers.size() < count - 1) {
+        cudaStream_t ps = nullptr;
+        DM_TRY_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+        dm_ctx* peer = nullptr;
+        const dm_status cs = dm_create(&peer, ctx->device, ps);
+        if (cs != DM_OK) { cudaStreamDestroy(ps); return cs; }
+        ctx->peers.push_back(peer);
+        ctx->peer_streams.push_back(ps);
+    }
+    // X and Z cross the host link once for all products, in the device's
+    // link order (X alone first, Z on the second stream behind it)
+    {
+        LinkOrder& L = link_order();
+        std::lock_guard<std::mutex> lock(L.mu);
+        cudaEvent_t& last = L.last_h2d[ctx->device];
+        if (!last) DM_TRY_CUDA(cudaEventCreateWithFlags(&last, cudaEventDisableTiming));
+        else DM_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, last, 0));
+        DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hx, d * es, Xh, ldx * es, d * es, n, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        DM_TRY_CUDA(cudaEventRecord(ctx->x_done, ctx->stream));
+        DM_TRY_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->x_done, 0));
+        DM_TRY_CUDA(cudaMemcpy2DAsync(ctx->hz, k * es, Zh, ldz * es, k * es, n, cudaMemcpyHostToDevice,
+                                      ctx->aux));
+        DM_TRY_CUDA(cudaEventRecord(ctx->aux_done, ctx->aux));
+        DM_TRY_CUDA(cudaEventRecord(last, ctx->aux));
+    }
+    // Issue order: products whose preprocessing does not wait on the host
+    // first (an l1 plan reads its key histograms back), each on its context.
+    int order[kMaxHostProducts];
+    int m = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < count; ++i)
+            if (sorted_metric(metrics[i]) == (pass == 1)) order[m++] = i;
+    dm_status s = DM_OK;
+    int used = 0;
+    for (int j = 0; j < count && s == DM_OK; ++j) {
+        used = j + 1;
+        const int i = order[j];
+        dm_ctx* e = j == 0 ? ctx : ctx->peers[j - 1];
+        if (j > 0) {
+            e->deterministic = ctx->deterministic;
+            e->spin_limit = ctx->spin_limit;
+            e->engine = ctx->engine;
+            s = from_cuda(cudaStreamWaitEvent(e->stream, ctx->x_done, 0));
+            if (s != DM_OK) break;
+        }
+        const int64_t before = e->launches;
+        dm_plan* p = nullptr;
+        s = dm_prepare(e, metrics[i], dtype, ctx->hx, n, d, d, &p);
+        if (s != DM_OK) break;
+        void* oi = static_cast<unsigned char*>(ctx->ho) + out_bytes * i;
+        s = from_cuda(cudaStreamWaitEvent(e->stream, ctx->aux_done, 0));
+        if (s == DM_OK) s = dm_matmat(p, ctx->hz, k, k, oi, k);
+        if (s == DM_OK)
+            s = from_cuda(cudaMemcpy2DAsync(outh[i], ldo * os, oi, k * os, k * os, n,
+                                            cudaMemcpyDeviceToHost, e->stream));
+        dm_plan_destroy(p);
+        if (j > 0) ctx->launches += e->launches - before;
+    }
+    // wait for every product issued; the first error wins
+    for (int j = 0; j < used; ++j) {
+        const dm_status t = dm_sync(j == 0 ? ctx : ctx->peers[j - 1]);
+        if (s == DM_OK) s = t;
+    }
+    return s;
 }
 
 }  // extern "C"

@@ -32,7 +32,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("dm_create", "dm_destroy", "dm_prepare", "dm_plan_destroy", "dm_matvec_l1",
                      "dm_matvec_l2sq", "dm_matmat", "dm_sync", "dm_status_string",
-                     "dm_bruteforce", "dm_matmat_host", "dm_matmat_host_async", "dm_plan_export", "dm_grad",
+                     "dm_bruteforce", "dm_matmat_host", "dm_matmat_host_async", "dm_matmat_host_multi", "dm_plan_export", "dm_grad",
                      "dm_batch_create", "dm_batch_run", "dm_batch_lanes", "dm_batch_destroy",
                      "dm_prepare_lpp", "dm_prepare_l2_embed", "dm_l2sq_matmat_noalloc",
                      "dm_set_deterministic", "dm_set_engine"):

@@ -335,6 +335,37 @@ def test_host_entry_point_async(dm, ctx):
         dm.dm_destroy(ctx2)
 
 
+@pytest.mark.parametrize("metrics", [("l1", "l2sq"), ("l2sq", "l1"), ("l1",), ("l2sq", "l2sq", "l1")])
+def test_host_entry_point_multi(dm, ctx, metrics):
+    # one copy of X and Z for every product, products on peer contexts; twice
+    # in a row (the second call reuses the peers and buffers), then FP64 and
+    # int32 inputs on the same context
+    X, Z = inputs.workload_mixture_f32(n=20011, d=9, k=7)
+    for Zq in (Z, (Z * -0.25 + 0.5).astype(np.float32)):
+        outs = dm.dm_matmat_host_multi(ctx, list(metrics), X, Zq)
+        for m, o in zip(metrics, outs):
+            check(o, reference(m, X, Zq), np.float32)
+    X64, Z64 = X.astype(np.float64), Z.astype(np.float64)
+    for m, o in zip(metrics, dm.dm_matmat_host_multi(ctx, list(metrics), X64, Z64)):
+        check(o, reference(m, X64, Z64), np.float64)
+    Xi = inputs.integer_points(5003, 4, 2, 0, 1000)
+    Zi = inputs.integer_queries(5003, 3, 3)
+    for m, o in zip(metrics, dm.dm_matmat_host_multi(ctx, list(metrics), Xi, Zi)):
+        check(o, reference(m, Xi, Zi), np.int32)
+
+
+def test_host_entry_point_multi_rejects(dm, ctx):
+    X, Z = inputs.workload_mixture_f32(n=100, d=3, k=2)
+    with pytest.raises(dm.DMError):
+        dm.dm_matmat_host_multi(ctx, [], X, Z)
+    with pytest.raises(dm.DMError):
+        dm.dm_matmat_host_multi(ctx, ["l1", "tv"], X, Z)          # TV has its own entry points
+    with pytest.raises(dm.DMError):
+        dm.dm_matmat_host_multi(ctx, ["l1"] * 9, X, Z)             # at most 8 products
+    with pytest.raises(dm.DMError):
+        dm.dm_matmat_host_multi(ctx, ["l1", "l2sq"], X, Z, outs=[np.empty((100, 2), np.float32)])
+
+
 # ----------------------------------------------------------- full size
 @pytest.fixture(scope="module")
 def full_fp32():
