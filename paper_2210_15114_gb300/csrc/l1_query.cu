@@ -456,9 +456,10 @@ l1_query_kernel(QParams<typename Types<DT>::V, typename Types<DT>::Acc, typename
 // over the tile, formed as (b - mu) sum z + sum (x - b) z with b the tile's
 // first sorted value (FP32 partial sums per lane, warp tree, FP64 frame
 // shift).  No shared memory and no barriers: a pure stream of loads.
-// FP32: four CTAs per SM (64 registers) measured 4% faster than three.
+// FP32 with 8-column groups: four CTAs per SM (64 registers) measured 4%
+// faster than three; with 4-column groups the same bound made it 43% slower.
 template <dm_dtype DT, int KC>
-__global__ void __launch_bounds__(kThreads, DT == DM_F32 ? 4 : 1)
+__global__ void __launch_bounds__(kThreads, DT == DM_F32 && KC == 8 ? 4 : 1)
 l1_aggregate_kernel(const typename Types<DT>::V* __restrict__ xs, const int32_t* __restrict__ perm,
                     int64_t n, int d, const typename Types<DT>::V* __restrict__ Zg,
                     const typename Types<DT>::V* __restrict__ mu, int64_t mu_stride,

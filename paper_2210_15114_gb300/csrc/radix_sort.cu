@@ -199,23 +199,31 @@ keygen_hist_kernel(const typename Types<DT>::V* __restrict__ X, int64_t n, int64
 }
 
 // ------------------------------------------------------------ onesweep pass
-template <dm_dtype DT>
+// Keys per thread: 20 for 4-byte keys in large passes (measured best of 8-32
+// at n = 2^20, d = 32: 0.191 ms per pass against 0.212 with 12), 12 where so
+// few keys would leave the GPU short of tiles (sets of a batch with n d below
+// 2^24: 58 against 64 ms for the whole batch with 20); 8 for 8-byte keys.
+template <dm_dtype DT, bool WIDE>
 struct PassCfg {
     using Key = typename Types<DT>::Key;
-    static constexpr int ITEMS = sizeof(Key) == 4 ? 20 : 8;   // keys per thread (20: measured best of 8-32)
+    static constexpr int ITEMS = sizeof(Key) == 4 ? (WIDE ? 20 : 12) : 8;
     static constexpr int TILE = kThreads * ITEMS;
     // the tile's keys and payload, staged for the scatter (dynamic shared memory)
     static constexpr size_t smem = (size_t)TILE * (sizeof(Key) + sizeof(int32_t));
 };
 
-template <dm_dtype DT>
+bool wide_tiles(dm_dtype t, int64_t n, int64_t d) {
+    return t != DM_F64 && n * d >= (int64_t(1) << 24);
+}
+
+template <dm_dtype DT, bool WIDE>
 cudaError_t onesweep_smem_attr();
 
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
-template <dm_dtype DT>
+template <dm_dtype DT, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 3)
 onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
                 const int32_t* __restrict__ vals_in,            // null on the first pass
@@ -228,7 +236,7 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
                 uint32_t spin_limit) {
     using Key = typename Types<DT>::Key;
     using V = typename Types<DT>::V;
-    constexpr int ITEMS = PassCfg<DT>::ITEMS, TILE = PassCfg<DT>::TILE;
+    constexpr int ITEMS = PassCfg<DT, WIDE>::ITEMS, TILE = PassCfg<DT, WIDE>::TILE;
 
     __shared__ uint32_t s_tile;
     __shared__ uint32_t wcount[kWarps][kRadix];
@@ -384,12 +392,16 @@ onesweep_kernel(const typename Types<DT>::Key* __restrict__ keys_in,
     }
 }
 
-template <dm_dtype DT>
+template <dm_dtype DT, bool WIDE>
 cudaError_t onesweep_smem_attr() {
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PassCfg<DT>::smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(onesweep_kernel<DT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<DT, WIDE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PassCfg<DT, WIDE>::smem);
+    if (e != cudaSuccess || !WIDE) return e;
+    // wide tiles: three CTAs of 50 KB per SM.  (Not for the narrow tiling: a
+    // batch's lanes run other kernels beside the passes, and an SM split
+    // fixed at the maximum kept them apart: 67 against 58 ms for the batch.)
+    return cudaFuncSetAttribute(onesweep_kernel<DT, WIDE>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 cudaSharedmemCarveoutMaxShared);
 }
 
@@ -413,12 +425,12 @@ cudaError_t launch_keygen_t(const SortArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <dm_dtype DT>
-cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, cudaStream_t s,
+template <dm_dtype DT, bool WIDE>
+cudaError_t launch_passes_w(const SortArgs& a, const int* pass_list, int npass, cudaStream_t s,
                             int64_t* launches) {
     using Key = typename Types<DT>::Key;
     using V = typename Types<DT>::V;
-    constexpr int TILE = PassCfg<DT>::TILE;
+    constexpr int TILE = PassCfg<DT, WIDE>::TILE;
     const int T = (int)((a.n + TILE - 1) / TILE);
     const int P = (int)sizeof(Key);
     const Key* kin = static_cast<const Key*>(a.keys_a);
@@ -426,13 +438,13 @@ cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, 
     Key* kbuf[2] = {static_cast<Key*>(a.keys_b), static_cast<Key*>(a.keys_a)};
     int32_t* vbuf[2] = {a.vals_b, a.vals_a};
     const size_t lb_stride = (size_t)a.d * T * kRadix;
-    cudaError_t ea = onesweep_smem_attr<DT>();
+    cudaError_t ea = onesweep_smem_attr<DT, WIDE>();
     if (ea != cudaSuccess) return ea;
     for (int i = 0; i < npass; ++i) {
         const int first = i == 0, last = i == npass - 1;
         Key* kout = kbuf[i & 1];
         int32_t* vout = vbuf[i & 1];
-        onesweep_kernel<DT><<<(unsigned)(a.d * T), kThreads, PassCfg<DT>::smem, s>>>(
+        onesweep_kernel<DT, WIDE><<<(unsigned)(a.d * T), kThreads, PassCfg<DT, WIDE>::smem, s>>>(
             kin, vin, kout, vout, static_cast<V*>(a.sorted_out), a.perm_out, a.hist,
             a.lookback + i * lb_stride, a.counters + i, a.n, (int)a.d, pass_list[i], P, T, first,
             last, a.err, a.spin_limit);
@@ -445,19 +457,30 @@ cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, 
     return cudaSuccess;
 }
 
+template <dm_dtype DT>
+cudaError_t launch_passes_t(const SortArgs& a, const int* pass_list, int npass, cudaStream_t s,
+                            int64_t* launches) {
+    if constexpr (sizeof(typename Types<DT>::Key) == 4) {
+        if (wide_tiles(DT, a.n, a.d)) return launch_passes_w<DT, true>(a, pass_list, npass, s, launches);
+    }
+    return launch_passes_w<DT, false>(a, pass_list, npass, s, launches);
+}
+
 }  // namespace
 
-int sort_tile_f32() { return PassCfg<DM_F32>::TILE; }
+// The tile of a one-column FP32 pass (the narrow tiling: n d below 2^24 for
+// the two-tile column of the unpublished-wait test).
+int sort_tile_f32() { return PassCfg<DM_F32, false>::TILE; }
 
 cudaError_t sort_launch_unpublished_wait(const SortArgs& a, cudaStream_t s, int64_t* launches) {
     using Key = Types<DM_F32>::Key;
-    constexpr int TILE = PassCfg<DM_F32>::TILE;
+    constexpr int TILE = PassCfg<DM_F32, false>::TILE;
     if (a.dtype != DM_F32 || a.d != 1 || a.n != 2 * TILE) return cudaErrorInvalidValue;
     // One CTA; it claims ticket 1 = (column 0, tile 1) and waits for tile 0.
     // First pass (no payload read), not the last (keys_b / vals_b written).
-    cudaError_t ea = onesweep_smem_attr<DM_F32>();
+    cudaError_t ea = onesweep_smem_attr<DM_F32, false>();
     if (ea != cudaSuccess) return ea;
-    onesweep_kernel<DM_F32><<<1, kThreads, PassCfg<DM_F32>::smem, s>>>(
+    onesweep_kernel<DM_F32, false><<<1, kThreads, PassCfg<DM_F32, false>::smem, s>>>(
         static_cast<const Key*>(a.keys_a), nullptr, static_cast<Key*>(a.keys_b), a.vals_b, nullptr,
         nullptr, a.hist, a.lookback, a.counters, a.n, 1, 0, sort_passes(DM_F32), 2, 1, 0, a.err,
         a.spin_limit);
@@ -471,7 +494,8 @@ int sort_passes(dm_dtype t) { return key_bits(t) / 8; }
 size_t sort_hist_words(dm_dtype t, int64_t d) { return (size_t)d * sort_passes(t) * kRadix; }
 
 size_t sort_lookback_words(dm_dtype t, int64_t n, int64_t d) {
-    const int tile = (t == DM_F64) ? PassCfg<DM_F64>::TILE : PassCfg<DM_F32>::TILE;
+    // sized for the narrower tiling (more tiles)
+    const int tile = (t == DM_F64) ? PassCfg<DM_F64, false>::TILE : PassCfg<DM_F32, false>::TILE;
     const int64_t T = (n + tile - 1) / tile;
     return (size_t)sort_passes(t) * d * T * kRadix;
 }
