@@ -526,17 +526,44 @@ def dm_bruteforce(ctx: Context, metric, X, Z, out=None):
     return out.reshape(-1) if squeeze else out
 
 
-def _host_call(fn_name, ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out):
-    m = METRICS[metric] if isinstance(metric, str) else int(metric)
+def _host_args(X, Z):
+    """Host (numpy) points and queries as 2-D arrays, checked against each
+    other: the library copies n x d and n x k elements from them."""
+    if not isinstance(X, np.ndarray) or not isinstance(Z, np.ndarray):
+        raise DMError(DM_ERR_INVALID_ARG, "host calls take numpy arrays")
     if X.ndim == 1:
         X = X.reshape(-1, 1)
     squeeze = Z.ndim == 1
     Z2 = Z.reshape(-1, 1) if squeeze else Z
+    if X.ndim != 2 or Z2.ndim != 2:
+        raise DMError(DM_ERR_INVALID_ARG, "X and Z must be 1-D or 2-D")
     code = dtype_code(X.dtype)
+    if Z2.dtype != X.dtype or Z2.shape[0] != X.shape[0]:
+        raise DMError(DM_ERR_INVALID_ARG, "Z must have n rows of the points' element type")
+    return X, Z2, squeeze, code
+
+
+def _host_out(out, n, k, code):
+    """A host result buffer of the right type and shape: (n, k), or (n,) when
+    k == 1 (the library writes n rows of k elements at its leading dimension)."""
+    want = out_numpy_dtype(code)
+    if out is None:
+        return np.empty((n, k), dtype=want)
+    if not isinstance(out, np.ndarray) or out.dtype != want:
+        raise DMError(DM_ERR_INVALID_ARG, f"out must be a numpy array of {np.dtype(want).name}")
+    if out.shape == (n,) and k == 1:
+        return out.reshape(n, 1)
+    if out.shape != (n, k):
+        raise DMError(DM_ERR_INVALID_ARG, f"out must have shape ({n}, {k})")
+    return out
+
+
+def _host_call(fn_name, ctx: Context, metric, X: np.ndarray, Z: np.ndarray, out):
+    m = METRICS[metric] if isinstance(metric, str) else int(metric)
+    X, Z2, squeeze, code = _host_args(X, Z)
     n, d = X.shape
     k = Z2.shape[1]
-    if out is None:
-        out = np.empty((n, k), dtype=out_numpy_dtype(code))
+    out = _host_out(out, n, k, code)
     _check(getattr(load(), fn_name)(ctx.handle, m, code, ctypes.c_void_p(X.ctypes.data), n, d, _ld(X),
                                     ctypes.c_void_p(Z2.ctypes.data), k, _ld(Z2),
                                     ctypes.c_void_p(out.ctypes.data), _ld(out)), fn_name)
@@ -559,11 +586,7 @@ def dm_matmat_host_multi(ctx: Context, metrics, X: np.ndarray, Z: np.ndarray, ou
     """Products of several metrics for the same host (numpy) X and Z, X and Z
     copied to the device once; returns the list of numpy results."""
     codes = [METRICS[m] if isinstance(m, str) else int(m) for m in metrics]
-    if X.ndim == 1:
-        X = X.reshape(-1, 1)
-    squeeze = Z.ndim == 1
-    Z2 = Z.reshape(-1, 1) if squeeze else Z
-    code = dtype_code(X.dtype)
+    X, Z2, squeeze, code = _host_args(X, Z)
     n, d = X.shape
     k = Z2.shape[1]
     if outs is None:

@@ -4,6 +4,8 @@ would otherwise read or write outside the caller's buffers on the device).
 CPU only: the checks run on plan metadata and CPU tensors."""
 import types
 
+import numpy as np
+
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -57,3 +59,21 @@ def test_noalloc_wrapper_checks_before_the_call():
                                        torch.zeros(10, 2, dtype=torch.int32))
     with pytest.raises(binding.DMError):     # CPU tensors
         binding.dm_l2sq_matmat_noalloc(X, torch.zeros(10, 2), torch.zeros(10, 2))
+
+
+@pytest.mark.parametrize("X,Z,out", [
+    (np.zeros((10, 3), np.float32), np.zeros((9, 2), np.float32), None),          # rows differ
+    (np.zeros((10, 3), np.float32), np.zeros((10, 2), np.float64), None),         # element types differ
+    (np.zeros((10, 3), np.float32), np.zeros((10, 2), np.float32), np.zeros((10, 3), np.float32)),
+    (np.zeros((10, 3), np.float32), np.zeros((10, 2), np.float32), np.zeros((10, 2), np.float64)),
+    (np.zeros((10, 3), np.int32), np.zeros((10, 2), np.int32), np.zeros((10, 2), np.int32)),   # int64 results
+    (torch.zeros(10, 3), torch.zeros(10, 2), None),                                # not numpy
+])
+def test_host_calls_check_before_the_call(X, Z, out):
+    ctx = types.SimpleNamespace(device=0, handle=None)
+    for fn in (binding.dm_matmat_host, binding.dm_matmat_host_async):
+        with pytest.raises(binding.DMError) as e:
+            fn(ctx, "l1", X, Z, out)
+        assert e.value.status == binding.DM_ERR_INVALID_ARG
+    with pytest.raises(binding.DMError):
+        binding.dm_matmat_host_multi(ctx, ["l1", "l2sq"], X, Z, None if out is None else [out, out])
