@@ -593,7 +593,8 @@ def dm_matmat_host_multi(ctx: Context, metrics, X: np.ndarray, Z: np.ndarray, ou
         outs = [np.empty((n, k), dtype=out_numpy_dtype(code)) for _ in codes]
     if len(outs) != len(codes):
         raise DMError(DM_ERR_INVALID_ARG, "one output per metric")
-    if any(o.dtype != out_numpy_dtype(code) or o.size != n * k or not o.flags.c_contiguous for o in outs):
+    if any(not isinstance(o, np.ndarray) or o.dtype != out_numpy_dtype(code) or o.size != n * k
+           or not o.flags.c_contiguous for o in outs):
         raise DMError(DM_ERR_INVALID_ARG, "outputs must be contiguous n x k arrays of the output type")
     marr = (ctypes.c_int32 * max(len(codes), 1))(*codes)
     oarr = (ctypes.c_void_p * max(len(outs), 1))(*[o.ctypes.data for o in outs])
